@@ -1,0 +1,7 @@
+"""GB300-native supernodal sparse direct factorization.
+
+The library ``libspx.so`` (C ABI, declared in ``include/spx.h``) holds the
+host analysis and the sm_103a CUDA kernels; ``spx`` is its thin Python
+binding.  ``inputs`` draws the seeded synthetic workloads.
+"""
+__all__ = ["spx", "inputs"]
