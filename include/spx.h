@@ -1,0 +1,191 @@
+/*
+ * spx.h -- C ABI of the GB300-native supernodal sparse direct solver.
+ *
+ * The operations follow the problem statement of Lacoste et al., "Taking
+ * advantage of hybrid systems for sparse direct solvers via task-based
+ * runtimes": solve A x = b by a supernodal Cholesky (L L^T) or static-pivot
+ * LU factorization (Sec. III).  The analysis orders the unknowns by nested
+ * dissection, builds the elimination tree and the block-symbolic structure of
+ * the factor; the numerical factorization then processes, for every panel
+ * (supernode), the factorization of its diagonal block, the triangular solve
+ * of its off-diagonal blocks, and the updates of the facing panels (Sec. III,
+ * the three steps of the 1D task), all on the GPU.
+ *
+ * Conventions for every call:
+ *  - Indices are 0-based.  Matrices are CSC: colptr (int64, n+1 entries),
+ *    rowind (int32, colptr[n] entries, sorted or not), values (double).
+ *  - The caller owns every buffer it passes in and keeps ownership; the
+ *    library copies what it needs.  A handle owns all host and device memory
+ *    it allocates, released by spx_free.
+ *  - Dense right-hand sides and solutions are column-major with a leading
+ *    dimension >= n.
+ *  - A call never aborts; it returns a status.  spx_last_error gives a
+ *    message for the last failing call on a handle.  Calls on one handle are
+ *    not thread-safe; different handles are independent.
+ *  - `cuda_stream` is a cudaStream_t (NULL: the legacy default stream); all
+ *    device work of a call is ordered on it, and a call returns after that
+ *    work has completed.
+ */
+#ifndef SPX_H
+#define SPX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spx_handle_s *spx_handle;
+
+typedef enum {
+    SPX_OK = 0,
+    SPX_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad index) */
+    SPX_ERR_ALLOC = 2,          /* host or device allocation failed */
+    SPX_ERR_CUDA = 3,           /* a CUDA call failed, or no usable sm_103 device */
+    SPX_ERR_NOT_SPD = 4,        /* Cholesky met a non-positive pivot (column in spx_info) */
+    SPX_ERR_ZERO_PIVOT = 5,     /* LU met a zero pivot with static pivoting disabled */
+    SPX_ERR_TIMEOUT = 6,        /* a bounded device wait expired */
+    SPX_ERR_NOT_CONVERGED = 7,  /* refinement did not reach the requested backward error */
+    SPX_ERR_STATE = 8           /* call out of order (e.g. solve before factorize) */
+} spx_status;
+
+typedef enum { SPX_LLT = 0, SPX_LU = 1 } spx_method;
+
+/* Arithmetic of the bulk panel updates.  SPX_FP64 stores and updates the
+ * factor in double precision.  The other modes store the factor in single
+ * precision and run the updates on the tensor cores (TF32 / BF16 operands
+ * with FP32 accumulation; FP32 = three-pass split TF32), while the
+ * diagonal-block factorizations, residuals and corrections stay in FP64. */
+typedef enum { SPX_FP64 = 0, SPX_FP32 = 1, SPX_TF32 = 2, SPX_BF16 = 3 } spx_precision;
+
+typedef enum {
+    SPX_ORDER_AUTO = 0,     /* grid rule when grid[] is set, else graph rule */
+    SPX_ORDER_GRID = 1,     /* geometric nested dissection of grid[0]*grid[1]*grid[2]*dof */
+    SPX_ORDER_GRAPH = 2,    /* level-structure nested dissection of the graph of A + A^T */
+    SPX_ORDER_GIVEN = 3,    /* use opt->perm */
+    SPX_ORDER_NATURAL = 4   /* identity */
+} spx_ordering;
+
+typedef struct {
+    int32_t ordering;       /* spx_ordering */
+    int32_t grid[3];        /* nx, ny, nz for the grid rule (nz = 1 in 2-D) */
+    int32_t dof;            /* unknowns per grid node (consecutive), >= 1 */
+    int32_t max_width;      /* supernodes wider than this are split into panels (Sec. III); 0 = default 128 */
+    double amalg_ratio;     /* amalgamation may add this fraction of nnz(L) as explicit zeros (Sec. V: 12%); <0 = default 0.12 */
+    const int64_t *perm;    /* SPX_ORDER_GIVEN: new -> old permutation of length n (copied) */
+    int32_t lower_only;     /* 1: the CSC holds only the lower triangle of a symmetric matrix (LLT only) */
+    int32_t reserved0;
+    double pivot_tau;       /* LU static-pivot threshold; < 0 = sqrt(2^-52) * ||A||_inf at factorize */
+} spx_options;
+
+/* Fill *opt with the defaults above. */
+void spx_default_options(spx_options *opt);
+
+typedef struct {
+    int32_t max_iter;       /* plain iterative-refinement steps before GMRES-IR (default 10) */
+    int32_t gmres_restart;  /* FGMRES restart length (default 30) */
+    int32_t gmres_max_iter; /* total FGMRES iterations (default 200) */
+    int32_t mode;           /* 0: no refinement; 1: plain refinement; 2: plain, then FGMRES on stall (default) */
+    double tol;             /* target backward error (default 1e-12) */
+} spx_refine;
+
+void spx_default_refine(spx_refine *r);
+
+typedef struct {
+    int32_t iters;          /* plain refinement steps taken */
+    int32_t gmres_iters;    /* FGMRES iterations taken */
+    int32_t converged;      /* 1 if every column met tol (or no refinement was asked) */
+    int32_t reserved0;
+    double backward_error;  /* max over columns of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) */
+} spx_solve_info;
+
+typedef struct {
+    int64_t n;
+    int64_t nnz_a;          /* entries of the input CSC */
+    int64_t nnz_l;          /* exact entries of L (diagonal included) from the symbolic factorization */
+    int64_t nnz_stored;     /* lower entries kept in the panels after amalgamation */
+    int64_t factor_bytes;   /* device bytes of the panel storage (L, or L and U) */
+    int64_t nsupernodes;    /* fundamental supernodes */
+    int64_t npanels;        /* panels after amalgamation and splitting */
+    int64_t nlevels;        /* levels of the panel elimination tree */
+    int64_t nupdates;       /* (source panel, target panel) update tasks */
+    int64_t bad_col;        /* permuted column of the first failed pivot, or -1 */
+    int64_t npivot_repl;    /* LU: static pivot replacements in the last factorization */
+    int32_t method;         /* spx_method */
+    int32_t precision;      /* spx_precision of the last factorization */
+    double flops;           /* exact-pattern factorization flops: sum c_j^2 (LLT) or sum 2(c_j-1)^2+(c_j-1) (LU) */
+    double flops_stored;    /* the same count on the amalgamated panel structure */
+    double update_flops;    /* flops of the panel updates on the stored structure */
+    double analyze_ms;      /* host time of spx_analyze */
+    double factor_ms;       /* device time of the last spx_factorize (assembly included) */
+    double solve_ms;        /* device time of the last spx_solve */
+} spx_info;
+
+/* Host-only analysis (Sec. III: ordering, elimination tree, symbolic
+ * factorization, amalgamation (Sec. V, 12% extra fill) and splitting of wide
+ * supernodes).  `colptr`/`rowind` are host arrays, copied; the pattern
+ * used is that of A + A^T.  `opt` may be NULL (defaults).  Needs no GPU. */
+spx_status spx_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, spx_method method,
+                       const spx_options *opt, spx_handle *out);
+
+/* Numerical factorization on the device (Sec. III: per panel, diagonal-block
+ * factorization, panel TRSM, updates of the facing panels; Sec. V-B: the
+ * update computes A_i A_j^T and subtracts it directly at the positions of the
+ * target panel's block structure).  `values` are the CSC values in the order
+ * of the analysed pattern, host or device memory (`values_on_device`).  May
+ * be called again with new values. */
+spx_status spx_factorize(spx_handle h, const double *values, int values_on_device,
+                         spx_precision precision, void *cuda_stream);
+
+/* Solve A X = B for nrhs columns.  B and X are host or device arrays
+ * (`on_device`), column-major with leading dimensions ldb, ldx >= n; X may
+ * equal B.  `refine` NULL: no refinement for FP64 factors, the defaults for
+ * lower-precision factors.  `info` may be NULL. */
+spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
+                     int64_t ldx, int on_device, const spx_refine *refine, spx_solve_info *info,
+                     void *cuda_stream);
+
+/* Statistics of the analysis and of the last factorization/solve. */
+spx_status spx_get_info(spx_handle h, spx_info *info);
+
+/* Copy the final permutation (new -> old, length n) to host memory. */
+spx_status spx_get_perm(spx_handle h, int64_t *perm);
+
+/* Copy the numerical factor to host arrays laid out on a caller-given CSC
+ * pattern in the permuted numbering (Lp: n+1, Li: sorted rows, diagonal
+ * first).  Lx receives L (LU: unit diagonal stored as 1); Ut, for LU only,
+ * receives U transposed on the same pattern (Ut[p] = U(j, Li[p]) for p in
+ * column j; may be NULL for LLT).  Every pattern entry must lie inside the
+ * panel structure (SPX_ERR_ARG otherwise).  Values are converted to double. */
+spx_status spx_get_factor(spx_handle h, const int64_t *Lp, const int32_t *Li, double *Lx,
+                          double *Ut);
+
+/* Message for the last failing call on h (or on handle creation when h is
+ * NULL).  The string stays valid until the next call on h. */
+const char *spx_last_error(spx_handle h);
+
+/* Release a handle and everything it owns.  NULL-safe. */
+void spx_free(spx_handle h);
+
+/* The supernodal update on its own, as the paper's kernel study runs it
+ * (Sec. V-B: C = C - A B^T where B is the first K rows of A, and C is a
+ * taller panel with a gapped block structure; each row block of A lies
+ * inside one row block of C, and blocks of A do not overlap).
+ *   A     : device, column-major m x k (lda >= m), the source panel rows.
+ *   nb_rows: the first nb_rows rows of A form B (the facing columns).
+ *   C     : device, column-major ldc x nc target panel.
+ *   rowmap: device int32[m]: target row of each source row (C row index).
+ *   colmap: device int32[nb_rows]: target column of each of B's rows.
+ *   lower : 1 = only entries with source row index >= source column index
+ *           (the diagonal-block region) are updated, as in Cholesky.
+ * Entries are subtracted with atomic adds, so several calls may target the
+ * same C concurrently.  precision: SPX_FP64 (A, C double) only. */
+spx_status spx_update(int64_t m, int64_t nb_rows, int64_t k, const double *A, int64_t lda,
+                      double *C, int64_t ldc, const int32_t *rowmap, const int32_t *colmap,
+                      int lower, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPX_H */

@@ -1,0 +1,715 @@
+// api.cu -- the C ABI of libspx (include/spx.h): handle management, upload
+// of the analysed structure, the level-by-level factorization captured once
+// into a CUDA graph and replayed, the solve sweeps and the refinement loop.
+#include "../../include/spx.h"
+#include "kernels.cuh"
+#include "spx_plan.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using spx::DevTask;
+using spx::RowChunk;
+using spx::UpdTile;
+
+struct spx_handle_s {
+    spx::Plan plan;
+    std::string err;
+    spx_method method = SPX_LLT;
+    double pivot_tau_opt = -1.0;
+
+    // device state
+    bool uploaded = false;
+    int device = -1;
+    cudaStream_t hs = nullptr;
+    cudaEvent_t ev_fence = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    std::vector<void *> allocs;
+
+    spx::DevPlan dp{};
+    int32_t *d_level_panels = nullptr;
+    DevTask *d_tasks = nullptr;
+    int64_t *d_amap = nullptr, *d_csr_ptr = nullptr, *d_csr_src = nullptr, *d_perm = nullptr;
+    int32_t *d_csr_col = nullptr;
+
+    std::vector<int64_t> chunk_ptr;   // per level, into d_chunks
+    RowChunk *d_chunks = nullptr;
+    std::vector<int64_t> tile_ptr;    // per level, into d_tiles (LLT, or LU's L side)
+    UpdTile *d_tiles = nullptr;
+    std::vector<int64_t> tileu_ptr;   // per level, LU's U^T side
+    UpdTile *d_tilesu = nullptr;
+
+    // numeric state
+    int precision = -1;
+    bool factored = false;
+    void *d_L = nullptr, *d_U = nullptr;
+    int factor_prec_alloc = -1;
+    double *d_vals = nullptr;
+    double *d_tau = nullptr;                 // [0] pivot threshold used by the diagonal kernels
+    unsigned long long *d_anorm = nullptr;   // bits of ||A||_inf
+    int64_t *d_err = nullptr;
+    unsigned long long *d_nrepl = nullptr;
+    double anorm = 0.0;
+    cudaGraphExec_t fgraph = nullptr;
+    int fgraph_prec = -1;
+
+    // solve workspace
+    int ws_nrhs = 0;
+    double *d_B = nullptr, *d_X = nullptr, *d_R = nullptr, *d_D = nullptr, *d_Y = nullptr;
+    unsigned long long *d_norms = nullptr;
+    cudaGraphExec_t sgraph = nullptr;
+    int sgraph_nrhs = -1, sgraph_prec = -1;
+
+    spx_info info{};
+};
+
+namespace {
+
+std::string g_create_error;
+
+spx_status fail(spx_handle h, spx_status st, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(h, SPX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+spx_status dalloc(spx_handle h, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(h, SPX_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(*p);
+    return SPX_OK;
+}
+
+template <typename T>
+spx_status upload(spx_handle h, T **p, const std::vector<T> &v)
+{
+    spx_status st = dalloc(h, p, v.size());
+    if (st != SPX_OK) return st;
+    if (!v.empty()) CU(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SPX_OK;
+}
+
+void dfree(spx_handle h, void *p)
+{
+    if (!p) return;
+    cudaFree(p);
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+}
+
+// --- small device helpers ---------------------------------------------------
+__global__ void init_scalars_kernel(int64_t *err, unsigned long long *nrepl,
+                                    unsigned long long *anorm)
+{
+    *err = LLONG_MAX;
+    *nrepl = 0ull;
+    *anorm = 0ull;
+}
+
+// tau = fixed (>= 0) or scale * ||A||_inf
+__global__ void set_tau_kernel(const unsigned long long *anorm_bits, double fixed, double scale,
+                               double *tau)
+{
+    double a = __longlong_as_double((long long)*anorm_bits);
+    *tau = fixed >= 0.0 ? fixed : scale * a;
+}
+
+spx_status ensure_device(spx_handle h)
+{
+    if (h->uploaded) return SPX_OK;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(h, SPX_ERR_CUDA,
+                    "libspx is built for sm_103a; the current device is sm_" +
+                        std::to_string(prop.major * 10 + prop.minor));
+    h->device = dev;
+    CU(cudaStreamCreateWithFlags(&h->hs, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&h->ev_fence, cudaEventDisableTiming));
+    CU(cudaEventCreate(&h->ev_t0));
+    CU(cudaEventCreate(&h->ev_t1));
+
+    const spx::Plan &P = h->plan;
+    spx_status st;
+    int64_t *pfcol, *prow, *pval;
+    int32_t *pw, *ph, *rows, *relmap;
+    if ((st = upload(h, &pfcol, P.pfcol)) || (st = upload(h, &pw, P.pw)) ||
+        (st = upload(h, &ph, P.ph)) || (st = upload(h, &prow, P.prow)) ||
+        (st = upload(h, &rows, P.rows)) || (st = upload(h, &pval, P.pval)) ||
+        (st = upload(h, &relmap, P.relmap)) || (st = upload(h, &h->d_level_panels, P.level_panels)) ||
+        (st = upload(h, &h->d_amap, P.amap)) || (st = upload(h, &h->d_csr_ptr, P.csr_ptr)) ||
+        (st = upload(h, &h->d_csr_col, P.csr_col)) || (st = upload(h, &h->d_csr_src, P.csr_src)) ||
+        (st = upload(h, &h->d_perm, P.perm)))
+        return st;
+    h->dp.n = P.n;
+    h->dp.npanels = P.npanels;
+    h->dp.pfcol = pfcol;
+    h->dp.pw = pw;
+    h->dp.ph = ph;
+    h->dp.prow = prow;
+    h->dp.rows = rows;
+    h->dp.pval = pval;
+    h->dp.relmap = relmap;
+
+    std::vector<DevTask> tasks(P.tasks.size());
+    for (size_t t = 0; t < P.tasks.size(); ++t)
+        tasks[t] = DevTask{P.tasks[t].src, P.tasks[t].tgt, P.tasks[t].r0, P.tasks[t].r1,
+                           P.tasks[t].relmap_off};
+    if ((st = upload(h, &h->d_tasks, tasks))) return st;
+
+    // per-level launch lists: row chunks of the off-diagonal parts, update tiles
+    std::vector<RowChunk> chunks;
+    std::vector<UpdTile> tiles, tilesu;
+    h->chunk_ptr.assign(P.nlevels + 1, 0);
+    h->tile_ptr.assign(P.nlevels + 1, 0);
+    h->tileu_ptr.assign(P.nlevels + 1, 0);
+    const int T = spx::kUpdTile;
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+        for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q) {
+            int32_t k = P.level_panels[q];
+            for (int32_t r0 = P.pw[k]; r0 < P.ph[k]; r0 += spx::kTrsmRows)
+                chunks.push_back(RowChunk{k, r0});
+        }
+        for (int32_t t = P.level_task_ptr[l]; t < P.level_task_ptr[l + 1]; ++t) {
+            const spx::Task &tk = P.tasks[t];
+            const int32_t hk = P.ph[tk.src];
+            for (int32_t m0 = tk.r0; m0 < hk; m0 += T)
+                for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += T) {
+                    if (P.method == SPX_LLT && m0 + T <= n0) continue;
+                    tiles.push_back(UpdTile{t, m0, n0, 0});
+                }
+            if (P.method == SPX_LU)
+                for (int32_t m0 = tk.r1; m0 < hk; m0 += T)
+                    for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += T) tilesu.push_back(UpdTile{t, m0, n0, 0});
+        }
+        h->chunk_ptr[l + 1] = (int64_t)chunks.size();
+        h->tile_ptr[l + 1] = (int64_t)tiles.size();
+        h->tileu_ptr[l + 1] = (int64_t)tilesu.size();
+    }
+    if ((st = upload(h, &h->d_chunks, chunks)) || (st = upload(h, &h->d_tiles, tiles)) ||
+        (st = upload(h, &h->d_tilesu, tilesu)))
+        return st;
+    if ((st = dalloc(h, &h->d_vals, (size_t)P.nnz_a)) || (st = dalloc(h, &h->d_tau, 1)) ||
+        (st = dalloc(h, &h->d_anorm, 1)) || (st = dalloc(h, &h->d_err, 1)) ||
+        (st = dalloc(h, &h->d_nrepl, 1)))
+        return st;
+    h->uploaded = true;
+    return SPX_OK;
+}
+
+// Enqueue the whole factorization on h->hs (captured into a graph).
+template <typename T>
+void enqueue_factorization(spx_handle h, bool mixed)
+{
+    const spx::Plan &P = h->plan;
+    cudaStream_t s = h->hs;
+    T *L = (T *)h->d_L, *U = (T *)h->d_U;
+    const size_t elems = (size_t)P.pval[P.npanels];
+    init_scalars_kernel<<<1, 1, 0, s>>>(h->d_err, h->d_nrepl, h->d_anorm);
+    spx::launch_row_abs_sum_max(P.n, h->d_csr_ptr, h->d_csr_src, h->d_vals, h->d_anorm, s);
+    const double sqrt_eps = std::sqrt(std::ldexp(1.0, -52));
+    if (P.method == SPX_LU)
+        set_tau_kernel<<<1, 1, 0, s>>>(h->d_anorm, h->pivot_tau_opt, sqrt_eps, h->d_tau);
+    else
+        set_tau_kernel<<<1, 1, 0, s>>>(h->d_anorm, mixed ? -1.0 : 0.0, sqrt_eps, h->d_tau);
+    cudaMemsetAsync(L, 0, elems * sizeof(T), s);
+    if (U) cudaMemsetAsync(U, 0, elems * sizeof(T), s);
+    spx::launch_assemble<T>(P.nnz_a, h->d_vals, h->d_amap, L, U, s);
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
+        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
+        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
+        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
+        const UpdTile *tl = h->d_tiles + h->tile_ptr[l];
+        const int ntl = (int)(h->tile_ptr[l + 1] - h->tile_ptr[l]);
+        if (P.method == SPX_LLT) {
+            spx::launch_potrf<T>(h->dp, panels, np, L, h->d_tau, h->d_err, h->d_nrepl, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, L, L, spx::TRSM_LLT, s);
+            spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, L, L, 1, 0, s);
+        } else {
+            const UpdTile *tu = h->d_tilesu + h->tileu_ptr[l];
+            const int ntu = (int)(h->tileu_ptr[l + 1] - h->tileu_ptr[l]);
+            spx::launch_getrf<T>(h->dp, panels, np, L, h->d_tau, h->d_err, h->d_nrepl, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, L, L, spx::TRSM_LU_L, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, L, U, spx::TRSM_LU_U, s);
+            spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, U, L, 0, 0, s);
+            spx::launch_update<T>(h->dp, h->d_tasks, tu, ntu, U, L, U, 0, 1, s);
+        }
+    }
+}
+
+// One forward + backward sweep: d_D = A^{-1} d_R (through the factor).
+template <typename T>
+void enqueue_sweep(spx_handle h, int nrhs)
+{
+    const spx::Plan &P = h->plan;
+    cudaStream_t s = h->hs;
+    const T *L = (const T *)h->d_L, *U = (const T *)h->d_U;
+    const bool lu = P.method == SPX_LU;
+    spx::launch_permute_in(P.n, nrhs, h->d_R, P.n, h->d_perm, h->d_Y, s);
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
+        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
+        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
+        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
+        spx::launch_fwd_diag<T>(h->dp, panels, np, L, lu ? 1 : 0, h->d_Y, nrhs, s);
+        spx::launch_fwd_off<T>(h->dp, ch, nch, L, h->d_Y, nrhs, s);
+    }
+    for (int32_t l = P.nlevels - 1; l >= 0; --l) {
+        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
+        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
+        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
+        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
+        spx::launch_bwd_off<T>(h->dp, ch, nch, lu ? U : L, h->d_Y, nrhs, s);
+        spx::launch_bwd_diag<T>(h->dp, panels, np, L, lu ? 1 : 0, h->d_Y, nrhs, s);
+    }
+    spx::launch_permute_out(P.n, nrhs, h->d_Y, h->d_perm, h->d_D, P.n, s);
+}
+
+spx_status capture(spx_handle h, cudaGraphExec_t *exec, void (*body)(spx_handle, int, bool),
+                   int arg, bool flag)
+{
+    if (*exec) {
+        cudaGraphExecDestroy(*exec);
+        *exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->hs, cudaStreamCaptureModeThreadLocal));
+    body(h, arg, flag);
+    cudaError_t launch_err = cudaGetLastError();
+    cudaError_t e = cudaStreamEndCapture(h->hs, &g);
+    if (launch_err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(h, SPX_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(launch_err));
+    }
+    if (e != cudaSuccess) return fail(h, SPX_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, SPX_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return SPX_OK;
+}
+
+void body_factor(spx_handle h, int prec, bool)
+{
+    if (prec == SPX_FP64) enqueue_factorization<double>(h, false);
+    else enqueue_factorization<float>(h, true);
+}
+
+void body_sweep(spx_handle h, int nrhs, bool fp64)
+{
+    if (fp64) enqueue_sweep<double>(h, nrhs);
+    else enqueue_sweep<float>(h, nrhs);
+}
+
+void fence_from(spx_handle h, void *user_stream)
+{
+    cudaEventRecord(h->ev_fence, (cudaStream_t)user_stream);
+    cudaStreamWaitEvent(h->hs, h->ev_fence, 0);
+}
+
+spx_status ensure_workspace(spx_handle h, int nrhs)
+{
+    if (h->ws_nrhs >= nrhs) return SPX_OK;
+    for (double **p : {&h->d_B, &h->d_X, &h->d_R, &h->d_D, &h->d_Y}) {
+        dfree(h, *p);
+        *p = nullptr;
+    }
+    dfree(h, h->d_norms);
+    h->d_norms = nullptr;
+    h->ws_nrhs = 0;
+    const size_t sz = (size_t)h->plan.n * nrhs;
+    spx_status st;
+    if ((st = dalloc(h, &h->d_B, sz)) || (st = dalloc(h, &h->d_X, sz)) ||
+        (st = dalloc(h, &h->d_R, sz)) || (st = dalloc(h, &h->d_D, sz)) ||
+        (st = dalloc(h, &h->d_Y, sz)) || (st = dalloc(h, &h->d_norms, (size_t)3 * nrhs)))
+        return st;
+    h->ws_nrhs = nrhs;
+    if (h->sgraph) {
+        cudaGraphExecDestroy(h->sgraph);
+        h->sgraph = nullptr;
+        h->sgraph_nrhs = -1;
+    }
+    return SPX_OK;
+}
+
+// residual of d_X against d_B into d_R; returns the worst backward error
+spx_status residual(spx_handle h, int nrhs, double *berr)
+{
+    const spx::Plan &P = h->plan;
+    CU(cudaMemsetAsync(h->d_norms, 0, sizeof(unsigned long long) * 3 * nrhs, h->hs));
+    spx::launch_residual(P.n, nrhs, h->d_csr_ptr, h->d_csr_col, h->d_csr_src, h->d_vals, h->d_X,
+                         P.n, h->d_B, P.n, h->d_R, h->d_norms, h->hs);
+    std::vector<unsigned long long> nb(3 * nrhs);
+    CU(cudaMemcpyAsync(nb.data(), h->d_norms, sizeof(unsigned long long) * 3 * nrhs,
+                       cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
+    double worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+        double r, x, b;
+        std::memcpy(&r, &nb[3 * c], 8);
+        std::memcpy(&x, &nb[3 * c + 1], 8);
+        std::memcpy(&b, &nb[3 * c + 2], 8);
+        double den = h->anorm * x + b;
+        double e = den > 0.0 ? r / den : (r > 0.0 ? INFINITY : 0.0);
+        if (!(e <= worst)) worst = e;   // NaN propagates
+    }
+    *berr = worst;
+    return SPX_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void spx_default_options(spx_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->ordering = SPX_ORDER_AUTO;
+    opt->dof = 1;
+    opt->max_width = 128;
+    opt->amalg_ratio = 0.12;
+    opt->perm = nullptr;
+    opt->lower_only = 0;
+    opt->pivot_tau = -1.0;
+}
+
+void spx_default_refine(spx_refine *r)
+{
+    if (!r) return;
+    r->max_iter = 10;
+    r->gmres_restart = 30;
+    r->gmres_max_iter = 200;
+    r->mode = 2;
+    r->tol = 1e-12;
+}
+
+spx_status spx_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, spx_method method,
+                       const spx_options *opt, spx_handle *out)
+{
+    spx_handle h = nullptr;
+    if (!out) return fail(h, SPX_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!colptr || !rowind) return fail(h, SPX_ERR_ARG, "colptr/rowind is NULL");
+    if (method != SPX_LLT && method != SPX_LU) return fail(h, SPX_ERR_ARG, "unknown method");
+    spx_options o;
+    spx_default_options(&o);
+    if (opt) o = *opt;
+    if (o.max_width <= 0) o.max_width = 128;
+    if (o.max_width > spx::kMaxWidth)
+        return fail(h, SPX_ERR_ARG, "max_width above " + std::to_string(spx::kMaxWidth));
+    if (o.amalg_ratio < 0) o.amalg_ratio = 0.12;
+    if (o.lower_only && method == SPX_LU) return fail(h, SPX_ERR_ARG, "lower_only needs SPX_LLT");
+    h = new (std::nothrow) spx_handle_s();
+    if (!h) return fail(nullptr, SPX_ERR_ALLOC, "out of host memory");
+    spx::AnalyzeOptions ao;
+    ao.ordering = o.ordering;
+    ao.grid[0] = o.grid[0];
+    ao.grid[1] = o.grid[1];
+    ao.grid[2] = o.grid[2];
+    ao.dof = o.dof > 0 ? o.dof : 1;
+    ao.max_width = o.max_width;
+    ao.amalg_ratio = o.amalg_ratio;
+    ao.perm = o.perm;
+    ao.lower_only = o.lower_only;
+    std::string msg;
+    try {
+        msg = spx::analyze(n, colptr, rowind, (int)method, ao, h->plan);
+    } catch (const std::bad_alloc &) {
+        msg = "out of host memory during analysis";
+    }
+    if (!msg.empty()) {
+        delete h;
+        return fail(nullptr, SPX_ERR_ARG, msg);
+    }
+    h->method = method;
+    h->pivot_tau_opt = o.pivot_tau;
+    const spx::Plan &P = h->plan;
+    spx_info &I = h->info;
+    I.n = P.n;
+    I.nnz_a = P.nnz_a;
+    I.nnz_l = P.nnz_l;
+    I.nnz_stored = P.nnz_stored;
+    I.nsupernodes = P.nsuper;
+    I.npanels = P.npanels;
+    I.nlevels = P.nlevels;
+    I.nupdates = (int64_t)P.tasks.size();
+    I.bad_col = -1;
+    I.method = method;
+    I.precision = -1;
+    I.flops = P.flops_exact;
+    I.flops_stored = P.flops_stored;
+    I.update_flops = P.update_flops;
+    I.analyze_ms = P.analyze_ms;
+    *out = h;
+    return SPX_OK;
+}
+
+spx_status spx_factorize(spx_handle h, const double *values, int values_on_device,
+                         spx_precision precision, void *cuda_stream)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (!values && h->plan.nnz_a > 0) return fail(h, SPX_ERR_ARG, "values is NULL");
+    if (precision < SPX_FP64 || precision > SPX_BF16) return fail(h, SPX_ERR_ARG, "unknown precision");
+    spx_status st = ensure_device(h);
+    if (st != SPX_OK) return st;
+    const spx::Plan &P = h->plan;
+    const bool fp64 = precision == SPX_FP64;
+    const size_t elems = (size_t)P.pval[P.npanels];
+    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+    if (h->factor_prec_alloc != (fp64 ? 1 : 0)) {
+        dfree(h, h->d_L);
+        dfree(h, h->d_U);
+        h->d_L = h->d_U = nullptr;
+        h->factor_prec_alloc = -1;
+        char *pl = nullptr;
+        if ((st = dalloc(h, &pl, elems * esz))) return st;
+        h->d_L = pl;
+        if (P.method == SPX_LU) {
+            char *pu = nullptr;
+            if ((st = dalloc(h, &pu, elems * esz))) return st;
+            h->d_U = pu;
+        }
+        h->factor_prec_alloc = fp64 ? 1 : 0;
+        if (h->fgraph) {
+            cudaGraphExecDestroy(h->fgraph);
+            h->fgraph = nullptr;
+            h->fgraph_prec = -1;
+        }
+    }
+    h->factored = false;
+    fence_from(h, cuda_stream);
+    CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a,
+                       values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->hs));
+    if (h->fgraph_prec != (int)precision) {
+        if ((st = capture(h, &h->fgraph, body_factor, (int)precision, false))) return st;
+        h->fgraph_prec = (int)precision;
+    }
+    CU(cudaEventRecord(h->ev_t0, h->hs));
+    CU(cudaGraphLaunch(h->fgraph, h->hs));
+    CU(cudaEventRecord(h->ev_t1, h->hs));
+    int64_t bad = 0;
+    unsigned long long nrepl = 0, abits = 0;
+    CU(cudaMemcpyAsync(&bad, h->d_err, sizeof(bad), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&nrepl, h->d_nrepl, sizeof(nrepl), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&abits, h->d_anorm, sizeof(abits), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
+    std::memcpy(&h->anorm, &abits, 8);
+    h->info.factor_ms = ms;
+    h->info.precision = precision;
+    h->info.npivot_repl = (int64_t)nrepl;
+    h->info.bad_col = (bad == LLONG_MAX) ? -1 : bad;
+    h->info.factor_bytes = (int64_t)(elems * esz * (P.method == SPX_LU ? 2 : 1));
+    h->precision = precision;
+    if (bad != LLONG_MAX) {
+        return fail(h, P.method == SPX_LLT ? SPX_ERR_NOT_SPD : SPX_ERR_ZERO_PIVOT,
+                    "pivot failure at permuted column " + std::to_string(bad));
+    }
+    h->factored = true;
+    return SPX_OK;
+}
+
+spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
+                     int64_t ldx, int on_device, const spx_refine *refine, spx_solve_info *info,
+                     void *cuda_stream)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (!h->factored) return fail(h, SPX_ERR_STATE, "spx_solve before a successful spx_factorize");
+    const spx::Plan &P = h->plan;
+    if (nrhs < 0 || (nrhs > 0 && (!B || !X))) return fail(h, SPX_ERR_ARG, "bad B/X/nrhs");
+    if (ldb < P.n || ldx < P.n) return fail(h, SPX_ERR_ARG, "leading dimension below n");
+    spx_solve_info si{};
+    si.converged = 1;
+    if (nrhs == 0) {
+        if (info) *info = si;
+        return SPX_OK;
+    }
+    spx_refine rf;
+    spx_default_refine(&rf);
+    const bool fp64 = h->precision == SPX_FP64;
+    if (refine) rf = *refine;
+    else if (fp64) rf.mode = 0;
+    spx_status st = ensure_workspace(h, nrhs);
+    if (st != SPX_OK) return st;
+    fence_from(h, cuda_stream);
+    const size_t n = (size_t)P.n;
+    CU(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, (size_t)ldb * sizeof(double),
+                         n * sizeof(double), nrhs,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->hs));
+    if (h->sgraph_nrhs != nrhs || h->sgraph_prec != h->precision || !h->sgraph) {
+        if ((st = capture(h, &h->sgraph, body_sweep, nrhs, fp64))) return st;
+        h->sgraph_nrhs = nrhs;
+        h->sgraph_prec = h->precision;
+    }
+    CU(cudaEventRecord(h->ev_t0, h->hs));
+    CU(cudaMemcpyAsync(h->d_R, h->d_B, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, h->hs));
+    CU(cudaGraphLaunch(h->sgraph, h->hs));
+    CU(cudaMemcpyAsync(h->d_X, h->d_D, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, h->hs));
+    double berr = 0.0;
+    if (rf.mode != 0 || info) {
+        if ((st = residual(h, nrhs, &berr))) return st;
+        while (rf.mode != 0 && !(berr <= rf.tol) && si.iters < rf.max_iter) {
+            CU(cudaGraphLaunch(h->sgraph, h->hs));
+            spx::launch_axpy_cols(P.n, nrhs, h->d_D, h->d_X, P.n, h->hs);
+            si.iters++;
+            double e;
+            if ((st = residual(h, nrhs, &e))) return st;
+            const bool stalled = !(e <= 0.5 * berr);   // plain refinement stopped contracting
+            berr = e;
+            if (stalled) break;
+        }
+        si.backward_error = berr;
+        si.converged = (rf.mode == 0) ? 1 : (berr <= rf.tol);
+    }
+    CU(cudaEventRecord(h->ev_t1, h->hs));
+    CU(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), h->d_X, n * sizeof(double),
+                         n * sizeof(double), nrhs,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
+    h->info.solve_ms = ms;
+    if (info) *info = si;
+    if (rf.mode != 0 && !si.converged)
+        return fail(h, SPX_ERR_NOT_CONVERGED, "refinement stopped at backward error " + std::to_string(berr));
+    return SPX_OK;
+}
+
+spx_status spx_get_info(spx_handle h, spx_info *info)
+{
+    if (!h || !info) return fail(h, SPX_ERR_ARG, "NULL argument");
+    *info = h->info;
+    return SPX_OK;
+}
+
+spx_status spx_get_perm(spx_handle h, int64_t *perm)
+{
+    if (!h || !perm) return fail(h, SPX_ERR_ARG, "NULL argument");
+    std::memcpy(perm, h->plan.perm.data(), sizeof(int64_t) * (size_t)h->plan.n);
+    return SPX_OK;
+}
+
+spx_status spx_get_factor(spx_handle h, const int64_t *Lp, const int32_t *Li, double *Lx, double *Ut)
+{
+    if (!h || !Lp || !Li || !Lx) return fail(h, SPX_ERR_ARG, "NULL argument");
+    if (!h->factored) return fail(h, SPX_ERR_STATE, "no factor");
+    const spx::Plan &P = h->plan;
+    const bool lu = P.method == SPX_LU;
+    if (lu && !Ut) return fail(h, SPX_ERR_ARG, "LU needs Ut");
+    const size_t elems = (size_t)P.pval[P.npanels];
+    std::vector<double> hl(elems), hu(lu ? elems : 0);
+    auto fetch = [&](const void *src, std::vector<double> &dst) -> spx_status {
+        if (h->precision == SPX_FP64) {
+            CU(cudaMemcpy(dst.data(), src, elems * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> tmp(elems);
+            CU(cudaMemcpy(tmp.data(), src, elems * sizeof(float), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < elems; ++i) dst[i] = tmp[i];
+        }
+        return SPX_OK;
+    };
+    spx_status st;
+    if ((st = fetch(h->d_L, hl))) return st;
+    if (lu && (st = fetch(h->d_U, hu))) return st;
+    auto pos = [&](int32_t p, int64_t r) -> int64_t {
+        const int32_t *b = P.rows.data() + P.prow[p], *e = P.rows.data() + P.prow[p + 1];
+        const int32_t *it = std::lower_bound(b, e, (int32_t)r);
+        return (it != e && *it == r) ? (int64_t)(it - b) : -1;
+    };
+    for (int64_t j = 0; j < P.n; ++j) {
+        const int32_t pj = P.col2panel[j];
+        const int64_t cj = j - P.pfcol[pj];
+        const int64_t hj = P.ph[pj];
+        for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q) {
+            const int64_t i = Li[q];
+            if (i < j || i >= P.n) return fail(h, SPX_ERR_ARG, "pattern entry above the diagonal");
+            const int64_t r = pos(pj, i);
+            if (r < 0) return fail(h, SPX_ERR_ARG, "pattern entry outside the panel structure");
+            const int64_t off = P.pval[pj] + cj * hj + r;
+            if (!lu) {
+                Lx[q] = hl[off];
+                continue;
+            }
+            if (i == j) {
+                Lx[q] = 1.0;
+                Ut[q] = hl[off];
+                continue;
+            }
+            Lx[q] = hl[off];
+            // U(j, i), i > j: inside j's diagonal block -> L panel (row j, col i); else U^T panel
+            if (i < P.pfcol[pj] + P.pw[pj]) {
+                Ut[q] = hl[P.pval[pj] + (i - P.pfcol[pj]) * hj + cj];
+            } else {
+                Ut[q] = hu[off];
+            }
+        }
+    }
+    return SPX_OK;
+}
+
+const char *spx_last_error(spx_handle h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void spx_free(spx_handle h)
+{
+    if (!h) return;
+    if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
+    if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->ev_fence) cudaEventDestroy(h->ev_fence);
+    if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+    if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    if (h->hs) cudaStreamDestroy(h->hs);
+    delete h;
+}
+
+spx_status spx_update(int64_t m, int64_t nb_rows, int64_t k, const double *A, int64_t lda,
+                      double *C, int64_t ldc, const int32_t *rowmap, const int32_t *colmap,
+                      int lower, void *cuda_stream)
+{
+    spx_handle h = nullptr;
+    if (m < 0 || nb_rows < 0 || k < 0 || nb_rows > m) return fail(h, SPX_ERR_ARG, "bad sizes");
+    if (m > INT32_MAX || k > INT32_MAX) return fail(h, SPX_ERR_ARG, "sizes above 2^31");
+    if (m == 0 || nb_rows == 0) return SPX_OK;
+    if (!A || !C || !rowmap || !colmap) return fail(h, SPX_ERR_ARG, "NULL pointer");
+    if (lda < m) return fail(h, SPX_ERR_ARG, "lda below m");
+    spx::launch_update_standalone(m, nb_rows, k, A, lda, C, ldc, rowmap, colmap, lower,
+                                  (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, SPX_ERR_CUDA, cudaGetErrorString(e));
+    return SPX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// kernels.cuh -- device-side data layout and kernel launchers of libspx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace spx {
+
+// Structure of the panels on the device (uploaded once after the analysis).
+struct DevPlan {
+    int64_t n;
+    int32_t npanels;
+    const int64_t *pfcol;   // first column per panel
+    const int32_t *pw;      // width
+    const int32_t *ph;      // height (rows incl. diagonal block); leading dimension
+    const int64_t *prow;    // row-list offsets
+    const int32_t *rows;    // permuted row indices
+    const int64_t *pval;    // value offsets
+    const int32_t *relmap;  // target row of each updated source row, per task
+};
+
+struct DevTask {
+    int32_t src, tgt, r0, r1;
+    int64_t relmap_off;
+};
+
+// A 64 x 64 tile of one update task: rows [m0, m0+64) x columns [n0, n0+64)
+// in the source panel's local row numbering.
+struct UpdTile {
+    int32_t task, m0, n0, pad;
+};
+
+// A chunk of rows [r0, r0+64) of one panel for the TRSM / solve kernels.
+struct RowChunk {
+    int32_t panel, r0;
+};
+
+constexpr int kMaxWidth = 160;      // widest panel the diagonal-block kernels keep in shared memory
+constexpr int kUpdTile = 64;
+constexpr int kTrsmRows = 64;
+
+// TRSM variants on the off-diagonal rows X of a panel (diagonal block D):
+enum TrsmMode : int {
+    TRSM_LLT = 0,        // X <- X L^{-T}, L = lower(D)            (Cholesky)
+    TRSM_LU_L = 1,       // X <- X U^{-1}, U = upper(D)            (LU, L panel)
+    TRSM_LU_U = 2        // X <- X L^{-T}, L = unit lower(D)       (LU, U^T panel)
+};
+
+// ---- factorization -------------------------------------------------------
+template <typename T>
+void launch_assemble(int64_t nnz, const double *vals, const int64_t *amap, T *L, T *U,
+                     cudaStream_t s);
+
+template <typename T>
+void launch_potrf(const DevPlan &p, const int32_t *panels, int count, T *L, const double *replace_tau,
+                  int64_t *err_col, unsigned long long *nrepl, cudaStream_t s);
+
+template <typename T>
+void launch_getrf(const DevPlan &p, const int32_t *panels, int count, T *L, const double *tau,
+                  int64_t *err_col, unsigned long long *nrepl, cudaStream_t s);
+
+template <typename T>
+void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, const T *Dsrc, T *X,
+                 int mode, cudaStream_t s);
+
+template <typename T>
+void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles, int count,
+                   const T *Aop, const T *Bop, T *C, int lower, int from_r1, cudaStream_t s);
+
+// The standalone update of the paper's kernel study (double).
+void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A, int64_t lda,
+                              double *C, int64_t ldc, const int32_t *rowmap,
+                              const int32_t *colmap, int lower, cudaStream_t s);
+
+// ---- solves ----------------------------------------------------------------
+void launch_permute_in(int64_t n, int nrhs, const double *B, int64_t ldb, const int64_t *perm,
+                       double *Y, cudaStream_t s);
+void launch_permute_out(int64_t n, int nrhs, const double *Y, const int64_t *perm, double *X,
+                        int64_t ldx, cudaStream_t s);
+
+// Forward: diagonal solve per panel, then the off-diagonal scatter.
+template <typename T>
+void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, const T *L, int unit,
+                     double *Y, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, const T *L, double *Y,
+                    int nrhs, cudaStream_t s);
+// Backward: off-diagonal gather (partial sums per chunk), then the diagonal solve.
+template <typename T>
+void launch_bwd_off(const DevPlan &p, const RowChunk *chunks, int count, const T *Lop,
+                    double *Y, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, const T *L, int upper_from_d,
+                     double *Y, int nrhs, cudaStream_t s);
+
+// ---- residuals and norms ---------------------------------------------------
+// R = B - A X for nrhs columns (A by rows, original numbering); per column
+// stores max|r|, max|x|, max|b| into norms[3*c + {0,1,2}] (bit patterns of
+// non-negative doubles, combined with atomicMax).
+void launch_residual(int64_t n, int nrhs, const int64_t *rp, const int32_t *ci,
+                     const int64_t *src, const double *vals, const double *X, int64_t ldx,
+                     const double *B, int64_t ldb, double *R, unsigned long long *norms,
+                     cudaStream_t s);
+void launch_row_abs_sum_max(int64_t n, const int64_t *rp, const int64_t *src, const double *vals,
+                            unsigned long long *out, cudaStream_t s);
+void launch_axpy_cols(int64_t n, int nrhs, const double *D, double *X, int64_t ldx,
+                      cudaStream_t s);
+
+}  // namespace spx

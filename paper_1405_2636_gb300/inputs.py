@@ -238,3 +238,41 @@ class Workload:
 LAPLACE2D_31 = Workload("laplace2d_31x31", (31, 31, 1), 1, 1, 1)
 DIFFUSION3D_64 = Workload("diffusion3d_64^3", (64, 64, 64), 1, 16, 2)
 ELASTICITY27_40 = Workload("elasticity27_40^3x3", (40, 40, 40), 3, 1, 3)
+
+
+def gapped_update_case(m: int, k: int, nb: int, seed: int, avg_block: int = 200):
+    """The kernel-study input of Sec. V-B: C = C - A B^T with B the first nb rows
+    of A; C is a panel twice as tall as A whose rows are cut into random blocks
+    of about ``avg_block`` rows; A's rows come in blocks that each lie inside
+    one block of C, without overlap.
+
+    Returns (A m x k column-major, C hc x nc column-major, rowmap int32[m],
+    colmap int32[nb]) as NumPy arrays.
+    """
+    g = rng(seed, STREAM_EXTRA)
+    hc = 2 * m
+    # C blocks: random sizes in [1, 2*avg-1] until they cover hc rows
+    cuts = [0]
+    while cuts[-1] < hc:
+        cuts.append(min(hc, cuts[-1] + int(g.integers(1, 2 * avg_block))))
+    cblocks = list(zip(cuts[:-1], cuts[1:]))
+    # A blocks: walk C blocks in order, take a random sub-interval of each
+    # until m rows are placed (rows stay increasing, blocks never overlap)
+    rowmap = []
+    while len(rowmap) < m:
+        for (a, b) in cblocks:
+            if len(rowmap) >= m:
+                break
+            if g.random() < 0.5:
+                continue
+            size = min(b - a, m - len(rowmap))
+            take = int(g.integers(1, size + 1))
+            start = a + int(g.integers(0, (b - a) - take + 1))
+            rowmap.extend(range(start, start + take))
+        rowmap = sorted(set(rowmap))[:m]
+    rowmap = np.asarray(rowmap[:m], dtype=np.int32)
+    nc = max(nb, int(np.ceil(nb * 1.5)))
+    colmap = np.sort(g.choice(nc, size=nb, replace=False)).astype(np.int32)
+    A = np.asfortranarray(g.standard_normal((m, k)))
+    C = np.asfortranarray(g.standard_normal((hc, nc)))
+    return A, C, rowmap, colmap

@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libspx (include/spx.h).
+
+Argument marshalling only: every step of the factorization and the solves
+runs in the library's CUDA kernels.  Device arrays are passed as PyTorch CUDA
+tensors (their data pointers); host arrays as NumPy arrays.  There is no CPU
+fallback: if ``libspx.so`` is missing or no sm_103 GPU is present, calls fail
+loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspx.so")
+
+SPX_OK, SPX_ERR_ARG, SPX_ERR_ALLOC, SPX_ERR_CUDA, SPX_ERR_NOT_SPD = 0, 1, 2, 3, 4
+SPX_ERR_ZERO_PIVOT, SPX_ERR_TIMEOUT, SPX_ERR_NOT_CONVERGED, SPX_ERR_STATE = 5, 6, 7, 8
+SPX_LLT, SPX_LU = 0, 1
+SPX_FP64, SPX_FP32, SPX_TF32, SPX_BF16 = 0, 1, 2, 3
+SPX_ORDER_AUTO, SPX_ORDER_GRID, SPX_ORDER_GRAPH, SPX_ORDER_GIVEN, SPX_ORDER_NATURAL = 0, 1, 2, 3, 4
+
+PRECISIONS = {"fp64": SPX_FP64, "fp32": SPX_FP32, "tf32": SPX_TF32, "bf16": SPX_BF16}
+STATUS_NAMES = {0: "SPX_OK", 1: "SPX_ERR_ARG", 2: "SPX_ERR_ALLOC", 3: "SPX_ERR_CUDA",
+                4: "SPX_ERR_NOT_SPD", 5: "SPX_ERR_ZERO_PIVOT", 6: "SPX_ERR_TIMEOUT",
+                7: "SPX_ERR_NOT_CONVERGED", 8: "SPX_ERR_STATE"}
+
+# Every symbol include/spx.h declares.
+EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_factorize",
+            "spx_solve", "spx_get_info", "spx_get_perm", "spx_get_factor", "spx_last_error",
+            "spx_free", "spx_update"]
+
+
+class spx_options(ctypes.Structure):
+    _fields_ = [("ordering", ctypes.c_int32), ("grid", ctypes.c_int32 * 3),
+                ("dof", ctypes.c_int32), ("max_width", ctypes.c_int32),
+                ("amalg_ratio", ctypes.c_double), ("perm", ctypes.POINTER(ctypes.c_int64)),
+                ("lower_only", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("pivot_tau", ctypes.c_double)]
+
+
+class spx_refine(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
+                ("gmres_max_iter", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("tol", ctypes.c_double)]
+
+
+class spx_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("gmres_iters", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("backward_error", ctypes.c_double)]
+
+
+class spx_info(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "n", "nnz_a", "nnz_l", "nnz_stored", "factor_bytes", "nsupernodes", "npanels",
+        "nlevels", "nupdates", "bad_col", "npivot_repl")] + [
+        ("method", ctypes.c_int32), ("precision", ctypes.c_int32)] + [
+        (name, ctypes.c_double) for name in (
+            "flops", "flops_stored", "update_flops", "analyze_ms", "factor_ms", "solve_ms")]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def load():
+    """Load libspx.so (built in-tree by ``build.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_1405_2636_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.spx_default_options.argtypes = [ctypes.POINTER(spx_options)]
+    lib.spx_default_options.restype = None
+    lib.spx_default_refine.argtypes = [ctypes.POINTER(spx_refine)]
+    lib.spx_default_refine.restype = None
+    lib.spx_analyze.argtypes = [_i64, _vp, _vp, ctypes.c_int, ctypes.POINTER(spx_options),
+                                ctypes.POINTER(_vp)]
+    lib.spx_factorize.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp]
+    lib.spx_solve.argtypes = [_vp, ctypes.c_int32, _vp, _i64, _vp, _i64, ctypes.c_int,
+                              ctypes.POINTER(spx_refine), ctypes.POINTER(spx_solve_info), _vp]
+    lib.spx_get_info.argtypes = [_vp, ctypes.POINTER(spx_info)]
+    lib.spx_get_perm.argtypes = [_vp, _vp]
+    lib.spx_get_factor.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    lib.spx_last_error.argtypes = [_vp]
+    lib.spx_last_error.restype = ctypes.c_char_p
+    lib.spx_free.argtypes = [_vp]
+    lib.spx_free.restype = None
+    lib.spx_update.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]
+    for name in ("spx_analyze", "spx_factorize", "spx_solve", "spx_get_info", "spx_get_perm",
+                 "spx_get_factor", "spx_update"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class SpxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int, handle=None):
+    if status != SPX_OK:
+        msg = load().spx_last_error(handle)
+        raise SpxError(status, msg.decode() if msg else "")
+
+
+def _ptr(a) -> int:
+    """Data pointer of a NumPy array or a torch tensor."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def default_options(**kw) -> spx_options:
+    o = spx_options()
+    load().spx_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "grid":
+            for i, g in enumerate(list(v) + [1] * (3 - len(v))):
+                o.grid[i] = int(g)
+        elif k == "perm":
+            continue
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def default_refine(**kw) -> spx_refine:
+    r = spx_refine()
+    load().spx_default_refine(ctypes.byref(r))
+    for k, v in kw.items():
+        setattr(r, k, v)
+    return r
+
+
+class Handle:
+    """An analysed pattern and (after ``factorize``) its device-resident factor."""
+
+    def __init__(self, raw: int, n: int, nnz: int):
+        self._h = raw
+        self.n = n
+        self.nnz = nnz
+
+    # -- lifecycle -----------------------------------------------------------
+    def free(self):
+        if self._h:
+            load().spx_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # -- calls -----------------------------------------------------------------
+    def factorize(self, values, precision="fp64", stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if not _is_device(values):
+            values = np.ascontiguousarray(values, dtype=np.float64)
+        st = load().spx_factorize(self._h, _ptr(values), 1 if _is_device(values) else 0, prec,
+                                  _stream_ptr(stream))
+        _check(st, self._h)
+
+    def solve(self, B, X=None, refine=None, stream=None) -> tuple:
+        """Solve A X = B.  B: (n,) or (n, nrhs), column-major host array or a
+        CUDA tensor laid out column-major (i.e. ``B.t().contiguous().t()``)."""
+        dev = _is_device(B)
+        if dev:
+            one = B.dim() == 1
+            nrhs = 1 if one else B.shape[1]
+            ldb = self.n if one else B.stride(1)
+            if X is None:
+                import torch
+                X = torch.empty((nrhs, self.n), dtype=torch.float64, device=B.device).t() \
+                    if not one else torch.empty(self.n, dtype=torch.float64, device=B.device)
+            ldx = self.n if one else X.stride(1)
+        else:
+            B = np.asfortranarray(B, dtype=np.float64)
+            one = B.ndim == 1
+            nrhs = 1 if one else B.shape[1]
+            ldb = self.n
+            if X is None:
+                X = np.empty_like(B, order="F")
+            ldx = self.n
+        info = spx_solve_info()
+        rptr = ctypes.byref(refine) if refine is not None else None
+        st = load().spx_solve(self._h, nrhs, _ptr(B), ldb, _ptr(X), ldx, 1 if dev else 0, rptr,
+                              ctypes.byref(info), _stream_ptr(stream))
+        if st not in (SPX_OK, SPX_ERR_NOT_CONVERGED):
+            _check(st, self._h)
+        return X, {"iters": info.iters, "gmres_iters": info.gmres_iters,
+                   "converged": bool(info.converged), "backward_error": info.backward_error,
+                   "status": STATUS_NAMES[st]}
+
+    def info(self) -> dict:
+        i = spx_info()
+        _check(load().spx_get_info(self._h, ctypes.byref(i)), self._h)
+        return i.as_dict()
+
+    def perm(self) -> np.ndarray:
+        p = np.empty(self.n, dtype=np.int64)
+        _check(load().spx_get_perm(self._h, _ptr(p)), self._h)
+        return p
+
+    def factor_on_pattern(self, Lp: np.ndarray, Li: np.ndarray, lu: bool = False):
+        Lp = np.ascontiguousarray(Lp, dtype=np.int64)
+        Li = np.ascontiguousarray(Li, dtype=np.int32)
+        Lx = np.empty(len(Li), dtype=np.float64)
+        Ut = np.empty(len(Li), dtype=np.float64) if lu else None
+        _check(load().spx_get_factor(self._h, _ptr(Lp), _ptr(Li), _ptr(Lx), _ptr(Ut)), self._h)
+        return (Lx, Ut) if lu else Lx
+
+
+def analyze(colptr: np.ndarray, rowind: np.ndarray, method: str = "llt", perm=None,
+            **opts) -> Handle:
+    """spx_analyze on host CSC arrays (int64 colptr, int32 rowind)."""
+    colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(rowind, dtype=np.int32)
+    n = len(colptr) - 1
+    o = default_options(**opts)
+    keep = None
+    if perm is not None:
+        keep = np.ascontiguousarray(perm, dtype=np.int64)
+        o.perm = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        o.ordering = SPX_ORDER_GIVEN
+    raw = _vp()
+    m = SPX_LLT if method == "llt" else SPX_LU
+    st = load().spx_analyze(n, _ptr(colptr), _ptr(rowind), m, ctypes.byref(o), ctypes.byref(raw))
+    _check(st, None)
+    del keep
+    return Handle(raw.value, n, int(colptr[-1]))
+
+
+def update(m, nb_rows, k, A, lda, C, ldc, rowmap, colmap, lower=True, stream=None):
+    """spx_update on CUDA tensors (the supernodal update kernel on its own)."""
+    st = load().spx_update(m, nb_rows, k, _ptr(A), lda, _ptr(C), ldc, _ptr(rowmap), _ptr(colmap),
+                           1 if lower else 0, _stream_ptr(stream))
+    _check(st, None)

