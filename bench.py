@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the supernodal factorization on one GB300 (per rank).
+
+Workload: 3-D 7-point variable-coefficient diffusion on a 64^3 grid
+(n = 262,144), node coefficients exp(g), g ~ N(0,1), 16 right-hand sides
+~ U(-1,1), geometric nested-dissection ordering.  One step is the whole hot
+path: assembly + numerical factorization + solve of the 16 right-hand sides to
+backward error <= 1e-12 (with refinement when the factor is single
+precision).  Each precision mode runs its own steps; the headline is the
+fastest mode that reaches the target.
+
+value = exact-pattern factorization flops / step time (GFlop/s), summed over
+ranks (independent replicas: the factorization of one system does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "factorization GFlop/s & time-to-solve at 1e-12 backward error, FP64 vs mixed"
+TARGET_BERR = 1e-12
+GRID = (64, 64, 64)
+NRHS = 16
+SEED = 2
+WORKLOAD = "diffusion3d_64^3_7pt_expN01_16rhs"
+FP64_ALU_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9        # 2 DFMA / clk / SM
+FP32_ALU_PEAK_GFLOPS = 152 * 128 * 2 * 2.07e9 / 1e9      # 128 FFMA / clk / SM
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="spx", choices=["spx", "reference"])
+    ap.add_argument("--modes", default="fp64,fp32")
+    ap.add_argument("--grid", default="64,64,64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        busy = [r for r in rows if num(r[4]) >= 50] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(num(r[1]) for r in busy),
+                "sm_max_mhz": max(num(r[2]) for r in rows),
+                "power_w_max": max(num(r[3]) for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(busy)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(grid, seconds_budget: float) -> dict:
+    """Oracle factorization + 16-RHS solve on a sub-grid of the same workload."""
+    import oracle
+    from paper_1405_2636_gb300 import inputs
+
+    A = inputs.diffusion_3d(*grid, SEED)
+    B = inputs.rhs(A.shape[0], NRHS, SEED)
+    perm = oracle.nd_grid(*grid)
+    flops = None
+    times = []
+    t_end = time.perf_counter() + seconds_budget
+    while True:
+        t0 = time.perf_counter()
+        F = oracle.cholesky(A, perm)
+        oracle.solve(F, B)
+        times.append(time.perf_counter() - t0)
+        flops = oracle.flops(F.sym.counts, "llt")
+        if time.perf_counter() > t_end:
+            break
+    t = statistics.median(times)
+    return {"value": flops / t / 1e9, "unit": "GFlop/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle left-looking FP64 Cholesky + 16-RHS solve of the same diffusion "
+                      f"generator on a {grid[0]}x{grid[1]}x{grid[2]} sub-grid "
+                      f"({flops / 1e9:.2f} GFlop), median of {len(times)} runs",
+            "seconds": sum(times)}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1405_2636_gb300 import inputs
+
+    oracle.build()
+    grid = (24, 24, 24)
+    A = inputs.diffusion_3d(*grid, SEED)
+    B = inputs.rhs(A.shape[0], NRHS, SEED)
+    perm = oracle.nd_grid(*grid)
+    F = None
+    for _ in range(args.warmup):
+        F = oracle.cholesky(A, perm)
+        oracle.solve(F, B)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        F = oracle.cholesky(A, perm)
+        X = oracle.solve(F, B)
+        times.append(time.perf_counter() - t0)
+    flops = oracle.flops(F.sym.counts, "llt")
+    berr = oracle.backward_error(A, X, B)
+    ms = 1e3 * sum(times) / len(times)
+    value = flops / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GFlop/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_grid": list(grid),
+                       "note": "the oracle (plain single-threaded C, FP64) on a bounded "
+                               "sub-grid of the same workload; one step = factorization "
+                               "+ 16-RHS solve"},
+            "backward_error": berr,
+            "cpu_baseline": {"value": value, "unit": "GFlop/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{grid[0]}^3 sub-grid of the diffusion workload, "
+                                       f"{flops / 1e9:.2f} GFlop per step"},
+            "e2e": {"value": value, "unit": "GFlop/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = _dist()
+    import torch
+
+    import __graft_entry__
+    from paper_1405_2636_gb300 import inputs, spx
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+
+    grid = tuple(int(v) for v in args.grid.split(","))
+    A = inputs.diffusion_3d(*grid, SEED)
+    colptr, rowind, vals = inputs.csc_arrays(A)
+    n = A.shape[0]
+    B = inputs.rhs(n, NRHS, SEED)
+    h = spx.analyze(colptr, rowind, "llt", ordering=spx.SPX_ORDER_GRID, grid=grid)
+    info0 = h.info()
+    flops = info0["flops"]
+
+    dev = torch.device("cuda", local)
+    vals_d = torch.from_numpy(vals).to(dev)
+    B_d = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev).t()      # column-major n x 16
+    X_d = torch.empty((NRHS, n), dtype=torch.float64, device=dev).t()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def step(mode):
+        h.factorize(vals_d, mode)
+        refine = None if mode == "fp64" else spx.default_refine(tol=TARGET_BERR)
+        _, sinfo = h.solve(B_d, X_d, refine=refine)
+        return sinfo
+
+    results = {}
+    launches_total = 0
+    clocks = None
+    modes = [m for m in args.modes.split(",") if m]
+    for mode in modes:
+        for _ in range(args.warmup):
+            step(mode)
+        torch.cuda.synchronize()
+        times = []
+        sinfo = None
+        with ClockSampler(local) as cs:
+            for _ in range(args.steps):
+                flush.fill_(float(len(times)))           # L2 flush between timed steps
+                barrier()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sinfo = step(mode)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                barrier()
+                times.append(e0.elapsed_time(e1))
+        ck = cs.summary()
+        info = h.info()
+        # independent host check of the timed step's output (scipy residual)
+        Xc = X_d.cpu().numpy()
+        R_host = B - A @ Xc
+        den = (abs(A).sum(axis=1).max() * np.abs(Xc).max(axis=0) + np.abs(B).max(axis=0))
+        host_berr = float(np.max(np.abs(R_host).max(axis=0) / den))
+        ms = max_over_ranks(sum(times) / len(times))
+        launches_total += args.steps * (info["launches_factor"] + info["launches_solve"])
+        # profiled factorization: per-kernel-class device time (events on the library stream)
+        h.set_profiling(True)
+        h.factorize(vals_d, mode)
+        h.set_profiling(False)
+        ks = h.kernel_stats()
+        # end-to-end through the C ABI with host buffers (copies inside the timed region)
+        e2e_times = []
+        for i in range(0 if args.no_e2e else max(2, args.steps)):
+            barrier()
+            t0 = time.perf_counter()
+            h.factorize(vals, mode)
+            Xh, sinfo_h = h.solve(B, refine=None if mode == "fp64" else spx.default_refine(tol=TARGET_BERR))
+            dt = time.perf_counter() - t0
+            if i > 0:
+                e2e_times.append(dt)
+        e2e_ms = max_over_ranks(1e3 * sum(e2e_times) / len(e2e_times)) if e2e_times else float("nan")
+        if not e2e_times:
+            sinfo_h = {"backward_error": float("nan")}
+        results[mode] = {
+            "ms_per_step": ms,
+            "factor_ms": info["factor_ms"],
+            "solve_ms": info["solve_ms"],
+            "factor_gflops": flops / (info["factor_ms"] / 1e3) / 1e9,
+            "time_to_solve_gflops": flops / (ms / 1e3) / 1e9,
+            "backward_error": sinfo["backward_error"],
+            "host_backward_error": host_berr,
+            "refine_iters": sinfo["iters"],
+            "converged": bool(sinfo["backward_error"] <= TARGET_BERR and host_berr <= TARGET_BERR),
+            "launches_per_step": info["launches_factor"] + info["launches_solve"],
+            "kernel_stats": ks,
+            "e2e_ms": e2e_ms,
+            "e2e_backward_error": sinfo_h["backward_error"],
+            "clocks": ck,
+        }
+        clocks = ck if clocks is None else clocks
+
+    ok = [m for m in modes if results[m]["converged"]]
+    head = min(ok, key=lambda m: results[m]["ms_per_step"]) if ok else modes[0]
+    R = results[head]
+    ks = R["kernel_stats"]["update"]
+    esz_mode = "fp64" if head == "fp64" else "fp32"
+    peak = FP64_ALU_PEAK_GFLOPS if esz_mode == "fp64" else FP32_ALU_PEAK_GFLOPS
+    achieved = ks["flops"] / (ks["ms"] / 1e3) / 1e9 if ks["ms"] > 0 else 0.0
+    roofline = {"kernel": "update_kernel (supernodal update with fused scatter)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
+                                if esz_mode == "fp64" else
+                                "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"),
+                "traffic": None,
+                "launches": ks["launches"], "algorithmic_flops": ks["flops"],
+                "algorithmic_bytes": ks["bytes"], "device_ms": ks["ms"]}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_rate((32, 32, 32), 8.0)
+    value = world * flops / (R["ms_per_step"] / 1e3) / 1e9
+    e2e_value = world * flops / (R["e2e_ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": R["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "f32-factor+f64-refinement",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz_a": int(colptr[-1]), "nrhs": NRHS,
+                   "seed": SEED, "grid": list(grid), "ordering": "geometric nested dissection",
+                   "nnz_l": info0["nnz_l"], "flops_exact": flops,
+                   "panels": info0["npanels"], "levels": info0["nlevels"],
+                   "headline_mode": head, "l2": "flushed between timed steps (256 MiB write); "
+                   "the 1.3 GB factor also exceeds L2", "parallelism": f"replicas x{world}"},
+        "modes": {m: {k: v for k, v in results[m].items() if k not in ("kernel_stats",)}
+                  for m in modes},
+        "kernel_stats": {m: results[m]["kernel_stats"] for m in modes},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "GFlop/s",
+                "h2d_bytes_per_step": int(8 * colptr[-1] + 8 * n * NRHS),
+                "d2h_bytes_per_step": int(8 * n * NRHS)},
+        "gpu_launches": launches_total,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,8 @@ typedef struct {
     double flops;           /* exact-pattern factorization flops: sum c_j^2 (LLT) or sum 2(c_j-1)^2+(c_j-1) (LU) */
     double flops_stored;    /* the same count on the amalgamated panel structure */
     double update_flops;    /* flops of the panel updates on the stored structure */
+    int64_t launches_factor;/* kernels one spx_factorize launches */
+    int64_t launches_solve; /* kernels the last spx_solve launched */
     double analyze_ms;      /* host time of spx_analyze */
     double factor_ms;       /* device time of the last spx_factorize (assembly included) */
     double solve_ms;        /* device time of the last spx_solve */
@@ -163,6 +165,28 @@ spx_status spx_get_factor(spx_handle h, const int64_t *Lp, const int32_t *Li, do
 /* Message for the last failing call on h (or on handle creation when h is
  * NULL).  The string stays valid until the next call on h. */
 const char *spx_last_error(spx_handle h);
+
+/* Kernel classes of the factorization, for spx_kernel_stats. */
+enum {
+    SPX_K_ASSEMBLE = 0,   /* zeroing and scattering A into the panels, ||A||_inf */
+    SPX_K_DIAG = 1,       /* diagonal-block POTRF / GETRF */
+    SPX_K_TRSM = 2,       /* panel triangular solves */
+    SPX_K_UPDATE = 3,     /* supernodal updates with fused scatter */
+    SPX_K_CLASSES = 4
+};
+
+typedef struct {
+    double ms[SPX_K_CLASSES];       /* device time per class in the last profiled factorization */
+    int64_t launches[SPX_K_CLASSES];/* kernel launches per class */
+    double flops[SPX_K_CLASSES];    /* algorithmic flops per class on the stored structure */
+    double bytes[SPX_K_CLASSES];    /* algorithmic bytes per class (operands read once, targets read and written once) */
+} spx_kernel_stats;
+
+/* on = 1: the next factorizations run launch by launch (no graph) with CUDA
+ * events around every kernel class of every level, on the library's stream,
+ * and spx_get_kernel_stats reports the accumulated per-class device time. */
+spx_status spx_set_profiling(spx_handle h, int on);
+spx_status spx_get_kernel_stats(spx_handle h, spx_kernel_stats *out);
 
 /* Release a handle and everything it owns.  NULL-safe. */
 void spx_free(spx_handle h);

@@ -642,7 +642,7 @@ std::string analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, int
     std::vector<Task> tasks;
     std::vector<int32_t> level_task_ptr(nlev + 1, 0);
     std::vector<int32_t> relmap;
-    double upd = 0.0;
+    double upd = 0.0, upd_elems = 0.0;
     for (int32_t l = 0; l < nlev; ++l) {
         for (int32_t q = level_ptr[l]; q < level_ptr[l + 1]; ++q) {
             int32_t k = level_panels[q];
@@ -668,6 +668,10 @@ std::string analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, int
                 double M = (double)(h - i), N = (double)(r1 - i), K = (double)w;
                 upd += (method == 0) ? (2.0 * (M - N) * N * K + N * (N + 1.0) * K)
                                      : (2.0 * M * N * K + 2.0 * (M - N) * N * K);
+                // operands read once, updated target entries read and written once
+                upd_elems += (method == 0)
+                                 ? (M + N) * K + 2.0 * ((M - N) * N + N * (N + 1.0) / 2.0)
+                                 : (M + N) * K + (M - N + N) * K + 2.0 * (M * N + (M - N) * N);
                 tasks.push_back(tk);
                 i = r1;
             }
@@ -675,6 +679,17 @@ std::string analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, int
         level_task_ptr[l + 1] = (int32_t)tasks.size();
     }
     P.update_flops = upd;
+    P.update_elems = upd_elems;
+    for (int32_t p = 0; p < np; ++p) {
+        const double w = pw[p], off = (double)ph[p] - pw[p];
+        for (int32_t j = 0; j < pw[p]; ++j) {
+            const double c = w - j;
+            P.diag_flops += (method == 0) ? c * c : 2.0 * (c - 1.0) * (c - 1.0) + (c - 1.0);
+        }
+        P.trsm_flops += (method == 0 ? 1.0 : 2.0) * off * w * w;
+        P.diag_elems += 2.0 * w * w;
+        P.trsm_elems += (method == 0 ? 1.0 : 2.0) * (2.0 * off * w + w * w);
+    }
 
     // ---- assembly map --------------------------------------------------------
     std::vector<int64_t> amap(nnz, -1);

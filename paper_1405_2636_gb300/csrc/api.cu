@@ -40,6 +40,8 @@ struct spx_handle_s {
     int64_t *d_amap = nullptr, *d_csr_ptr = nullptr, *d_csr_src = nullptr, *d_perm = nullptr;
     int32_t *d_csr_col = nullptr;
 
+    std::vector<int32_t> lvl_wmax;    // widest panel per level
+    int64_t dinv_elems = 0;           // sum of w^2 over panels
     std::vector<int64_t> chunk_ptr;   // per level, into d_chunks
     RowChunk *d_chunks = nullptr;
     std::vector<int64_t> tile_ptr;    // per level, into d_tiles (LLT, or LU's L side)
@@ -50,7 +52,7 @@ struct spx_handle_s {
     // numeric state
     int precision = -1;
     bool factored = false;
-    void *d_L = nullptr, *d_U = nullptr;
+    void *d_L = nullptr, *d_U = nullptr, *d_Dinv = nullptr;
     int factor_prec_alloc = -1;
     double *d_vals = nullptr;
     double *d_tau = nullptr;                 // [0] pivot threshold used by the diagonal kernels
@@ -63,10 +65,18 @@ struct spx_handle_s {
 
     // solve workspace
     int ws_nrhs = 0;
-    double *d_B = nullptr, *d_X = nullptr, *d_R = nullptr, *d_D = nullptr, *d_Y = nullptr;
+    double *d_B = nullptr, *d_X = nullptr, *d_R = nullptr, *d_D = nullptr;
+    double *d_Y = nullptr, *d_Z = nullptr, *d_T = nullptr, *d_Xs = nullptr;   // sweep vectors (factor type)
     unsigned long long *d_norms = nullptr;
     cudaGraphExec_t sgraph = nullptr;
     int sgraph_nrhs = -1, sgraph_prec = -1;
+
+    // profiling and launch accounting
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    spx_kernel_stats kstats{};
+    int64_t cnt = 0;                  // kernels enqueued by the current call
+    int64_t sweep_launches = 0;       // kernels of one solve sweep
 
     spx_info info{};
 };
@@ -156,8 +166,16 @@ spx_status ensure_device(spx_handle h)
 
     const spx::Plan &P = h->plan;
     spx_status st;
-    int64_t *pfcol, *prow, *pval;
+    int64_t *pfcol, *prow, *pval, *pinv;
     int32_t *pw, *ph, *rows, *relmap;
+    std::vector<int64_t> hpinv(P.npanels + 1, 0);
+    for (int32_t q = 0; q < P.npanels; ++q) hpinv[q + 1] = hpinv[q] + (int64_t)P.pw[q] * P.pw[q];
+    h->dinv_elems = hpinv[P.npanels];
+    h->lvl_wmax.assign(P.nlevels, 1);
+    for (int32_t l = 0; l < P.nlevels; ++l)
+        for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q)
+            h->lvl_wmax[l] = std::max(h->lvl_wmax[l], P.pw[P.level_panels[q]]);
+    if ((st = upload(h, &pinv, hpinv))) return st;
     if ((st = upload(h, &pfcol, P.pfcol)) || (st = upload(h, &pw, P.pw)) ||
         (st = upload(h, &ph, P.ph)) || (st = upload(h, &prow, P.prow)) ||
         (st = upload(h, &rows, P.rows)) || (st = upload(h, &pval, P.pval)) ||
@@ -174,6 +192,7 @@ spx_status ensure_device(spx_handle h)
     h->dp.prow = prow;
     h->dp.rows = rows;
     h->dp.pval = pval;
+    h->dp.pinv = pinv;
     h->dp.relmap = relmap;
 
     std::vector<DevTask> tasks(P.tasks.size());
@@ -223,23 +242,49 @@ spx_status ensure_device(spx_handle h)
 }
 
 // Enqueue the whole factorization on h->hs (captured into a graph).
+// Profiling: events recorded between kernel classes (non-graph runs only).
+struct Marks {
+    spx_handle h;
+    bool on;
+    size_t used = 0;
+    std::vector<std::pair<int, size_t>> spans;   // class, index of its end event
+    void mark(int cls)
+    {
+        if (!on) return;
+        if (used >= h->ev_pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->ev_pool.push_back(e);
+        }
+        cudaEventRecord(h->ev_pool[used], h->hs);
+        if (cls >= 0) spans.emplace_back(cls, used);
+        ++used;
+    }
+};
+
 template <typename T>
-void enqueue_factorization(spx_handle h, bool mixed)
+void enqueue_factorization(spx_handle h, bool mixed, Marks &mk)
 {
     const spx::Plan &P = h->plan;
     cudaStream_t s = h->hs;
-    T *L = (T *)h->d_L, *U = (T *)h->d_U;
+    T *L = (T *)h->d_L, *U = (T *)h->d_U, *Dinv = (T *)h->d_Dinv;
     const size_t elems = (size_t)P.pval[P.npanels];
+    const bool lu = P.method == SPX_LU;
+    int64_t &cnt = h->cnt;
+    mk.mark(-1);
     init_scalars_kernel<<<1, 1, 0, s>>>(h->d_err, h->d_nrepl, h->d_anorm);
     spx::launch_row_abs_sum_max(P.n, h->d_csr_ptr, h->d_csr_src, h->d_vals, h->d_anorm, s);
     const double sqrt_eps = std::sqrt(std::ldexp(1.0, -52));
-    if (P.method == SPX_LU)
+    if (lu)
         set_tau_kernel<<<1, 1, 0, s>>>(h->d_anorm, h->pivot_tau_opt, sqrt_eps, h->d_tau);
     else
         set_tau_kernel<<<1, 1, 0, s>>>(h->d_anorm, mixed ? -1.0 : 0.0, sqrt_eps, h->d_tau);
+    cnt += 3;
     cudaMemsetAsync(L, 0, elems * sizeof(T), s);
     if (U) cudaMemsetAsync(U, 0, elems * sizeof(T), s);
     spx::launch_assemble<T>(P.nnz_a, h->d_vals, h->d_amap, L, U, s);
+    cnt += P.nnz_a > 0;
+    mk.mark(SPX_K_ASSEMBLE);
     for (int32_t l = 0; l < P.nlevels; ++l) {
         const int32_t *panels = h->d_level_panels + P.level_ptr[l];
         const int np = P.level_ptr[l + 1] - P.level_ptr[l];
@@ -247,48 +292,69 @@ void enqueue_factorization(spx_handle h, bool mixed)
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
         const UpdTile *tl = h->d_tiles + h->tile_ptr[l];
         const int ntl = (int)(h->tile_ptr[l + 1] - h->tile_ptr[l]);
-        if (P.method == SPX_LLT) {
-            spx::launch_potrf<T>(h->dp, panels, np, L, h->d_tau, h->d_err, h->d_nrepl, s);
-            spx::launch_trsm<T>(h->dp, ch, nch, L, L, spx::TRSM_LLT, s);
+        const int wmax = h->lvl_wmax[l];
+        if (!lu) {
+            spx::launch_potrf<T>(h->dp, panels, np, wmax, L, Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
+            cnt += np > 0;
+            mk.mark(SPX_K_DIAG);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LLT, s);
+            cnt += nch > 0;
+            mk.mark(SPX_K_TRSM);
             spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, L, L, 1, 0, s);
+            cnt += ntl > 0;
+            mk.mark(SPX_K_UPDATE);
         } else {
             const UpdTile *tu = h->d_tilesu + h->tileu_ptr[l];
             const int ntu = (int)(h->tileu_ptr[l + 1] - h->tileu_ptr[l]);
-            spx::launch_getrf<T>(h->dp, panels, np, L, h->d_tau, h->d_err, h->d_nrepl, s);
-            spx::launch_trsm<T>(h->dp, ch, nch, L, L, spx::TRSM_LU_L, s);
-            spx::launch_trsm<T>(h->dp, ch, nch, L, U, spx::TRSM_LU_U, s);
+            spx::launch_getrf<T>(h->dp, panels, np, wmax, L, Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
+            cnt += np > 0;
+            mk.mark(SPX_K_DIAG);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LU_L, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, U, spx::TRSM_LU_U, s);
+            cnt += 2 * (nch > 0);
+            mk.mark(SPX_K_TRSM);
             spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, U, L, 0, 0, s);
             spx::launch_update<T>(h->dp, h->d_tasks, tu, ntu, U, L, U, 0, 1, s);
+            cnt += (ntl > 0) + (ntu > 0);
+            mk.mark(SPX_K_UPDATE);
         }
     }
 }
 
-// One forward + backward sweep: d_D = A^{-1} d_R (through the factor).
+// One forward + backward sweep in the factor's arithmetic: d_D = A^{-1} d_R.
 template <typename T>
 void enqueue_sweep(spx_handle h, int nrhs)
 {
     const spx::Plan &P = h->plan;
     cudaStream_t s = h->hs;
-    const T *L = (const T *)h->d_L, *U = (const T *)h->d_U;
+    const T *L = (const T *)h->d_L, *U = (const T *)h->d_U, *Dinv = (const T *)h->d_Dinv;
+    T *Y = (T *)h->d_Y, *Z = (T *)h->d_Z, *Tacc = (T *)h->d_T, *Xs = (T *)h->d_Xs;
     const bool lu = P.method == SPX_LU;
-    spx::launch_permute_in(P.n, nrhs, h->d_R, P.n, h->d_perm, h->d_Y, s);
+    int64_t k = 0;
+    spx::launch_permute_in<T>(P.n, nrhs, h->d_R, P.n, h->d_perm, Y, s);
+    cudaMemsetAsync(Tacc, 0, sizeof(T) * (size_t)P.n * nrhs, s);
     for (int32_t l = 0; l < P.nlevels; ++l) {
         const int32_t *panels = h->d_level_panels + P.level_ptr[l];
         const int np = P.level_ptr[l + 1] - P.level_ptr[l];
         const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
-        spx::launch_fwd_diag<T>(h->dp, panels, np, L, lu ? 1 : 0, h->d_Y, nrhs, s);
-        spx::launch_fwd_off<T>(h->dp, ch, nch, L, h->d_Y, nrhs, s);
+        const int wmax = h->lvl_wmax[l];
+        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Y, Z, nrhs, s);
+        spx::launch_fwd_off<T>(h->dp, ch, nch, wmax, L, Z, Y, nrhs, s);
+        k += (np > 0) + (nch > 0);
     }
     for (int32_t l = P.nlevels - 1; l >= 0; --l) {
         const int32_t *panels = h->d_level_panels + P.level_ptr[l];
         const int np = P.level_ptr[l + 1] - P.level_ptr[l];
         const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
-        spx::launch_bwd_off<T>(h->dp, ch, nch, lu ? U : L, h->d_Y, nrhs, s);
-        spx::launch_bwd_diag<T>(h->dp, panels, np, L, lu ? 1 : 0, h->d_Y, nrhs, s);
+        const int wmax = h->lvl_wmax[l];
+        spx::launch_bwd_off<T>(h->dp, ch, nch, wmax, lu ? U : L, Xs, Tacc, nrhs, s);
+        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Z, Tacc, Xs, nrhs, s);
+        k += (np > 0) + (nch > 0);
     }
-    spx::launch_permute_out(P.n, nrhs, h->d_Y, h->d_perm, h->d_D, P.n, s);
+    spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, h->d_D, P.n, s);
+    h->sweep_launches = k + 2;
 }
 
 spx_status capture(spx_handle h, cudaGraphExec_t *exec, void (*body)(spx_handle, int, bool),
@@ -316,8 +382,9 @@ spx_status capture(spx_handle h, cudaGraphExec_t *exec, void (*body)(spx_handle,
 
 void body_factor(spx_handle h, int prec, bool)
 {
-    if (prec == SPX_FP64) enqueue_factorization<double>(h, false);
-    else enqueue_factorization<float>(h, true);
+    Marks mk{h, false};
+    if (prec == SPX_FP64) enqueue_factorization<double>(h, false, mk);
+    else enqueue_factorization<float>(h, true, mk);
 }
 
 void body_sweep(spx_handle h, int nrhs, bool fp64)
@@ -335,7 +402,7 @@ void fence_from(spx_handle h, void *user_stream)
 spx_status ensure_workspace(spx_handle h, int nrhs)
 {
     if (h->ws_nrhs >= nrhs) return SPX_OK;
-    for (double **p : {&h->d_B, &h->d_X, &h->d_R, &h->d_D, &h->d_Y}) {
+    for (double **p : {&h->d_B, &h->d_X, &h->d_R, &h->d_D, &h->d_Y, &h->d_Z, &h->d_T, &h->d_Xs}) {
         dfree(h, *p);
         *p = nullptr;
     }
@@ -346,7 +413,9 @@ spx_status ensure_workspace(spx_handle h, int nrhs)
     spx_status st;
     if ((st = dalloc(h, &h->d_B, sz)) || (st = dalloc(h, &h->d_X, sz)) ||
         (st = dalloc(h, &h->d_R, sz)) || (st = dalloc(h, &h->d_D, sz)) ||
-        (st = dalloc(h, &h->d_Y, sz)) || (st = dalloc(h, &h->d_norms, (size_t)3 * nrhs)))
+        (st = dalloc(h, &h->d_Y, sz)) || (st = dalloc(h, &h->d_Z, sz)) ||
+        (st = dalloc(h, &h->d_T, sz)) || (st = dalloc(h, &h->d_Xs, sz)) ||
+        (st = dalloc(h, &h->d_norms, (size_t)3 * nrhs)))
         return st;
     h->ws_nrhs = nrhs;
     if (h->sgraph) {
@@ -364,6 +433,7 @@ spx_status residual(spx_handle h, int nrhs, double *berr)
     CU(cudaMemsetAsync(h->d_norms, 0, sizeof(unsigned long long) * 3 * nrhs, h->hs));
     spx::launch_residual(P.n, nrhs, h->d_csr_ptr, h->d_csr_col, h->d_csr_src, h->d_vals, h->d_X,
                          P.n, h->d_B, P.n, h->d_R, h->d_norms, h->hs);
+    h->cnt += 1;
     std::vector<unsigned long long> nb(3 * nrhs);
     CU(cudaMemcpyAsync(nb.data(), h->d_norms, sizeof(unsigned long long) * 3 * nrhs,
                        cudaMemcpyDeviceToHost, h->hs));
@@ -488,11 +558,14 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     if (h->factor_prec_alloc != (fp64 ? 1 : 0)) {
         dfree(h, h->d_L);
         dfree(h, h->d_U);
-        h->d_L = h->d_U = nullptr;
+        dfree(h, h->d_Dinv);
+        h->d_L = h->d_U = h->d_Dinv = nullptr;
         h->factor_prec_alloc = -1;
-        char *pl = nullptr;
+        char *pl = nullptr, *pd = nullptr;
         if ((st = dalloc(h, &pl, elems * esz))) return st;
         h->d_L = pl;
+        if ((st = dalloc(h, &pd, (size_t)h->dinv_elems * esz))) return st;
+        h->d_Dinv = pd;
         if (P.method == SPX_LU) {
             char *pu = nullptr;
             if ((st = dalloc(h, &pu, elems * esz))) return st;
@@ -509,13 +582,26 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     fence_from(h, cuda_stream);
     CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a,
                        values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->hs));
-    if (h->fgraph_prec != (int)precision) {
-        if ((st = capture(h, &h->fgraph, body_factor, (int)precision, false))) return st;
-        h->fgraph_prec = (int)precision;
+    Marks mk{h, h->profiling};
+    if (h->profiling) {
+        h->cnt = 0;
+        CU(cudaEventRecord(h->ev_t0, h->hs));
+        if (fp64) enqueue_factorization<double>(h, false, mk);
+        else enqueue_factorization<float>(h, true, mk);
+        CU(cudaGetLastError());
+        CU(cudaEventRecord(h->ev_t1, h->hs));
+        h->info.launches_factor = h->cnt;
+    } else {
+        if (h->fgraph_prec != (int)precision) {
+            h->cnt = 0;
+            if ((st = capture(h, &h->fgraph, body_factor, (int)precision, false))) return st;
+            h->fgraph_prec = (int)precision;
+            h->info.launches_factor = h->cnt;
+        }
+        CU(cudaEventRecord(h->ev_t0, h->hs));
+        CU(cudaGraphLaunch(h->fgraph, h->hs));
+        CU(cudaEventRecord(h->ev_t1, h->hs));
     }
-    CU(cudaEventRecord(h->ev_t0, h->hs));
-    CU(cudaGraphLaunch(h->fgraph, h->hs));
-    CU(cudaEventRecord(h->ev_t1, h->hs));
     int64_t bad = 0;
     unsigned long long nrepl = 0, abits = 0;
     CU(cudaMemcpyAsync(&bad, h->d_err, sizeof(bad), cudaMemcpyDeviceToHost, h->hs));
@@ -524,6 +610,31 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     CU(cudaStreamSynchronize(h->hs));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
+    if (h->profiling) {
+        spx_kernel_stats &K = h->kstats;
+        K = spx_kernel_stats{};
+        for (auto &sp : mk.spans) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, h->ev_pool[sp.second - 1], h->ev_pool[sp.second]);
+            K.ms[sp.first] += t;
+        }
+        const double e = fp64 ? 8.0 : 4.0;
+        const double nfac = (P.method == SPX_LU) ? 2.0 : 1.0;
+        K.flops[SPX_K_DIAG] = P.diag_flops;
+        K.flops[SPX_K_TRSM] = P.trsm_flops;
+        K.flops[SPX_K_UPDATE] = P.update_flops;
+        K.bytes[SPX_K_ASSEMBLE] = (double)P.nnz_a * 16.0 + (double)elems * e * nfac * 2.0;
+        K.bytes[SPX_K_DIAG] = P.diag_elems * e;
+        K.bytes[SPX_K_TRSM] = P.trsm_elems * e;
+        K.bytes[SPX_K_UPDATE] = P.update_elems * e;
+        K.launches[SPX_K_ASSEMBLE] = P.nnz_a > 0 ? 4 : 3;
+        for (int32_t l = 0; l < P.nlevels; ++l) {
+            K.launches[SPX_K_DIAG] += (P.level_ptr[l + 1] > P.level_ptr[l]);
+            K.launches[SPX_K_TRSM] += (int64_t)nfac * (h->chunk_ptr[l + 1] > h->chunk_ptr[l]);
+            K.launches[SPX_K_UPDATE] += (h->tile_ptr[l + 1] > h->tile_ptr[l]) +
+                                        (h->tileu_ptr[l + 1] > h->tileu_ptr[l]);
+        }
+    }
     std::memcpy(&h->anorm, &abits, 8);
     h->info.factor_ms = ms;
     h->info.precision = precision;
@@ -571,9 +682,11 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
         h->sgraph_nrhs = nrhs;
         h->sgraph_prec = h->precision;
     }
+    h->cnt = 0;
     CU(cudaEventRecord(h->ev_t0, h->hs));
     CU(cudaMemcpyAsync(h->d_R, h->d_B, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, h->hs));
     CU(cudaGraphLaunch(h->sgraph, h->hs));
+    h->cnt += h->sweep_launches;
     CU(cudaMemcpyAsync(h->d_X, h->d_D, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, h->hs));
     double berr = 0.0;
     if (rf.mode != 0 || info) {
@@ -581,6 +694,7 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
         while (rf.mode != 0 && !(berr <= rf.tol) && si.iters < rf.max_iter) {
             CU(cudaGraphLaunch(h->sgraph, h->hs));
             spx::launch_axpy_cols(P.n, nrhs, h->d_D, h->d_X, P.n, h->hs);
+            h->cnt += h->sweep_launches + 1;
             si.iters++;
             double e;
             if ((st = residual(h, nrhs, &e))) return st;
@@ -599,6 +713,7 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
     h->info.solve_ms = ms;
+    h->info.launches_solve = h->cnt;
     if (info) *info = si;
     if (rf.mode != 0 && !si.converged)
         return fail(h, SPX_ERR_NOT_CONVERGED, "refinement stopped at backward error " + std::to_string(berr));
@@ -677,6 +792,20 @@ spx_status spx_get_factor(spx_handle h, const int64_t *Lp, const int32_t *Li, do
     return SPX_OK;
 }
 
+spx_status spx_set_profiling(spx_handle h, int on)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    h->profiling = on != 0;
+    return SPX_OK;
+}
+
+spx_status spx_get_kernel_stats(spx_handle h, spx_kernel_stats *out)
+{
+    if (!h || !out) return fail(h, SPX_ERR_ARG, "NULL argument");
+    *out = h->kstats;
+    return SPX_OK;
+}
+
 const char *spx_last_error(spx_handle h)
 {
     return h ? h->err.c_str() : g_create_error.c_str();
@@ -688,6 +817,7 @@ void spx_free(spx_handle h)
     if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
     if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
     for (void *p : h->allocs) cudaFree(p);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->ev_fence) cudaEventDestroy(h->ev_fence);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);

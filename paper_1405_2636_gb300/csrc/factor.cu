@@ -42,22 +42,56 @@ void launch_assemble(int64_t nnz, const double *vals, const int64_t *amap, T *L,
 }
 
 // ---------------------------------------------------------------------------
-// Diagonal block, Cholesky: one CTA per panel, the block in shared memory in
-// double, right-looking by columns.  A pivot that is not positive is either
-// reported (replace_tau <= 0: the smallest failing column goes to *err_col)
-// or replaced by replace_tau and counted.
+// In-place inversion of a lower-triangular w x w block held in shared memory
+// (column-major, leading dimension w), read through element (i, j) at
+// a[trans ? j + i*w : i + j*w].  Columns are taken from the right:
+//   X(j,j) = 1 / L(j,j)   (1 when unit),
+//   X(i,j) = -(sum_{k=j+1..i} X(i,k) L(k,j)) X(j,j)   for i > j,
+// using the already inverted columns k > j (from X L = I).  With trans the
+// same routine inverts U^T, i.e. writes U^{-1} in the upper triangle.  C is
+// the arithmetic type; `col` is w doubles of scratch.
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ void invert_lower_inplace(double *a, int w, bool trans, bool unit, double *col)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = w - 1; j >= 0; --j) {
+        for (int i = j + 1 + tid; i < w; i += nt) col[i] = a[trans ? j + i * w : i + j * w];
+        __syncthreads();
+        const C xjj = unit ? (C)1 : (C)1 / (C)a[trans ? j + j * w : j + j * w];
+        for (int i = j + 1 + tid; i < w; i += nt) {
+            const C xii = unit ? (C)1 : (C)a[trans ? i + i * w : i + i * w];
+            C s = xii * (C)col[i];
+            for (int k = j + 1; k < i; ++k) s += (C)a[trans ? k + i * w : i + k * w] * (C)col[k];
+            a[trans ? j + i * w : i + j * w] = (double)(-s * xjj);
+        }
+        __syncthreads();
+        if (tid == 0 && !unit) a[j + j * w] = (double)xjj;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal block, Cholesky (Sec. III step 1): one CTA per panel, the block in
+// shared memory in double, right-looking by columns.  A pivot that is not
+// positive is either reported (replace_tau <= 0: the smallest failing column
+// goes to *err_col) or replaced by replace_tau and counted.  The CTA then
+// inverts L_kk in place (arithmetic of the factor's type) and stores the
+// inverse at Dinv + pinv[panel]; the TRSM and the solves multiply by it.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__restrict__ panels,
-                                                    T *__restrict__ L, const double *replace_tau_p,
+                                                    T *__restrict__ L, T *__restrict__ Dinv,
+                                                    const double *replace_tau_p,
                                                     int64_t *err_col, unsigned long long *nrepl)
 {
     extern __shared__ double sm[];
-    __shared__ double s_piv;
+    __shared__ double s_piv, s_inv;
     const double replace_tau = *replace_tau_p;
     const int pid = panels[blockIdx.x];
     const int w = p.pw[pid], h = p.ph[pid];
     T *D = L + p.pval[pid];
+    double *col = sm + w * w;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int idx = tid; idx < w * w; idx += nt) {
         int i = idx % w, j = idx / w;
@@ -80,9 +114,10 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
             d = sqrt(d);
             sm[k + k * w] = d;
             s_piv = d;
+            s_inv = 1.0 / d;
         }
         __syncthreads();
-        const double inv = 1.0 / s_piv;
+        const double inv = s_inv;
         for (int i = k + 1 + tid; i < w; i += nt) sm[i + k * w] *= inv;
         __syncthreads();
         for (int j = k + 1 + warp; j < w; j += nw) {
@@ -95,38 +130,48 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
         int i = idx % w, j = idx / w;
         if (i >= j) D[i + (int64_t)j * h] = (T)sm[idx];
     }
+    __syncthreads();
+    invert_lower_inplace<T>(sm, w, false, false, col);
+    T *Mi = Dinv + p.pinv[pid];
+    for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = (T)sm[idx];
 }
 
 template <typename T>
-void launch_potrf(const DevPlan &p, const int32_t *panels, int count, T *L, const double *replace_tau,
-                  int64_t *err_col, unsigned long long *nrepl, cudaStream_t s)
+void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+                  const double *replace_tau, int64_t *err_col, unsigned long long *nrepl,
+                  cudaStream_t s)
 {
     if (count <= 0) return;
-    const size_t smem = sizeof(double) * kMaxWidth * kMaxWidth;
     static bool once = false;
     if (!once) {
-        cudaFuncSetAttribute(potrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(potrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * (kMaxWidth * kMaxWidth + kMaxWidth)));
         once = true;
     }
-    potrf_kernel<T><<<count, 256, smem, s>>>(p, panels, L, replace_tau, err_col, nrepl);
+    const size_t smem = sizeof(double) * ((size_t)wmax * wmax + wmax);
+    potrf_kernel<T><<<count, 256, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl);
 }
 
 // ---------------------------------------------------------------------------
 // Diagonal block, LU without pivoting (Sec. III: static pivoting): a pivot
 // whose magnitude is below tau becomes sign(pivot) * tau (+tau for 0) and is
-// counted; tau <= 0 turns a zero pivot into an error instead.
+// counted; tau <= 0 turns a zero pivot into an error instead.  The inverses
+// of the unit lower and the upper factor are stored together at Dinv (L^{-1}
+// strictly below the diagonal, U^{-1} on and above it).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) getrf_kernel(DevPlan p, const int32_t *__restrict__ panels,
-                                                    T *__restrict__ L, const double *tau_p,
-                                                    int64_t *err_col, unsigned long long *nrepl)
+                                                    T *__restrict__ L, T *__restrict__ Dinv,
+                                                    const double *tau_p, int64_t *err_col,
+                                                    unsigned long long *nrepl)
 {
     extern __shared__ double sm[];
-    __shared__ double s_piv;
+    __shared__ double s_inv;
     const double tau = *tau_p;
     const int pid = panels[blockIdx.x];
     const int w = p.pw[pid], h = p.ph[pid];
     T *D = L + p.pval[pid];
+    double *col = sm + w * w;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int idx = tid; idx < w * w; idx += nt) {
         int i = idx % w, j = idx / w;
@@ -147,10 +192,10 @@ __global__ void __launch_bounds__(256) getrf_kernel(DevPlan p, const int32_t *__
                 d = 1.0;
             }
             sm[k + k * w] = d;
-            s_piv = d;
+            s_inv = 1.0 / d;
         }
         __syncthreads();
-        const double inv = 1.0 / s_piv;
+        const double inv = s_inv;
         for (int i = k + 1 + tid; i < w; i += nt) sm[i + k * w] *= inv;
         __syncthreads();
         for (int j = k + 1 + warp; j < w; j += nw) {
@@ -163,87 +208,119 @@ __global__ void __launch_bounds__(256) getrf_kernel(DevPlan p, const int32_t *__
         int i = idx % w, j = idx / w;
         D[i + (int64_t)j * h] = (T)sm[idx];
     }
+    __syncthreads();
+    invert_lower_inplace<T>(sm, w, false, true, col);   // unit lower L
+    invert_lower_inplace<T>(sm, w, true, false, col);   // U through U^T
+    T *Mi = Dinv + p.pinv[pid];
+    for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = (T)sm[idx];
 }
 
 template <typename T>
-void launch_getrf(const DevPlan &p, const int32_t *panels, int count, T *L, const double *tau,
-                  int64_t *err_col, unsigned long long *nrepl, cudaStream_t s)
+void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+                  const double *tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s)
 {
     if (count <= 0) return;
-    const size_t smem = sizeof(double) * kMaxWidth * kMaxWidth;
     static bool once = false;
     if (!once) {
-        cudaFuncSetAttribute(getrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(getrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * (kMaxWidth * kMaxWidth + kMaxWidth)));
         once = true;
     }
-    getrf_kernel<T><<<count, 256, smem, s>>>(p, panels, L, tau, err_col, nrepl);
+    const size_t smem = sizeof(double) * ((size_t)wmax * wmax + wmax);
+    getrf_kernel<T><<<count, 256, smem, s>>>(p, panels, L, Dinv, tau, err_col, nrepl);
 }
 
 // ---------------------------------------------------------------------------
-// Panel TRSM (Sec. III step 2): rows [r0, r0+64) of the off-diagonal part,
-// one thread per row, by substitution against the factored diagonal block
-// held packed in shared memory.  Every mode solves Y M^T = X with M lower
-// triangular:  LLT: M = lower(D);  LU_L: M = upper(D)^T (Y U = X);
-// LU_U: M = unit lower(D).
+// Panel TRSM (Sec. III step 2) as a product with the inverted diagonal block:
+// rows [r0, r0+64) of the off-diagonal part X become X B with
+//   LLT : B = L^{-T}           (B(k,j) = Linv(j,k))
+//   LU_L: B = U^{-1}           (B(k,j) = Uinv(k,j))
+//   LU_U: B = L^{-T}, unit L   (B(k,j) = Linv(j,k), 1 on the diagonal)
+// The CTA copies its rows to shared memory first, so writing them back in
+// place is safe; 64 x 64 output tiles, 4 x 4 per thread, K-chunks of 16.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) trsm_kernel(DevPlan p,
-                                                         const RowChunk *__restrict__ chunks,
-                                                         const T *__restrict__ Dsrc,
-                                                         T *__restrict__ X, int mode)
+__global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
+                                                        const T *__restrict__ Dinv,
+                                                        T *__restrict__ X, int mode)
 {
-    extern __shared__ double sm[];
+    extern __shared__ unsigned char smraw[];
+    T *Xs = reinterpret_cast<T *>(smraw);      // Xs[k * 64 + r], k < wpad
+    __shared__ T Bs[16][kUpdTile + 1];
     const RowChunk ch = chunks[blockIdx.x];
     const int pid = ch.panel;
     const int w = p.pw[pid], h = p.ph[pid];
-    const int64_t base = p.pval[pid];
-    double *M = sm;                                   // packed by columns
-    double *Xs = sm + (w * (w + 1)) / 2;              // Xs[c * 64 + r]
-    const T *D = Dsrc + base;
-    const int tid = threadIdx.x;
-    int start = 0;
-    for (int c = 0; c < w; ++c) {
-        for (int j = c + tid; j < w; j += kTrsmRows) {
-            double v = (mode == TRSM_LU_L) ? (double)D[c + (int64_t)j * h]
-                                           : (double)D[j + (int64_t)c * h];
-            if (mode == TRSM_LU_U && j == c) v = 1.0;
-            M[start + (j - c)] = v;
-        }
-        start += w - c;
-    }
+    const int wpad = (w + 15) & ~15;
+    const T *Mi = Dinv + p.pinv[pid];
+    T *Xg = X + p.pval[pid] + ch.r0;
     const int nr = min(kTrsmRows, h - ch.r0);
-    T *Xg = X + base + ch.r0;
-    if (tid < nr)
-        for (int c = 0; c < w; ++c) Xs[c * kTrsmRows + tid] = (double)Xg[tid + (int64_t)c * h];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int e = tid; e < wpad * kTrsmRows; e += 256) {
+        const int r = e & 63, k = e >> 6;
+        Xs[e] = (r < nr && k < w) ? Xg[r + (int64_t)k * h] : (T)0;
+    }
     __syncthreads();
-    if (tid < nr) {
-        int diag = 0;   // packed index of M(j, j)
-        for (int j = 0; j < w; ++j) {
-            double s = Xs[j * kTrsmRows + tid];
-            int idx = j;  // M(j, 0)
-            for (int c = 0; c < j; ++c) {
-                s -= Xs[c * kTrsmRows + tid] * M[idx];
-                idx += w - c - 1;
+    for (int c0 = 0; c0 < w; c0 += kUpdTile) {
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+        for (int k0 = 0; k0 < wpad; k0 += 16) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                const int kk = e >> 6, jj = e & 63;
+                const int k = k0 + kk, j = c0 + jj;
+                T v = (T)0;
+                if (k < w && j < w) {
+                    if (mode == TRSM_LU_L) v = (k <= j) ? Mi[k + j * w] : (T)0;
+                    else if (j > k) v = Mi[j + k * w];
+                    else if (j == k) v = (mode == TRSM_LU_U) ? (T)1 : Mi[j + k * w];
+                }
+                Bs[kk][jj] = v;
             }
-            Xs[j * kTrsmRows + tid] = s / M[diag];
-            diag += w - j;
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                T av[4], bv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) av[a] = Xs[(k0 + kk) * 64 + tx + 16 * a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+            }
+            __syncthreads();
         }
-        for (int c = 0; c < w; ++c) Xg[tid + (int64_t)c * h] = (T)Xs[c * kTrsmRows + tid];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int r = tx + 16 * a;
+            if (r >= nr) continue;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int j = c0 + ty + 16 * b;
+                if (j < w) Xg[r + (int64_t)j * h] = acc[a][b];
+            }
+        }
     }
 }
 
 template <typename T>
-void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, const T *Dsrc, T *X,
-                 int mode, cudaStream_t s)
+void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
+                 T *X, int mode, cudaStream_t s)
 {
     if (count <= 0) return;
-    const size_t smem = sizeof(double) * ((kMaxWidth * (kMaxWidth + 1)) / 2 + kMaxWidth * kTrsmRows);
     static bool once = false;
     if (!once) {
-        cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(trsm_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * kMaxWidth * kTrsmRows));
         once = true;
     }
-    trsm_kernel<T><<<count, kTrsmRows, smem, s>>>(p, chunks, Dsrc, X, mode);
+    const size_t smem = sizeof(T) * (size_t)((wmax + 15) & ~15) * kTrsmRows;
+    trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,12 +488,12 @@ void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A,
 // explicit instantiations
 template void launch_assemble<double>(int64_t, const double *, const int64_t *, double *, double *, cudaStream_t);
 template void launch_assemble<float>(int64_t, const double *, const int64_t *, float *, float *, cudaStream_t);
-template void launch_potrf<double>(const DevPlan &, const int32_t *, int, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_potrf<float>(const DevPlan &, const int32_t *, int, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_getrf<double>(const DevPlan &, const int32_t *, int, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_getrf<float>(const DevPlan &, const int32_t *, int, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, const double *, double *, int, cudaStream_t);
-template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, const float *, float *, int, cudaStream_t);
+template void launch_potrf<double>(const DevPlan &, const int32_t *, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_potrf<float>(const DevPlan &, const int32_t *, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_getrf<double>(const DevPlan &, const int32_t *, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_getrf<float>(const DevPlan &, const int32_t *, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, cudaStream_t);
+template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, cudaStream_t);
 template void launch_update<double>(const DevPlan &, const DevTask *, const UpdTile *, int, const double *, const double *, double *, int, int, cudaStream_t);
 template void launch_update<float>(const DevPlan &, const DevTask *, const UpdTile *, int, const float *, const float *, float *, int, int, cudaStream_t);
 

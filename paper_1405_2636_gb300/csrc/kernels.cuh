@@ -16,6 +16,7 @@ struct DevPlan {
     const int64_t *prow;    // row-list offsets
     const int32_t *rows;    // permuted row indices
     const int64_t *pval;    // value offsets
+    const int64_t *pinv;    // offsets of the inverted diagonal blocks (w x w, column-major)
     const int32_t *relmap;  // target row of each updated source row, per task
 };
 
@@ -52,16 +53,17 @@ void launch_assemble(int64_t nnz, const double *vals, const int64_t *amap, T *L,
                      cudaStream_t s);
 
 template <typename T>
-void launch_potrf(const DevPlan &p, const int32_t *panels, int count, T *L, const double *replace_tau,
-                  int64_t *err_col, unsigned long long *nrepl, cudaStream_t s);
+void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+                  const double *replace_tau, int64_t *err_col, unsigned long long *nrepl,
+                  cudaStream_t s);
 
 template <typename T>
-void launch_getrf(const DevPlan &p, const int32_t *panels, int count, T *L, const double *tau,
-                  int64_t *err_col, unsigned long long *nrepl, cudaStream_t s);
+void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+                  const double *tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s);
 
 template <typename T>
-void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, const T *Dsrc, T *X,
-                 int mode, cudaStream_t s);
+void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
+                 T *X, int mode, cudaStream_t s);
 
 template <typename T>
 void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles, int count,
@@ -73,25 +75,28 @@ void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A,
                               const int32_t *colmap, int lower, cudaStream_t s);
 
 // ---- solves ----------------------------------------------------------------
+// Vectors in the permuted numbering are of the factor's type T, column-major
+// n x nrhs.  Forward: Z_p = D_p^{-1} Y_p, then Y(rows below) -= L_off Z_p.
+// Backward: T_p += L_off^T X(rows below) (split over row chunks), then
+// X_p = D_p^{-T} (Z_p - T_p)  (LU: U_p^{-1} (Z_p - T_p) with the U^T panel).
+template <typename T>
 void launch_permute_in(int64_t n, int nrhs, const double *B, int64_t ldb, const int64_t *perm,
-                       double *Y, cudaStream_t s);
-void launch_permute_out(int64_t n, int nrhs, const double *Y, const int64_t *perm, double *X,
+                       T *Y, cudaStream_t s);
+template <typename T>
+void launch_permute_out(int64_t n, int nrhs, const T *Y, const int64_t *perm, double *X,
                         int64_t ldx, cudaStream_t s);
-
-// Forward: diagonal solve per panel, then the off-diagonal scatter.
 template <typename T>
-void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, const T *L, int unit,
-                     double *Y, int nrhs, cudaStream_t s);
+void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const T *Dinv,
+                     int unit, const T *Y, T *Z, int nrhs, cudaStream_t s);
 template <typename T>
-void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, const T *L, double *Y,
-                    int nrhs, cudaStream_t s);
-// Backward: off-diagonal gather (partial sums per chunk), then the diagonal solve.
+void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *L,
+                    const T *Z, T *Y, int nrhs, cudaStream_t s);
 template <typename T>
-void launch_bwd_off(const DevPlan &p, const RowChunk *chunks, int count, const T *Lop,
-                    double *Y, int nrhs, cudaStream_t s);
+void launch_bwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Lop,
+                    const T *X, T *Tacc, int nrhs, cudaStream_t s);
 template <typename T>
-void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, const T *L, int upper_from_d,
-                     double *Y, int nrhs, cudaStream_t s);
+void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const T *Dinv,
+                     int lu, const T *Z, const T *Tacc, T *X, int nrhs, cudaStream_t s);
 
 // ---- residuals and norms ---------------------------------------------------
 // R = B - A X for nrhs columns (A by rows, original numbering); per column

@@ -8,19 +8,22 @@
 namespace spx {
 
 constexpr int kRhsChunk = 16;
+constexpr int kDiagRows = 32;   // rows of D^{-1} one CTA of the diagonal products handles
 
+template <typename T>
 __global__ void permute_in_kernel(int64_t n, int nrhs, const double *__restrict__ B, int64_t ldb,
-                                  const int64_t *__restrict__ perm, double *__restrict__ Y)
+                                  const int64_t *__restrict__ perm, T *__restrict__ Y)
 {
     const int64_t total = n * nrhs;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / n, k = e - c * n;
-        Y[e] = B[perm[k] + c * ldb];
+        Y[e] = (T)B[perm[k] + c * ldb];
     }
 }
 
-__global__ void permute_out_kernel(int64_t n, int nrhs, const double *__restrict__ Y,
+template <typename T>
+__global__ void permute_out_kernel(int64_t n, int nrhs, const T *__restrict__ Y,
                                    const int64_t *__restrict__ perm, double *__restrict__ X,
                                    int64_t ldx)
 {
@@ -28,7 +31,7 @@ __global__ void permute_out_kernel(int64_t n, int nrhs, const double *__restrict
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / n, k = e - c * n;
-        X[perm[k] + c * ldx] = Y[e];
+        X[perm[k] + c * ldx] = (double)Y[e];
     }
 }
 
@@ -40,64 +43,70 @@ static unsigned grid_for(int64_t total)
     return (unsigned)b;
 }
 
+template <typename T>
 void launch_permute_in(int64_t n, int nrhs, const double *B, int64_t ldb, const int64_t *perm,
-                       double *Y, cudaStream_t s)
+                       T *Y, cudaStream_t s)
 {
-    permute_in_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, B, ldb, perm, Y);
+    permute_in_kernel<T><<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, B, ldb, perm, Y);
 }
 
-void launch_permute_out(int64_t n, int nrhs, const double *Y, const int64_t *perm, double *X,
+template <typename T>
+void launch_permute_out(int64_t n, int nrhs, const T *Y, const int64_t *perm, double *X,
                         int64_t ldx, cudaStream_t s)
 {
-    permute_out_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, Y, perm, X, ldx);
+    permute_out_kernel<T><<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, Y, perm, X, ldx);
 }
 
 // ---------------------------------------------------------------------------
-// Forward, diagonal block: y_p <- D_lower^{-1} y_p (unit: LU's L).
+// Forward, diagonal block: Z_p = Linv_p Y_p, rows [32 y, 32 y + 32) of the
+// panel per CTA (grid.y).  LU: Linv is unit (the diagonal slot holds U^{-1}).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) fwd_diag_kernel(DevPlan p, const int32_t *__restrict__ panels,
-                                                       const T *__restrict__ L, int unit,
-                                                       double *__restrict__ Y, int nrhs)
+                                                       const T *__restrict__ Dinv, int unit,
+                                                       const T *__restrict__ Y, T *__restrict__ Z,
+                                                       int nrhs)
 {
-    __shared__ double ys[kMaxWidth * kRhsChunk];
+    extern __shared__ unsigned char smraw[];
+    T *ys = reinterpret_cast<T *>(smraw);       // ys[c * w + k]
     const int pid = panels[blockIdx.x];
-    const int w = p.pw[pid], h = p.ph[pid];
-    const T *D = L + p.pval[pid];
+    const int w = p.pw[pid];
+    const int i0 = blockIdx.y * kDiagRows;
+    if (i0 >= w) return;
+    const T *Mi = Dinv + p.pinv[pid];
     const int64_t f = p.pfcol[pid], n = p.n;
     const int tid = threadIdx.x;
+    const int li = tid & 31, cg = tid >> 5;     // row within the block, column group of 8
+    const int i = i0 + li;
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
-        for (int e = tid; e < w * nc; e += blockDim.x) {
-            const int k = e % w, c = e / w;
+        const int kend = min(w, i0 + kDiagRows);   // rows of Linv below i0+32 are not needed
+        for (int e = tid; e < kend * nc; e += blockDim.x) {
+            const int k = e % kend, c = e / kend;
             ys[c * w + k] = Y[f + k + (int64_t)(c0 + c) * n];
         }
         __syncthreads();
-        for (int j = 0; j < w; ++j) {
-            if (!unit && tid < nc) ys[tid * w + j] /= (double)D[j + (int64_t)j * h];
-            __syncthreads();
-            const int rest = w - j - 1;
-            for (int e = tid; e < rest * nc; e += blockDim.x) {
-                const int i = j + 1 + e % rest, c = e / rest;
-                ys[c * w + i] -= (double)D[i + (int64_t)j * h] * ys[c * w + j];
+        if (i < w) {
+            for (int c = cg; c < nc; c += 8) {
+                T acc = unit ? ys[c * w + i] : (T)0;
+                const int kl = unit ? i : i + 1;
+                for (int k = 0; k < kl; ++k) acc += Mi[i + k * w] * ys[c * w + k];
+                Z[f + i + (int64_t)(c0 + c) * n] = acc;
             }
-            __syncthreads();
-        }
-        for (int e = tid; e < w * nc; e += blockDim.x) {
-            const int k = e % w, c = e / w;
-            Y[f + k + (int64_t)(c0 + c) * n] = ys[c * w + k];
         }
         __syncthreads();
     }
 }
 
-// Forward, off-diagonal rows of one chunk: y[rows(i)] -= L(i, :) y_p.
+// Forward, off-diagonal rows of one chunk: Y[rows(i)] -= L(i, :) Z_p.
 template <typename T>
 __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                       const T *__restrict__ L,
-                                                      double *__restrict__ Y, int nrhs)
+                                                      const T *__restrict__ Z, T *__restrict__ Y,
+                                                      int nrhs)
 {
-    __shared__ double yp[kMaxWidth * kRhsChunk];
+    extern __shared__ unsigned char smraw[];
+    T *zp = reinterpret_cast<T *>(smraw);       // zp[c * w + k]
     const RowChunk ch = chunks[blockIdx.x];
     const int pid = ch.panel;
     const int w = p.pw[pid], h = p.ph[pid];
@@ -111,17 +120,17 @@ __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk 
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < w * nc; e += blockDim.x) {
             const int k = e % w, c = e / w;
-            yp[c * w + k] = Y[f + k + (int64_t)(c0 + c) * n];
+            zp[c * w + k] = Z[f + k + (int64_t)(c0 + c) * n];
         }
         __syncthreads();
         if (i < h) {
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            T acc[4] = {(T)0, (T)0, (T)0, (T)0};
             for (int k = 0; k < w; ++k) {
-                const double l = (double)Pn[i + (int64_t)k * h];
+                const T l = Pn[i + (int64_t)k * h];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int c = g + 4 * q;
-                    if (c < nc) acc[q] += l * yp[c * w + k];
+                    if (c < nc) acc[q] += l * zp[c * w + k];
                 }
             }
             const int64_t gi = rows[i];
@@ -135,113 +144,154 @@ __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk 
     }
 }
 
-// Backward, off-diagonal rows of one chunk: y_p -= Lop(chunk, :)^T y[rows(chunk)].
+// Backward, off-diagonal rows of one chunk: Tacc_p += Lop(chunk, :)^T X[rows(chunk)].
 template <typename T>
 __global__ void __launch_bounds__(256) bwd_off_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                       const T *__restrict__ Lop,
-                                                      double *__restrict__ Y, int nrhs)
+                                                      const T *__restrict__ X,
+                                                      T *__restrict__ Tacc, int nrhs)
 {
-    __shared__ double ys[64 * kRhsChunk];
+    extern __shared__ unsigned char smraw[];
+    T *ls = reinterpret_cast<T *>(smraw);            // ls[k * 65 + r]
     const RowChunk ch = chunks[blockIdx.x];
     const int pid = ch.panel;
     const int w = p.pw[pid], h = p.ph[pid];
+    T *xs = ls + (size_t)w * 65;                      // xs[c * 64 + r]
     const T *Pn = Lop + p.pval[pid];
     const int64_t f = p.pfcol[pid], n = p.n;
     const int32_t *rows = p.rows + p.prow[pid];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int nr = min(64, h - ch.r0);
+    for (int e = tid; e < w * 64; e += blockDim.x) {
+        const int r = e & 63, k = e >> 6;
+        ls[k * 65 + r] = r < nr ? Pn[ch.r0 + r + (int64_t)k * h] : (T)0;
+    }
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < 64 * nc; e += blockDim.x) {
             const int r = e & 63, c = e >> 6;
-            ys[c * 64 + r] = (r < nr) ? Y[rows[ch.r0 + r] + (int64_t)(c0 + c) * n] : 0.0;
+            xs[c * 64 + r] = (r < nr) ? X[rows[ch.r0 + r] + (int64_t)(c0 + c) * n] : (T)0;
         }
         __syncthreads();
-        for (int k = warp; k < w; k += 8) {
-            const double l0 = lane < nr ? (double)Pn[ch.r0 + lane + (int64_t)k * h] : 0.0;
-            const double l1 = lane + 32 < nr ? (double)Pn[ch.r0 + lane + 32 + (int64_t)k * h] : 0.0;
-            for (int c = 0; c < nc; ++c) {
-                double v = l0 * ys[c * 64 + lane] + l1 * ys[c * 64 + lane + 32];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                if (lane == 0) atomicAdd(Y + f + k + (int64_t)(c0 + c) * n, -v);
-            }
+        for (int e = tid; e < w * nc; e += blockDim.x) {
+            const int k = e % w, c = e / w;
+            T acc = (T)0;
+#pragma unroll 8
+            for (int r = 0; r < 64; ++r) acc += ls[k * 65 + r] * xs[c * 64 + r];
+            atomicAdd(Tacc + f + k + (int64_t)(c0 + c) * n, acc);
         }
         __syncthreads();
     }
 }
 
-// Backward, diagonal block: y_p <- M^{-1} y_p with M upper triangular:
-// M = lower(D)^T (Cholesky) or upper(D) (LU's U).
+// Backward, diagonal block: X_p = M (Z_p - Tacc_p) with M = Linv^T (Cholesky)
+// or U^{-1} (LU), rows [32 y, 32 y + 32) per CTA.
 template <typename T>
 __global__ void __launch_bounds__(256) bwd_diag_kernel(DevPlan p, const int32_t *__restrict__ panels,
-                                                       const T *__restrict__ L, int upper_from_d,
-                                                       double *__restrict__ Y, int nrhs)
+                                                       const T *__restrict__ Dinv, int lu,
+                                                       const T *__restrict__ Z,
+                                                       const T *__restrict__ Tacc,
+                                                       T *__restrict__ X, int nrhs)
 {
-    __shared__ double ys[kMaxWidth * kRhsChunk];
+    extern __shared__ unsigned char smraw[];
+    T *ys = reinterpret_cast<T *>(smraw);          // ys[c * w + k]
     const int pid = panels[blockIdx.x];
-    const int w = p.pw[pid], h = p.ph[pid];
-    const T *D = L + p.pval[pid];
+    const int w = p.pw[pid];
+    const int i0 = blockIdx.y * kDiagRows;
+    if (i0 >= w) return;
+    T *ms = ys + (size_t)w * kRhsChunk;            // ms[li * (w + 1) + k] = M(i0 + li, k)
+    const T *Mi = Dinv + p.pinv[pid];
     const int64_t f = p.pfcol[pid], n = p.n;
     const int tid = threadIdx.x;
+    const int li = tid & 31, cg = tid >> 5;
+    const int i = i0 + li;
+    const int nrow = min(kDiagRows, w - i0);
+    // M(i, k) for k >= i: Cholesky Linv(k, i) = Mi[k + i w]; LU Uinv(i, k) = Mi[i + k w]
+    for (int e = tid; e < nrow * w; e += blockDim.x) {
+        int a, k;
+        if (lu) { a = e % nrow; k = e / nrow; } else { k = e % w; a = e / w; }
+        const int ii = i0 + a;
+        T v = (T)0;
+        if (k >= ii) v = lu ? Mi[ii + k * w] : Mi[k + ii * w];
+        ms[a * (w + 1) + k] = v;
+    }
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < w * nc; e += blockDim.x) {
             const int k = e % w, c = e / w;
-            ys[c * w + k] = Y[f + k + (int64_t)(c0 + c) * n];
+            const int64_t g = f + k + (int64_t)(c0 + c) * n;
+            ys[c * w + k] = Z[g] - Tacc[g];
         }
         __syncthreads();
-        for (int j = w - 1; j >= 0; --j) {
-            if (tid < nc) ys[tid * w + j] /= (double)D[j + (int64_t)j * h];
-            __syncthreads();
-            for (int e = tid; e < j * nc; e += blockDim.x) {
-                const int i = e % j, c = e / j;
-                const double m = upper_from_d ? (double)D[i + (int64_t)j * h]
-                                              : (double)D[j + (int64_t)i * h];
-                ys[c * w + i] -= m * ys[c * w + j];
+        if (li < nrow) {
+            for (int c = cg; c < nc; c += 8) {
+                T acc = (T)0;
+                for (int k = i; k < w; ++k) acc += ms[li * (w + 1) + k] * ys[c * w + k];
+                X[f + i + (int64_t)(c0 + c) * n] = acc;
             }
-            __syncthreads();
-        }
-        for (int e = tid; e < w * nc; e += blockDim.x) {
-            const int k = e % w, c = e / w;
-            Y[f + k + (int64_t)(c0 + c) * n] = ys[c * w + k];
         }
         __syncthreads();
     }
 }
 
 template <typename T>
-void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, const T *L, int unit,
-                     double *Y, int nrhs, cudaStream_t s)
+void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const T *Dinv,
+                     int unit, const T *Y, T *Z, int nrhs, cudaStream_t s)
 {
-    if (count > 0) fwd_diag_kernel<T><<<count, 256, 0, s>>>(p, panels, L, unit, Y, nrhs);
+    if (count <= 0) return;
+    dim3 grid(count, (wmax + kDiagRows - 1) / kDiagRows);
+    fwd_diag_kernel<T><<<grid, 256, sizeof(T) * wmax * kRhsChunk, s>>>(p, panels, Dinv, unit, Y, Z, nrhs);
 }
+
 template <typename T>
-void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, const T *L, double *Y,
-                    int nrhs, cudaStream_t s)
+void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *L,
+                    const T *Z, T *Y, int nrhs, cudaStream_t s)
 {
-    if (count > 0) fwd_off_kernel<T><<<count, 256, 0, s>>>(p, chunks, L, Y, nrhs);
+    if (count <= 0) return;
+    fwd_off_kernel<T><<<count, 256, sizeof(T) * wmax * kRhsChunk, s>>>(p, chunks, L, Z, Y, nrhs);
 }
+
 template <typename T>
-void launch_bwd_off(const DevPlan &p, const RowChunk *chunks, int count, const T *Lop, double *Y,
-                    int nrhs, cudaStream_t s)
+void launch_bwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Lop,
+                    const T *X, T *Tacc, int nrhs, cudaStream_t s)
 {
-    if (count > 0) bwd_off_kernel<T><<<count, 256, 0, s>>>(p, chunks, Lop, Y, nrhs);
+    if (count <= 0) return;
+    static bool once = false;
+    const size_t most = sizeof(T) * ((size_t)kMaxWidth * 65 + 64 * kRhsChunk);
+    if (!once) {
+        cudaFuncSetAttribute(bwd_off_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        once = true;
+    }
+    const size_t smem = sizeof(T) * ((size_t)wmax * 65 + 64 * kRhsChunk);
+    bwd_off_kernel<T><<<count, 256, smem, s>>>(p, chunks, Lop, X, Tacc, nrhs);
 }
+
 template <typename T>
-void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, const T *L,
-                     int upper_from_d, double *Y, int nrhs, cudaStream_t s)
+void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const T *Dinv,
+                     int lu, const T *Z, const T *Tacc, T *X, int nrhs, cudaStream_t s)
 {
-    if (count > 0) bwd_diag_kernel<T><<<count, 256, 0, s>>>(p, panels, L, upper_from_d, Y, nrhs);
+    if (count <= 0) return;
+    static bool once = false;
+    const size_t most = sizeof(T) * ((size_t)kMaxWidth * kRhsChunk + kDiagRows * (kMaxWidth + 1));
+    if (!once) {
+        cudaFuncSetAttribute(bwd_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        once = true;
+    }
+    dim3 grid(count, (wmax + kDiagRows - 1) / kDiagRows);
+    const size_t smem = sizeof(T) * ((size_t)wmax * kRhsChunk + kDiagRows * (wmax + 1));
+    bwd_diag_kernel<T><<<grid, 256, smem, s>>>(p, panels, Dinv, lu, Z, Tacc, X, nrhs);
 }
 
 // ---------------------------------------------------------------------------
 // Residual R = B - A X (A by rows in the original numbering) with the
 // per-column infinity norms of r, x and b.
 // ---------------------------------------------------------------------------
+// NaN compares as +inf so that a broken solution can never look converged.
+__device__ __forceinline__ double nan_to_inf(double v) { return v != v ? INFINITY : v; }
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *a, double v)
 {
-    atomicMax(a, (unsigned long long)__double_as_longlong(v));
+    atomicMax(a, (unsigned long long)__double_as_longlong(nan_to_inf(v)));
 }
 
 __global__ void __launch_bounds__(256) residual_kernel(int64_t n, int nrhs,
@@ -264,9 +314,9 @@ __global__ void __launch_bounds__(256) residual_kernel(int64_t n, int nrhs,
             const double b = B[i + c * ldb];
             r = b - s;
             R[i + c * n] = r;
-            r = fabs(r);
-            ax = fabs(X[i + c * ldx]);
-            ab = fabs(b);
+            r = nan_to_inf(fabs(r));
+            ax = nan_to_inf(fabs(X[i + c * ldx]));
+            ab = nan_to_inf(fabs(b));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -298,6 +348,7 @@ __global__ void row_abs_sum_kernel(int64_t n, const int64_t *__restrict__ rp,
     double s = 0.0;
     if (i < n)
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e) s += fabs(vals[src[e]]);
+    s = nan_to_inf(s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, s);
@@ -325,13 +376,17 @@ void launch_axpy_cols(int64_t n, int nrhs, const double *D, double *X, int64_t l
     axpy_cols_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, D, X, ldx);
 }
 
-template void launch_fwd_diag<double>(const DevPlan &, const int32_t *, int, const double *, int, double *, int, cudaStream_t);
-template void launch_fwd_diag<float>(const DevPlan &, const int32_t *, int, const float *, int, double *, int, cudaStream_t);
-template void launch_fwd_off<double>(const DevPlan &, const RowChunk *, int, const double *, double *, int, cudaStream_t);
-template void launch_fwd_off<float>(const DevPlan &, const RowChunk *, int, const float *, double *, int, cudaStream_t);
-template void launch_bwd_off<double>(const DevPlan &, const RowChunk *, int, const double *, double *, int, cudaStream_t);
-template void launch_bwd_off<float>(const DevPlan &, const RowChunk *, int, const float *, double *, int, cudaStream_t);
-template void launch_bwd_diag<double>(const DevPlan &, const int32_t *, int, const double *, int, double *, int, cudaStream_t);
-template void launch_bwd_diag<float>(const DevPlan &, const int32_t *, int, const float *, int, double *, int, cudaStream_t);
+template void launch_permute_in<double>(int64_t, int, const double *, int64_t, const int64_t *, double *, cudaStream_t);
+template void launch_permute_out<double>(int64_t, int, const double *, const int64_t *, double *, int64_t, cudaStream_t);
+template void launch_fwd_diag<double>(const DevPlan &, const int32_t *, int, int, const double *, int, const double *, double *, int, cudaStream_t);
+template void launch_fwd_off<double>(const DevPlan &, const RowChunk *, int, int, const double *, const double *, double *, int, cudaStream_t);
+template void launch_bwd_off<double>(const DevPlan &, const RowChunk *, int, int, const double *, const double *, double *, int, cudaStream_t);
+template void launch_bwd_diag<double>(const DevPlan &, const int32_t *, int, int, const double *, int, const double *, const double *, double *, int, cudaStream_t);
+template void launch_permute_in<float>(int64_t, int, const double *, int64_t, const int64_t *, float *, cudaStream_t);
+template void launch_permute_out<float>(int64_t, int, const float *, const int64_t *, double *, int64_t, cudaStream_t);
+template void launch_fwd_diag<float>(const DevPlan &, const int32_t *, int, int, const float *, int, const float *, float *, int, cudaStream_t);
+template void launch_fwd_off<float>(const DevPlan &, const RowChunk *, int, int, const float *, const float *, float *, int, cudaStream_t);
+template void launch_bwd_off<float>(const DevPlan &, const RowChunk *, int, int, const float *, const float *, float *, int, cudaStream_t);
+template void launch_bwd_diag<float>(const DevPlan &, const int32_t *, int, int, const float *, int, const float *, const float *, float *, int, cudaStream_t);
 
 }  // namespace spx

@@ -66,6 +66,9 @@ struct Plan {
     int64_t nnz_stored = 0;
     double flops_stored = 0.0;
     double update_flops = 0.0;
+    // algorithmic work per kernel class (flops; element traffic, x element size = bytes)
+    double diag_flops = 0.0, trsm_flops = 0.0;
+    double diag_elems = 0.0, trsm_elems = 0.0, update_elems = 0.0;
     double analyze_ms = 0.0;
 };
 

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "SPX_OK", 1: "SPX_ERR_ARG", 2: "SPX_ERR_ALLOC", 3: "SPX_ERR_C
 # Every symbol include/spx.h declares.
 EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_factorize",
             "spx_solve", "spx_get_info", "spx_get_perm", "spx_get_factor", "spx_last_error",
-            "spx_free", "spx_update"]
+            "spx_free", "spx_update", "spx_set_profiling", "spx_get_kernel_stats"]
 
 
 class spx_options(ctypes.Structure):
@@ -59,11 +59,24 @@ class spx_info(ctypes.Structure):
         "n", "nnz_a", "nnz_l", "nnz_stored", "factor_bytes", "nsupernodes", "npanels",
         "nlevels", "nupdates", "bad_col", "npivot_repl")] + [
         ("method", ctypes.c_int32), ("precision", ctypes.c_int32)] + [
-        (name, ctypes.c_double) for name in (
-            "flops", "flops_stored", "update_flops", "analyze_ms", "factor_ms", "solve_ms")]
+        (name, ctypes.c_double) for name in ("flops", "flops_stored", "update_flops")] + [
+        ("launches_factor", ctypes.c_int64), ("launches_solve", ctypes.c_int64)] + [
+        (name, ctypes.c_double) for name in ("analyze_ms", "factor_ms", "solve_ms")]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+KERNEL_CLASSES = ["assemble", "diag", "trsm", "update"]
+
+
+class spx_kernel_stats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4),
+                ("flops", ctypes.c_double * 4), ("bytes", ctypes.c_double * 4)]
+
+    def as_dict(self) -> dict:
+        return {c: {"ms": self.ms[i], "launches": self.launches[i], "flops": self.flops[i],
+                    "bytes": self.bytes[i]} for i, c in enumerate(KERNEL_CLASSES)}
 
 
 _lib = None
@@ -93,11 +106,13 @@ def load():
     lib.spx_get_factor.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.spx_last_error.argtypes = [_vp]
     lib.spx_last_error.restype = ctypes.c_char_p
+    lib.spx_set_profiling.argtypes = [_vp, ctypes.c_int]
+    lib.spx_get_kernel_stats.argtypes = [_vp, ctypes.POINTER(spx_kernel_stats)]
     lib.spx_free.argtypes = [_vp]
     lib.spx_free.restype = None
     lib.spx_update.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]
     for name in ("spx_analyze", "spx_factorize", "spx_solve", "spx_get_info", "spx_get_perm",
-                 "spx_get_factor", "spx_update"):
+                 "spx_get_factor", "spx_update", "spx_set_profiling", "spx_get_kernel_stats"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -220,6 +235,14 @@ class Handle:
         i = spx_info()
         _check(load().spx_get_info(self._h, ctypes.byref(i)), self._h)
         return i.as_dict()
+
+    def set_profiling(self, on: bool = True):
+        _check(load().spx_set_profiling(self._h, 1 if on else 0), self._h)
+
+    def kernel_stats(self) -> dict:
+        k = spx_kernel_stats()
+        _check(load().spx_get_kernel_stats(self._h, ctypes.byref(k)), self._h)
+        return k.as_dict()
 
     def perm(self) -> np.ndarray:
         p = np.empty(self.n, dtype=np.int64)
