@@ -37,6 +37,47 @@ WORKLOAD = "diffusion3d_64^3_7pt_expN01_16rhs"
 FP64_ALU_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9        # 2 DFMA / clk / SM
 FP32_ALU_PEAK_GFLOPS = 152 * 128 * 2 * 2.07e9 / 1e9      # 128 FFMA / clk / SM
 L2_FLUSH_BYTES = 256 << 20
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25                       # nominal dense tensor rates
+
+
+def measured_peaks() -> dict:
+    """HBM GB/s and bf16 TFLOP/s measured on this machine (generated file)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "of measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "of fallback"}
+
+
+def class_roofline(cls: str, st: dict, mode: str, peaks: dict) -> dict:
+    """Roofline of one kernel class from its algorithmic work and device time."""
+    ms = st["ms"]
+    out = {"kernel_class": cls, "launches": st["launches"], "device_ms": ms,
+           "algorithmic_flops": st["flops"], "algorithmic_bytes": st["bytes"], "traffic": None}
+    if ms <= 0:
+        return out
+    if cls in ("assemble", "update_tc"):
+        ach = st["bytes"] / (ms / 1e3) / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "peak_source": peaks["source"]})
+        if cls == "update_tc":
+            tpeak = peaks["bf16_tflops"] * (1.0 if mode == "bf16" else NOMINAL_TF32_OVER_BF16)
+            tach = st["flops"] / (ms / 1e3) / 1e12
+            out["tensor"] = {"achieved_tflops": tach, "peak_tflops": tpeak, "frac": tach / tpeak,
+                             "peak_source": ("measured bf16" if mode == "bf16" else
+                                             "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)")}
+        return out
+    fp64_arith = mode == "fp64" or cls == "diag"
+    peak = FP64_ALU_PEAK_GFLOPS if fp64_arith else FP32_ALU_PEAK_GFLOPS
+    ach = st["flops"] / (ms / 1e3) / 1e9
+    out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
+                "frac": ach / peak,
+                "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz" if fp64_arith
+                                else "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz")})
+    return out
 
 
 def _args():
@@ -45,8 +86,10 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="spx", choices=["spx", "reference"])
-    ap.add_argument("--modes", default="fp64,fp32")
+    ap.add_argument("--modes", default="fp64,fp32,tf32,bf16")
     ap.add_argument("--grid", default="64,64,64")
+    ap.add_argument("--max-width", type=int, default=64,
+                    help="split supernodes wider than this (panel width)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     return ap.parse_args()
@@ -219,7 +262,8 @@ def main():
     colptr, rowind, vals = inputs.csc_arrays(A)
     n = A.shape[0]
     B = inputs.rhs(n, NRHS, SEED)
-    h = spx.analyze(colptr, rowind, "llt", ordering=spx.SPX_ORDER_GRID, grid=grid)
+    h = spx.analyze(colptr, rowind, "llt", ordering=spx.SPX_ORDER_GRID, grid=grid,
+                    max_width=args.max_width)
     info0 = h.info()
     flops = info0["flops"]
 
@@ -318,19 +362,15 @@ def main():
     ok = [m for m in modes if results[m]["converged"]]
     head = min(ok, key=lambda m: results[m]["ms_per_step"]) if ok else modes[0]
     R = results[head]
-    ks = R["kernel_stats"]["update"]
-    esz_mode = "fp64" if head == "fp64" else "fp32"
-    peak = FP64_ALU_PEAK_GFLOPS if esz_mode == "fp64" else FP32_ALU_PEAK_GFLOPS
-    achieved = ks["flops"] / (ks["ms"] / 1e3) / 1e9 if ks["ms"] > 0 else 0.0
-    roofline = {"kernel": "update_kernel (supernodal update with fused scatter)",
-                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                "frac": achieved / peak,
-                "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
-                                if esz_mode == "fp64" else
-                                "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"),
-                "traffic": None,
-                "launches": ks["launches"], "algorithmic_flops": ks["flops"],
-                "algorithmic_bytes": ks["bytes"], "device_ms": ks["ms"]}
+    peaks = measured_peaks()
+    rooflines = {c: class_roofline(c, st, head, peaks) for c, st in R["kernel_stats"].items()
+                 if st["ms"] > 0}
+    dominant = max(rooflines, key=lambda c: rooflines[c]["device_ms"])
+    roofline = dict(rooflines[dominant])
+    roofline["kernel"] = {"diag": "potrf_kernel (FP64 diagonal blocks)",
+                          "trsm": "trsm_gemm_kernel", "update": "update_kernel (CUDA cores)",
+                          "update_tc": "update_tc_kernel (tcgen05)",
+                          "assemble": "assemble_kernel"}[dominant]
 
     if rank != 0:
         if world > 1:
@@ -351,12 +391,14 @@ def main():
                    "seed": SEED, "grid": list(grid), "ordering": "geometric nested dissection",
                    "nnz_l": info0["nnz_l"], "flops_exact": flops,
                    "panels": info0["npanels"], "levels": info0["nlevels"],
+                   "max_width": args.max_width,
                    "headline_mode": head, "l2": "flushed between timed steps (256 MiB write); "
                    "the 1.3 GB factor also exceeds L2", "parallelism": f"replicas x{world}"},
         "modes": {m: {k: v for k, v in results[m].items() if k not in ("kernel_stats",)}
                   for m in modes},
         "kernel_stats": {m: results[m]["kernel_stats"] for m in modes},
         "roofline": roofline,
+        "rooflines": rooflines,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GFlop/s",
                 "h2d_bytes_per_step": int(8 * colptr[-1] + 8 * n * NRHS),

@@ -162,6 +162,13 @@ spx_status spx_get_perm(spx_handle h, int64_t *perm);
 spx_status spx_get_factor(spx_handle h, const int64_t *Lp, const int32_t *Li, double *Lx,
                           double *Ut);
 
+/* Copy the panel structure (host arrays of info.npanels entries; any may be
+ * NULL): first column, width, height (rows of the panel including its
+ * diagonal block), level in the panel elimination tree (leaves 0) and parent
+ * panel (-1 for a root).  Panels are numbered in column order. */
+spx_status spx_get_panels(spx_handle h, int64_t *first_col, int32_t *width, int32_t *height,
+                          int32_t *level, int32_t *parent);
+
 /* Message for the last failing call on h (or on handle creation when h is
  * NULL).  The string stays valid until the next call on h. */
 const char *spx_last_error(spx_handle h);
@@ -171,8 +178,9 @@ enum {
     SPX_K_ASSEMBLE = 0,   /* zeroing and scattering A into the panels, ||A||_inf */
     SPX_K_DIAG = 1,       /* diagonal-block POTRF / GETRF */
     SPX_K_TRSM = 2,       /* panel triangular solves */
-    SPX_K_UPDATE = 3,     /* supernodal updates with fused scatter */
-    SPX_K_CLASSES = 4
+    SPX_K_UPDATE = 3,     /* supernodal updates with fused scatter, CUDA cores */
+    SPX_K_UPDATE_TC = 4,  /* supernodal updates with fused scatter, tensor cores (tcgen05) */
+    SPX_K_CLASSES = 5
 };
 
 typedef struct {

@@ -41,6 +41,9 @@ struct spx_handle_s {
     int32_t *d_csr_col = nullptr;
 
     std::vector<int32_t> lvl_wmax;    // widest panel per level
+    // panels of a level sorted by width class (kWidthClass); class c of level l
+    // is d_level_panels[cls_ptr[l * kNumClasses + c] .. cls_ptr[l * kNumClasses + c + 1])
+    std::vector<int32_t> cls_ptr;
     int64_t dinv_elems = 0;           // sum of w^2 over panels
     std::vector<int64_t> chunk_ptr;   // per level, into d_chunks
     RowChunk *d_chunks = nullptr;
@@ -48,6 +51,19 @@ struct spx_handle_s {
     UpdTile *d_tiles = nullptr;
     std::vector<int64_t> tileu_ptr;   // per level, LU's U^T side
     UpdTile *d_tilesu = nullptr;
+    // tensor-core updates (Cholesky, TF32/BF16): tasks with a source at least
+    // kTcMinWidth wide go to the tcgen05 kernel, the rest to the SIMT kernel
+    std::vector<int64_t> tcsmall_ptr; // per level, SIMT tiles of the narrow tasks
+    UpdTile *d_tcsmall = nullptr;
+    std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
+    spx::TcTile *d_tctiles = nullptr;
+    int kpad = 0;                     // operand-copy row length
+    int64_t op_rows = 0;              // operand-copy rows (sum of panel heights)
+    void *d_opc = nullptr;            // operand copy (TF32 floats or BF16)
+    int opc_bf16 = -1;
+    alignas(64) unsigned char tmap[128];   // CUtensorMap over d_opc
+    int *d_tcerr = nullptr;
+    double upd_flops_tc = 0, upd_elems_tc = 0, upd_op_elems_tc = 0;   // share of the tensor-core tasks
 
     // numeric state
     int precision = -1;
@@ -82,6 +98,19 @@ struct spx_handle_s {
 };
 
 namespace {
+
+constexpr int kTcMinWidth = 32;   // narrowest source panel sent to the tensor cores
+// Width classes of the diagonal-block kernel: shared memory and block size
+// follow the widest panel of the class, not of the level.
+constexpr int kNumClasses = 6;
+constexpr int kClassWidth[kNumClasses] = {16, 32, 64, 96, 128, 160};
+constexpr int kClassThreads[kNumClasses] = {64, 128, 256, 256, 256, 256};
+inline int width_class(int w)
+{
+    for (int c = 0; c < kNumClasses; ++c)
+        if (w <= kClassWidth[c]) return c;
+    return kNumClasses - 1;
+}
 
 std::string g_create_error;
 
@@ -176,10 +205,21 @@ spx_status ensure_device(spx_handle h)
         for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q)
             h->lvl_wmax[l] = std::max(h->lvl_wmax[l], P.pw[P.level_panels[q]]);
     if ((st = upload(h, &pinv, hpinv))) return st;
+    std::vector<int32_t> lp_sorted(P.level_panels.size());
+    h->cls_ptr.assign((size_t)P.nlevels * kNumClasses + 1, 0);
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+        int32_t pos = P.level_ptr[l];
+        for (int c = 0; c < kNumClasses; ++c) {
+            h->cls_ptr[(size_t)l * kNumClasses + c] = pos;
+            for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q)
+                if (width_class(P.pw[P.level_panels[q]]) == c) lp_sorted[pos++] = P.level_panels[q];
+        }
+    }
+    h->cls_ptr[(size_t)P.nlevels * kNumClasses] = P.level_ptr[P.nlevels];
     if ((st = upload(h, &pfcol, P.pfcol)) || (st = upload(h, &pw, P.pw)) ||
         (st = upload(h, &ph, P.ph)) || (st = upload(h, &prow, P.prow)) ||
         (st = upload(h, &rows, P.rows)) || (st = upload(h, &pval, P.pval)) ||
-        (st = upload(h, &relmap, P.relmap)) || (st = upload(h, &h->d_level_panels, P.level_panels)) ||
+        (st = upload(h, &relmap, P.relmap)) || (st = upload(h, &h->d_level_panels, lp_sorted)) ||
         (st = upload(h, &h->d_amap, P.amap)) || (st = upload(h, &h->d_csr_ptr, P.csr_ptr)) ||
         (st = upload(h, &h->d_csr_col, P.csr_col)) || (st = upload(h, &h->d_csr_src, P.csr_src)) ||
         (st = upload(h, &h->d_perm, P.perm)))
@@ -233,6 +273,46 @@ spx_status ensure_device(spx_handle h)
     if ((st = upload(h, &h->d_chunks, chunks)) || (st = upload(h, &h->d_tiles, tiles)) ||
         (st = upload(h, &h->d_tilesu, tilesu)))
         return st;
+    if (P.method == SPX_LLT) {
+        std::vector<UpdTile> small;
+        std::vector<spx::TcTile> tct;
+        h->tcsmall_ptr.assign(P.nlevels + 1, 0);
+        h->tctile_ptr.assign(P.nlevels + 1, 0);
+        for (int32_t l = 0; l < P.nlevels; ++l) {
+            for (int32_t t = P.level_task_ptr[l]; t < P.level_task_ptr[l + 1]; ++t) {
+                const spx::Task &tk = P.tasks[t];
+                const int32_t hk = P.ph[tk.src];
+                if (P.pw[tk.src] >= kTcMinWidth) {
+                    const double M = hk - tk.r0, N = tk.r1 - tk.r0, K = P.pw[tk.src];
+                    h->upd_flops_tc += 2.0 * (M - N) * N * K + N * (N + 1.0) * K;
+                    h->upd_op_elems_tc += (M + N) * K;
+                    h->upd_elems_tc += 2.0 * ((M - N) * N + N * (N + 1.0) / 2.0);
+                    for (int32_t m0 = tk.r0; m0 < hk; m0 += 128)
+                        for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += 128) {
+                            if (m0 + 128 <= n0) continue;
+                            tct.push_back(spx::TcTile{t, m0, n0, 0});
+                        }
+                } else {
+                    for (int32_t m0 = tk.r0; m0 < hk; m0 += T)
+                        for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += T) {
+                            if (m0 + T <= n0) continue;
+                            small.push_back(UpdTile{t, m0, n0, 0});
+                        }
+                }
+            }
+            h->tcsmall_ptr[l + 1] = (int64_t)small.size();
+            h->tctile_ptr[l + 1] = (int64_t)tct.size();
+        }
+        if ((st = upload(h, &h->d_tcsmall, small)) || (st = upload(h, &h->d_tctiles, tct)))
+            return st;
+    }
+    {
+        int wmax_all = 1;
+        for (int32_t q = 0; q < P.npanels; ++q) wmax_all = std::max(wmax_all, P.pw[q]);
+        h->kpad = (wmax_all + 63) & ~63;
+        h->op_rows = P.prow[P.npanels];
+    }
+    if ((st = dalloc(h, &h->d_tcerr, 1))) return st;
     if ((st = dalloc(h, &h->d_vals, (size_t)P.nnz_a)) || (st = dalloc(h, &h->d_tau, 1)) ||
         (st = dalloc(h, &h->d_anorm, 1)) || (st = dalloc(h, &h->d_err, 1)) ||
         (st = dalloc(h, &h->d_nrepl, 1)))
@@ -263,16 +343,20 @@ struct Marks {
 };
 
 template <typename T>
-void enqueue_factorization(spx_handle h, bool mixed, Marks &mk)
+void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
 {
     const spx::Plan &P = h->plan;
     cudaStream_t s = h->hs;
     T *L = (T *)h->d_L, *U = (T *)h->d_U, *Dinv = (T *)h->d_Dinv;
     const size_t elems = (size_t)P.pval[P.npanels];
     const bool lu = P.method == SPX_LU;
+    const bool tc = !lu && (prec == SPX_TF32 || prec == SPX_BF16) && sizeof(T) == 4;
+    void *opc = tc ? h->d_opc : nullptr;
+    const int op_bf16 = prec == SPX_BF16;
     int64_t &cnt = h->cnt;
     mk.mark(-1);
     init_scalars_kernel<<<1, 1, 0, s>>>(h->d_err, h->d_nrepl, h->d_anorm);
+    cudaMemsetAsync(h->d_tcerr, 0, sizeof(int), s);
     spx::launch_row_abs_sum_max(P.n, h->d_csr_ptr, h->d_csr_src, h->d_vals, h->d_anorm, s);
     const double sqrt_eps = std::sqrt(std::ldexp(1.0, -52));
     if (lu)
@@ -293,24 +377,47 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk)
         const UpdTile *tl = h->d_tiles + h->tile_ptr[l];
         const int ntl = (int)(h->tile_ptr[l + 1] - h->tile_ptr[l]);
         const int wmax = h->lvl_wmax[l];
+        for (int c = 0; c < kNumClasses; ++c) {
+            const int32_t a = h->cls_ptr[(size_t)l * kNumClasses + c];
+            const int32_t b = h->cls_ptr[(size_t)l * kNumClasses + c + 1];
+            if (b <= a) continue;
+            const int cw = std::min(kClassWidth[c], wmax);
+            if (!lu)
+                spx::launch_potrf<T>(h->dp, h->d_level_panels + a, b - a, cw, kClassThreads[c], L,
+                                     Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
+            else
+                spx::launch_getrf<T>(h->dp, h->d_level_panels + a, b - a, cw, kClassThreads[c], L,
+                                     Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
+            cnt += 1;
+        }
+        (void)panels;
+        (void)np;
+        mk.mark(SPX_K_DIAG);
         if (!lu) {
-            spx::launch_potrf<T>(h->dp, panels, np, wmax, L, Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
-            cnt += np > 0;
-            mk.mark(SPX_K_DIAG);
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LLT, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LLT, opc, h->kpad, op_bf16, s);
             cnt += nch > 0;
             mk.mark(SPX_K_TRSM);
-            spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, L, L, 1, 0, s);
-            cnt += ntl > 0;
-            mk.mark(SPX_K_UPDATE);
+            if (!tc) {
+                spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, L, L, 1, 0, s);
+                cnt += ntl > 0;
+                mk.mark(SPX_K_UPDATE);
+            } else {
+                const UpdTile *ts = h->d_tcsmall + h->tcsmall_ptr[l];
+                const int nts = (int)(h->tcsmall_ptr[l + 1] - h->tcsmall_ptr[l]);
+                const spx::TcTile *tt = h->d_tctiles + h->tctile_ptr[l];
+                const int ntt = (int)(h->tctile_ptr[l + 1] - h->tctile_ptr[l]);
+                spx::launch_update<T>(h->dp, h->d_tasks, ts, nts, L, L, L, 1, 0, s);
+                mk.mark(SPX_K_UPDATE);
+                spx::launch_update_tc(h->tmap, op_bf16, h->dp, h->d_tasks, tt, ntt, (float *)L, 1,
+                                      h->d_tcerr, s);
+                mk.mark(SPX_K_UPDATE_TC);
+                cnt += (nts > 0) + (ntt > 0);
+            }
         } else {
             const UpdTile *tu = h->d_tilesu + h->tileu_ptr[l];
             const int ntu = (int)(h->tileu_ptr[l + 1] - h->tileu_ptr[l]);
-            spx::launch_getrf<T>(h->dp, panels, np, wmax, L, Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
-            cnt += np > 0;
-            mk.mark(SPX_K_DIAG);
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LU_L, s);
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, U, spx::TRSM_LU_U, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LU_L, nullptr, 0, 0, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, U, spx::TRSM_LU_U, nullptr, 0, 0, s);
             cnt += 2 * (nch > 0);
             mk.mark(SPX_K_TRSM);
             spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, U, L, 0, 0, s);
@@ -383,8 +490,32 @@ spx_status capture(spx_handle h, cudaGraphExec_t *exec, void (*body)(spx_handle,
 void body_factor(spx_handle h, int prec, bool)
 {
     Marks mk{h, false};
-    if (prec == SPX_FP64) enqueue_factorization<double>(h, false, mk);
-    else enqueue_factorization<float>(h, true, mk);
+    if (prec == SPX_FP64) enqueue_factorization<double>(h, false, mk, prec);
+    else enqueue_factorization<float>(h, true, mk, prec);
+}
+
+// Operand copy for the tensor-core updates, allocated (zeroed) on first use.
+spx_status ensure_operand_copy(spx_handle h, int bf16)
+{
+    if (h->d_opc && h->opc_bf16 == bf16) return SPX_OK;
+    dfree(h, h->d_opc);
+    h->d_opc = nullptr;
+    const size_t esz = bf16 ? 2 : 4;
+    const size_t bytes = (size_t)h->op_rows * h->kpad * esz;
+    char *p = nullptr;
+    spx_status st = dalloc(h, &p, bytes);
+    if (st != SPX_OK) return st;
+    CU(cudaMemset(p, 0, bytes));
+    if (spx::make_operand_map(h->tmap, p, h->op_rows, h->kpad, bf16) != 0)
+        return fail(h, SPX_ERR_CUDA, "cuTensorMapEncodeTiled failed for the operand copy");
+    h->d_opc = p;
+    h->opc_bf16 = bf16;
+    if (h->fgraph) {   // the graph captured the old descriptor and buffer
+        cudaGraphExecDestroy(h->fgraph);
+        h->fgraph = nullptr;
+        h->fgraph_prec = -1;
+    }
+    return SPX_OK;
 }
 
 void body_sweep(spx_handle h, int nrhs, bool fp64)
@@ -579,6 +710,9 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         }
     }
     h->factored = false;
+    if (P.method == SPX_LLT && (precision == SPX_TF32 || precision == SPX_BF16)) {
+        if ((st = ensure_operand_copy(h, precision == SPX_BF16 ? 1 : 0))) return st;
+    }
     fence_from(h, cuda_stream);
     CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a,
                        values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->hs));
@@ -586,8 +720,8 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     if (h->profiling) {
         h->cnt = 0;
         CU(cudaEventRecord(h->ev_t0, h->hs));
-        if (fp64) enqueue_factorization<double>(h, false, mk);
-        else enqueue_factorization<float>(h, true, mk);
+        if (fp64) enqueue_factorization<double>(h, false, mk, (int)precision);
+        else enqueue_factorization<float>(h, true, mk, (int)precision);
         CU(cudaGetLastError());
         CU(cudaEventRecord(h->ev_t1, h->hs));
         h->info.launches_factor = h->cnt;
@@ -607,7 +741,10 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     CU(cudaMemcpyAsync(&bad, h->d_err, sizeof(bad), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaMemcpyAsync(&nrepl, h->d_nrepl, sizeof(nrepl), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaMemcpyAsync(&abits, h->d_anorm, sizeof(abits), cudaMemcpyDeviceToHost, h->hs));
+    int tcerr = 0;
+    CU(cudaMemcpyAsync(&tcerr, h->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaStreamSynchronize(h->hs));
+    if (tcerr) return fail(h, SPX_ERR_TIMEOUT, "a tensor-core update tile gave up waiting on its pipeline");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
     if (h->profiling) {
@@ -620,19 +757,30 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         }
         const double e = fp64 ? 8.0 : 4.0;
         const double nfac = (P.method == SPX_LU) ? 2.0 : 1.0;
+        const bool tcm = P.method == SPX_LLT && (precision == SPX_TF32 || precision == SPX_BF16);
+        const double eop = precision == SPX_BF16 ? 2.0 : 4.0;
         K.flops[SPX_K_DIAG] = P.diag_flops;
         K.flops[SPX_K_TRSM] = P.trsm_flops;
-        K.flops[SPX_K_UPDATE] = P.update_flops;
+        K.flops[SPX_K_UPDATE] = P.update_flops - (tcm ? h->upd_flops_tc : 0.0);
+        K.flops[SPX_K_UPDATE_TC] = tcm ? h->upd_flops_tc : 0.0;
         K.bytes[SPX_K_ASSEMBLE] = (double)P.nnz_a * 16.0 + (double)elems * e * nfac * 2.0;
         K.bytes[SPX_K_DIAG] = P.diag_elems * e;
         K.bytes[SPX_K_TRSM] = P.trsm_elems * e;
-        K.bytes[SPX_K_UPDATE] = P.update_elems * e;
+        K.bytes[SPX_K_UPDATE] = (P.update_elems - (tcm ? h->upd_op_elems_tc + h->upd_elems_tc : 0.0)) * e;
+        K.bytes[SPX_K_UPDATE_TC] = tcm ? h->upd_op_elems_tc * eop + h->upd_elems_tc * 4.0 : 0.0;
         K.launches[SPX_K_ASSEMBLE] = P.nnz_a > 0 ? 4 : 3;
         for (int32_t l = 0; l < P.nlevels; ++l) {
-            K.launches[SPX_K_DIAG] += (P.level_ptr[l + 1] > P.level_ptr[l]);
+            for (int c = 0; c < kNumClasses; ++c)
+                K.launches[SPX_K_DIAG] += (h->cls_ptr[(size_t)l * kNumClasses + c + 1] >
+                                           h->cls_ptr[(size_t)l * kNumClasses + c]);
             K.launches[SPX_K_TRSM] += (int64_t)nfac * (h->chunk_ptr[l + 1] > h->chunk_ptr[l]);
-            K.launches[SPX_K_UPDATE] += (h->tile_ptr[l + 1] > h->tile_ptr[l]) +
-                                        (h->tileu_ptr[l + 1] > h->tileu_ptr[l]);
+            if (tcm) {
+                K.launches[SPX_K_UPDATE] += (h->tcsmall_ptr[l + 1] > h->tcsmall_ptr[l]);
+                K.launches[SPX_K_UPDATE_TC] += (h->tctile_ptr[l + 1] > h->tctile_ptr[l]);
+            } else {
+                K.launches[SPX_K_UPDATE] += (h->tile_ptr[l + 1] > h->tile_ptr[l]) +
+                                            (h->tileu_ptr[l + 1] > h->tileu_ptr[l]);
+            }
         }
     }
     std::memcpy(&h->anorm, &abits, 8);
@@ -789,6 +937,20 @@ spx_status spx_get_factor(spx_handle h, const int64_t *Lp, const int32_t *Li, do
             }
         }
     }
+    return SPX_OK;
+}
+
+spx_status spx_get_panels(spx_handle h, int64_t *first_col, int32_t *width, int32_t *height,
+                          int32_t *level, int32_t *parent)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    const spx::Plan &P = h->plan;
+    const size_t np = (size_t)P.npanels;
+    if (first_col) std::memcpy(first_col, P.pfcol.data(), np * sizeof(int64_t));
+    if (width) std::memcpy(width, P.pw.data(), np * sizeof(int32_t));
+    if (height) std::memcpy(height, P.ph.data(), np * sizeof(int32_t));
+    if (level) std::memcpy(level, P.plevel.data(), np * sizeof(int32_t));
+    if (parent) std::memcpy(parent, P.pparent.data(), np * sizeof(int32_t));
     return SPX_OK;
 }
 

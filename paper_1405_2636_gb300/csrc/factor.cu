@@ -11,6 +11,7 @@
 // mixed-precision factor); the diagonal blocks are always factored in double.
 #include "kernels.cuh"
 
+#include <cuda_bf16.h>
 #include <cstdio>
 
 namespace spx {
@@ -49,26 +50,44 @@ void launch_assemble(int64_t nnz, const double *vals, const int64_t *amap, T *L,
 //   X(i,j) = -(sum_{k=j+1..i} X(i,k) L(k,j)) X(j,j)   for i > j,
 // using the already inverted columns k > j (from X L = I).  With trans the
 // same routine inverts U^T, i.e. writes U^{-1} in the upper triangle.  C is
-// the arithmetic type; `col` is w doubles of scratch.
+// the storage and arithmetic type; `col` is w elements of scratch.
 // ---------------------------------------------------------------------------
 template <typename C>
-__device__ void invert_lower_inplace(double *a, int w, bool trans, bool unit, double *col)
+__device__ void invert_lower_inplace(C *a, int w, bool trans, bool unit, C *col)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int j = w - 1; j >= 0; --j) {
         for (int i = j + 1 + tid; i < w; i += nt) col[i] = a[trans ? j + i * w : i + j * w];
         __syncthreads();
-        const C xjj = unit ? (C)1 : (C)1 / (C)a[trans ? j + j * w : j + j * w];
+        const C xjj = unit ? (C)1 : (C)1 / a[j + j * w];
         for (int i = j + 1 + tid; i < w; i += nt) {
-            const C xii = unit ? (C)1 : (C)a[trans ? i + i * w : i + i * w];
-            C s = xii * (C)col[i];
-            for (int k = j + 1; k < i; ++k) s += (C)a[trans ? k + i * w : i + k * w] * (C)col[k];
-            a[trans ? j + i * w : i + j * w] = (double)(-s * xjj);
+            const C xii = unit ? (C)1 : a[i + i * w];
+            C s = xii * col[i];
+            for (int k = j + 1; k < i; ++k) s += a[trans ? k + i * w : i + k * w] * col[k];
+            a[trans ? j + i * w : i + j * w] = -s * xjj;
         }
         __syncthreads();
-        if (tid == 0 && !unit) a[j + j * w] = (double)xjj;
+        if (tid == 0 && !unit) a[j + j * w] = xjj;
         __syncthreads();
     }
+}
+
+// Narrow the w*w doubles at sm to T in place (T = float: the floats land in
+// the first half of the same buffer; rounds of blockDim elements are read
+// before any of them is written, so no live double is overwritten).
+template <typename T>
+__device__ T *narrow_inplace(double *sm, int count)
+{
+    if (sizeof(T) == sizeof(double)) return reinterpret_cast<T *>(sm);
+    T *out = reinterpret_cast<T *>(sm);
+    for (int base = 0; base < count; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        const double v = idx < count ? sm[idx] : 0.0;
+        __syncthreads();
+        if (idx < count) out[idx] = (T)v;
+        __syncthreads();
+    }
+    return out;
 }
 
 // ---------------------------------------------------------------------------
@@ -131,13 +150,14 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
         if (i >= j) D[i + (int64_t)j * h] = (T)sm[idx];
     }
     __syncthreads();
-    invert_lower_inplace<T>(sm, w, false, false, col);
+    T *a = narrow_inplace<T>(sm, w * w);
+    invert_lower_inplace<T>(a, w, false, false, reinterpret_cast<T *>(col));
     T *Mi = Dinv + p.pinv[pid];
-    for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = (T)sm[idx];
+    for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = a[idx];
 }
 
 template <typename T>
-void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, int threads, T *L, T *Dinv,
                   const double *replace_tau, int64_t *err_col, unsigned long long *nrepl,
                   cudaStream_t s)
 {
@@ -149,7 +169,7 @@ void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
         once = true;
     }
     const size_t smem = sizeof(double) * ((size_t)wmax * wmax + wmax);
-    potrf_kernel<T><<<count, 256, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl);
+    potrf_kernel<T><<<count, threads, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl);
 }
 
 // ---------------------------------------------------------------------------
@@ -209,14 +229,15 @@ __global__ void __launch_bounds__(256) getrf_kernel(DevPlan p, const int32_t *__
         D[i + (int64_t)j * h] = (T)sm[idx];
     }
     __syncthreads();
-    invert_lower_inplace<T>(sm, w, false, true, col);   // unit lower L
-    invert_lower_inplace<T>(sm, w, true, false, col);   // U through U^T
+    T *a = narrow_inplace<T>(sm, w * w);
+    invert_lower_inplace<T>(a, w, false, true, reinterpret_cast<T *>(col));   // unit lower L
+    invert_lower_inplace<T>(a, w, true, false, reinterpret_cast<T *>(col));   // U through U^T
     T *Mi = Dinv + p.pinv[pid];
-    for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = (T)sm[idx];
+    for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = a[idx];
 }
 
 template <typename T>
-void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, int threads, T *L, T *Dinv,
                   const double *tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s)
 {
     if (count <= 0) return;
@@ -227,7 +248,7 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
         once = true;
     }
     const size_t smem = sizeof(double) * ((size_t)wmax * wmax + wmax);
-    getrf_kernel<T><<<count, 256, smem, s>>>(p, panels, L, Dinv, tau, err_col, nrepl);
+    getrf_kernel<T><<<count, threads, smem, s>>>(p, panels, L, Dinv, tau, err_col, nrepl);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,10 +260,18 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
 // The CTA copies its rows to shared memory first, so writing them back in
 // place is safe; 64 x 64 output tiles, 4 x 4 per thread, K-chunks of 16.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float round_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                         const T *__restrict__ Dinv,
-                                                        T *__restrict__ X, int mode)
+                                                        T *__restrict__ X, int mode, void *opc,
+                                                        int kpad, int op_bf16)
 {
     extern __shared__ unsigned char smraw[];
     T *Xs = reinterpret_cast<T *>(smraw);      // Xs[k * 64 + r], k < wpad
@@ -305,12 +334,39 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                 if (j < w) Xg[r + (int64_t)j * h] = acc[a][b];
             }
         }
+        if (opc) {
+            // the same rows, K-major, for the tensor-core updates
+            const int64_t orow0 = p.prow[pid] + ch.r0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int r = tx + 16 * a;
+                if (r >= nr) continue;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int j = c0 + ty + 16 * b;
+                    if (j >= w) continue;
+                    const int64_t o = (orow0 + r) * kpad + j;
+                    if (op_bf16) reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16((float)acc[a][b]);
+                    else reinterpret_cast<float *>(opc)[o] = round_tf32((float)acc[a][b]);
+                }
+            }
+        }
+    }
+    if (opc) {
+        const int64_t orow0 = p.prow[pid] + ch.r0;
+        const int padw = kpad - w;
+        for (int e = tid; e < nr * padw; e += 256) {
+            const int r = e / padw, j = w + e % padw;
+            const int64_t o = (orow0 + r) * kpad + j;
+            if (op_bf16) reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(0.0f);
+            else reinterpret_cast<float *>(opc)[o] = 0.0f;
+        }
     }
 }
 
 template <typename T>
 void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
-                 T *X, int mode, cudaStream_t s)
+                 T *X, int mode, void *opc, int kpad, int op_bf16, cudaStream_t s)
 {
     if (count <= 0) return;
     static bool once = false;
@@ -320,7 +376,7 @@ void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, 
         once = true;
     }
     const size_t smem = sizeof(T) * (size_t)((wmax + 15) & ~15) * kTrsmRows;
-    trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode);
+    trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, kpad, op_bf16);
 }
 
 // ---------------------------------------------------------------------------
@@ -488,12 +544,12 @@ void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A,
 // explicit instantiations
 template void launch_assemble<double>(int64_t, const double *, const int64_t *, double *, double *, cudaStream_t);
 template void launch_assemble<float>(int64_t, const double *, const int64_t *, float *, float *, cudaStream_t);
-template void launch_potrf<double>(const DevPlan &, const int32_t *, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_potrf<float>(const DevPlan &, const int32_t *, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_getrf<double>(const DevPlan &, const int32_t *, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_getrf<float>(const DevPlan &, const int32_t *, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, cudaStream_t);
-template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, cudaStream_t);
+template void launch_potrf<double>(const DevPlan &, const int32_t *, int, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_potrf<float>(const DevPlan &, const int32_t *, int, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_getrf<double>(const DevPlan &, const int32_t *, int, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_getrf<float>(const DevPlan &, const int32_t *, int, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
+template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, void *, int, int, cudaStream_t);
+template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, void *, int, int, cudaStream_t);
 template void launch_update<double>(const DevPlan &, const DevTask *, const UpdTile *, int, const double *, const double *, double *, int, int, cudaStream_t);
 template void launch_update<float>(const DevPlan &, const DevTask *, const UpdTile *, int, const float *, const float *, float *, int, int, cudaStream_t);
 

@@ -31,6 +31,12 @@ struct UpdTile {
     int32_t task, m0, n0, pad;
 };
 
+// A 128 x 128 tensor-core tile of one update task: source rows [m0, m0+128)
+// against facing rows [n0, n0+128).
+struct TcTile {
+    int32_t task, m0, n0, pad;
+};
+
 // A chunk of rows [r0, r0+64) of one panel for the TRSM / solve kernels.
 struct RowChunk {
     int32_t panel, r0;
@@ -53,17 +59,27 @@ void launch_assemble(int64_t nnz, const double *vals, const int64_t *amap, T *L,
                      cudaStream_t s);
 
 template <typename T>
-void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, int threads, T *L, T *Dinv,
                   const double *replace_tau, int64_t *err_col, unsigned long long *nrepl,
                   cudaStream_t s);
 
 template <typename T>
-void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, int threads, T *L, T *Dinv,
                   const double *tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s);
 
+// opc (may be null): K-major operand copy for the tensor-core updates, rows
+// at prow[panel] + r with kpad elements each; op_bf16 selects BF16 storage,
+// otherwise TF32-rounded FP32.
 template <typename T>
 void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
-                 T *X, int mode, cudaStream_t s);
+                 T *X, int mode, void *opc, int kpad, int op_bf16, cudaStream_t s);
+
+// Tensor-core update (update_tc.cu).  tmap: a CUtensorMap over the operand
+// copy (make_operand_map); err receives 1 if a bounded wait expired.
+size_t tc_smem_bytes();
+int make_operand_map(void *tmap_out, void *base, int64_t rows, int kpad, int bf16);
+void launch_update_tc(const void *tmap, int bf16, const DevPlan &p, const DevTask *tasks,
+                      const TcTile *tiles, int count, float *C, int lower, int *err, cudaStream_t s);
 
 template <typename T>
 void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles, int count,

@@ -1,0 +1,311 @@
+// update_tc.cu -- the supernodal update (Sec. V-B) on the 5th-generation
+// tensor cores: W = A_rows(M) * A_rows(N)^T with TF32 or BF16 operands and an
+// FP32 accumulator in tensor memory, then the index-mapped scatter-subtract of
+// W into the FP32 target panel (fused epilogue, no temporary buffer).
+//
+// Operands come from the K-major operand copy of every panel (row r of panel
+// p at operand row prow[p] + r, Kpad elements per row, TF32-rounded or BF16),
+// written by the TRSM kernel.  One 2-D TMA descriptor covers the whole copy;
+// a tile is loaded as 128 rows x 128 bytes with the 128-byte swizzle, the
+// canonical K-major layout of the MMA's shared-memory operand descriptors.
+//
+// One CTA = one 128 x 128 output tile of one (source, target) task:
+//   thread 0      issues the TMA loads (2-stage ring) and the MMAs,
+//   all 4 warps   read their 32 TMEM lanes and scatter the rows they own.
+// Every wait on an mbarrier is bounded; on expiry the CTA records an error
+// code, skips the epilogue and still releases its tensor memory.
+#include "kernels.cuh"
+
+#include <cuda.h>
+
+namespace spx {
+namespace {
+
+constexpr int kM = 128;                 // accumulator rows (TMEM lanes)
+constexpr int kN = 128;                 // accumulator columns
+constexpr int kStages = 2;
+constexpr int kRowBytes = 128;          // one swizzled K chunk per operand row
+constexpr int kTileBytes = kM * kRowBytes;
+constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr uint32_t kTmemCols = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false when it never came.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format (TF32 = 2 under
+// kind::tf32, BF16 = 1 under kind::f16), both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format)
+{
+    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(kN >> 3) << 17) |
+           ((uint32_t)(kM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate)
+{
+    if (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// KIND 0: TF32 operands (32 per 128-byte row chunk); KIND 1: BF16 (64).
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    update_tc_kernel(const __grid_constant__ CUtensorMap opmap, DevPlan p,
+                     const DevTask *__restrict__ tasks, const TcTile *__restrict__ tiles,
+                     float *__restrict__ C, int lower, int *err)
+{
+    constexpr int kElems = KIND == 0 ? 32 : 64;           // K elements per stage
+    constexpr uint32_t kIdesc = make_idesc(KIND == 0 ? 2u : 1u);
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;
+    unsigned char *sB = base + kStages * kTileBytes;
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ __align__(8) uint64_t empty[kStages];
+    __shared__ __align__(8) uint64_t done;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+
+    const TcTile tl = tiles[blockIdx.x];
+    const DevTask tk = tasks[tl.task];
+    const int src = tk.src, tgt = tk.tgt;
+    const int h = p.ph[src], K = p.pw[src];
+    const int nk = (K + kElems - 1) / kElems;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    if (threadIdx.x == 0) {
+        const int64_t rbase = p.prow[src];
+        const int ya = (int)(rbase + tl.m0), yb = (int)(rbase + tl.n0);
+        bool ok = true;
+        for (int kc = 0; kc < nk && kc < kStages; ++kc) {
+            mbar_expect_tx(&full[kc], 2 * kTileBytes);
+            tma_load_2d(sA + kc * kTileBytes, &opmap, &full[kc], kc * kElems, ya);
+            tma_load_2d(sB + kc * kTileBytes, &opmap, &full[kc], kc * kElems, yb);
+        }
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % kStages;
+            const uint32_t ph = (uint32_t)(kc / kStages) & 1u;
+            if (!mbar_wait(&full[s], ph)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)   // 32 bytes of K per MMA
+                mma<KIND>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
+                          (kc > 0 || ks > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            if (kc + kStages < nk) {
+                if (!mbar_wait(&empty[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&full[s], 2 * kTileBytes);
+                tma_load_2d(sA + s * kTileBytes, &opmap, &full[s], (kc + kStages) * kElems, ya);
+                tma_load_2d(sB + s * kTileBytes, &opmap, &full[s], (kc + kStages) * kElems, yb);
+            }
+        }
+        mma_commit(&done);   // arrives once every MMA issued above has completed
+        if (!ok) s_fail = 1;
+    }
+    __syncwarp();
+    const bool got = mbar_wait(&done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!got || s_fail) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else {
+        const int hT = p.ph[tgt];
+        float *Ct = C + p.pval[tgt];
+        const int64_t fcolT = p.pfcol[tgt];
+        const int32_t *srow = p.rows + p.prow[src];
+        const int32_t *rmap = p.relmap + tk.relmap_off - tk.r0;
+        const int i = tl.m0 + warp * 32 + lane;
+        const bool row_ok = i < h;
+        const int64_t roff = row_ok ? (int64_t)rmap[i] : 0;
+        const int jend = min(tk.r1, tl.n0 + kN);
+        for (int c0 = 0; tl.n0 + c0 < jend; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+                const int j = tl.n0 + c0 + cc;
+                if (j >= jend) break;
+                if (row_ok && (!lower || i >= j)) {
+                    const int64_t coff = (int64_t)(srow[j] - fcolT) * hT;
+                    atomicAdd(Ct + roff + coff, -__uint_as_float(v[cc]));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+}  // namespace
+
+size_t tc_smem_bytes() { return (size_t)2 * kStages * kTileBytes + 1024; }
+
+int make_operand_map(void *tmap_out, void *base, int64_t rows, int kpad, int bf16)
+{
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return -1;
+        encode = (EncodeTiledFn)fn;
+    }
+    const int esz = bf16 ? 2 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kpad * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(reinterpret_cast<CUtensorMap *>(tmap_out),
+                        bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -2;
+}
+
+void launch_update_tc(const void *tmap, int bf16, const DevPlan &p, const DevTask *tasks,
+                      const TcTile *tiles, int count, float *C, int lower, int *err, cudaStream_t s)
+{
+    if (count <= 0) return;
+    const CUtensorMap &m = *reinterpret_cast<const CUtensorMap *>(tmap);
+    const size_t smem = tc_smem_bytes();
+    static bool once0 = false, once1 = false;
+    if (bf16) {
+        if (!once1) {
+            cudaFuncSetAttribute(update_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            once1 = true;
+        }
+        update_tc_kernel<1><<<count, 128, smem, s>>>(m, p, tasks, tiles, C, lower, err);
+    } else {
+        if (!once0) {
+            cudaFuncSetAttribute(update_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            once0 = true;
+        }
+        update_tc_kernel<0><<<count, 128, smem, s>>>(m, p, tasks, tiles, C, lower, err);
+    }
+}
+
+}  // namespace spx

@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "SPX_OK", 1: "SPX_ERR_ARG", 2: "SPX_ERR_ALLOC", 3: "SPX_ERR_C
 # Every symbol include/spx.h declares.
 EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_factorize",
             "spx_solve", "spx_get_info", "spx_get_perm", "spx_get_factor", "spx_last_error",
-            "spx_free", "spx_update", "spx_set_profiling", "spx_get_kernel_stats"]
+            "spx_free", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
+            "spx_get_panels"]
 
 
 class spx_options(ctypes.Structure):
@@ -67,12 +68,12 @@ class spx_info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
-KERNEL_CLASSES = ["assemble", "diag", "trsm", "update"]
+KERNEL_CLASSES = ["assemble", "diag", "trsm", "update", "update_tc"]
 
 
 class spx_kernel_stats(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4),
-                ("flops", ctypes.c_double * 4), ("bytes", ctypes.c_double * 4)]
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5),
+                ("flops", ctypes.c_double * 5), ("bytes", ctypes.c_double * 5)]
 
     def as_dict(self) -> dict:
         return {c: {"ms": self.ms[i], "launches": self.launches[i], "flops": self.flops[i],
@@ -108,11 +109,13 @@ def load():
     lib.spx_last_error.restype = ctypes.c_char_p
     lib.spx_set_profiling.argtypes = [_vp, ctypes.c_int]
     lib.spx_get_kernel_stats.argtypes = [_vp, ctypes.POINTER(spx_kernel_stats)]
+    lib.spx_get_panels.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     lib.spx_free.argtypes = [_vp]
     lib.spx_free.restype = None
     lib.spx_update.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]
     for name in ("spx_analyze", "spx_factorize", "spx_solve", "spx_get_info", "spx_get_perm",
-                 "spx_get_factor", "spx_update", "spx_set_profiling", "spx_get_kernel_stats"):
+                 "spx_get_factor", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
+                 "spx_get_panels"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -243,6 +246,17 @@ class Handle:
         k = spx_kernel_stats()
         _check(load().spx_get_kernel_stats(self._h, ctypes.byref(k)), self._h)
         return k.as_dict()
+
+    def panels(self) -> dict:
+        """Panel structure: first column, width, height, level, parent."""
+        npn = self.info()["npanels"]
+        out = {"first_col": np.empty(npn, np.int64), "width": np.empty(npn, np.int32),
+               "height": np.empty(npn, np.int32), "level": np.empty(npn, np.int32),
+               "parent": np.empty(npn, np.int32)}
+        _check(load().spx_get_panels(self._h, *[_ptr(out[k]) for k in
+                                                 ("first_col", "width", "height", "level", "parent")]),
+               self._h)
+        return out
 
     def perm(self) -> np.ndarray:
         p = np.empty(self.n, dtype=np.int64)
