@@ -387,7 +387,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if head == "fp64" else "f32-factor+f64-refinement",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "nnz_a": int(colptr[-1]), "nrhs": NRHS,
+        "config": {"workload": WORKLOAD if grid == GRID else
+                   f"diffusion3d_{grid[0]}x{grid[1]}x{grid[2]}_7pt_expN01_16rhs",
+                   "n": n, "nnz_a": int(colptr[-1]), "nrhs": NRHS,
                    "seed": SEED, "grid": list(grid), "ordering": "geometric nested dissection",
                    "nnz_l": info0["nnz_l"], "flops_exact": flops,
                    "panels": info0["npanels"], "levels": info0["nlevels"],

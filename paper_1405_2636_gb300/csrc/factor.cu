@@ -17,6 +17,81 @@
 namespace spx {
 
 // ---------------------------------------------------------------------------
+// Pivot arithmetic in FP64 with short dependency chains.  IEEE FP64 division
+// and square root expand into long chains of dependent FP64 instructions, and
+// a dependent FP64 instruction costs tens of times its throughput slot on
+// this part, so the column-by-column pivots would dominate the diagonal
+// kernels.  Instead:
+//  * a float seed is cut from the double's bits with integer operations (no
+//    FP64 conversion), refined by the FP32 unit (rsqrtf / reciprocal) and
+//    widened back the same way;
+//  * reciprocal: Newton's method on 1/y - d, written with the error term
+//    e = 1 - d y so that two steps need three dependent FP64 operations
+//    (y1 = y0 + y0 e, e1 = e^2, y2 = y1 + y1 e1);
+//  * square root and its reciprocal together: Goldschmidt's iteration
+//    (g -> sqrt(d), h -> 1/(2 sqrt(d)); r = 1/2 - g h; g += g r; h += h r),
+//    two iterations, five dependent FP64 operations.
+// Each iteration squares the relative error: 2^-22 -> 2^-44 -> below FP64
+// rounding.  Magnitudes outside the FP32 normal range fall back to IEEE.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool float_seed(double d, float *f)
+{
+    const long long b = __double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < -125 || e > 126) return false;
+    const unsigned fb = (unsigned)((b >> 32) & 0x80000000u) | ((unsigned)(e + 127) << 23) |
+                        (unsigned)((b >> 29) & 0x7FFFFF);
+    *f = __uint_as_float(fb);
+    return true;
+}
+
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const int e = (int)((u >> 23) & 0xFF) - 127;
+    const long long b = ((long long)(u & 0x80000000u) << 32) | ((long long)(e + 1023) << 52) |
+                        ((long long)(u & 0x7FFFFF) << 29);
+    return __longlong_as_double(b);
+}
+
+__device__ __forceinline__ double rcp_newton(double d)
+{
+    float f;
+    if (!float_seed(d, &f)) return 1.0 / d;
+    const float yf = 1.0f / f;
+    if (!(fabsf(yf) > 1e-37f && fabsf(yf) < 1e37f)) return 1.0 / d;
+    const double y0 = widen(yf);
+    const double e0 = fma(-d, y0, 1.0);
+    const double y1 = fma(y0, e0, y0);
+    const double e1 = e0 * e0;
+    return fma(y1, e1, y1);
+}
+
+// sqrt(d) and 1/sqrt(d) for d > 0.
+__device__ __forceinline__ void sqrt_rsqrt(double d, double *s, double *rs)
+{
+    float f;
+    if (d <= 0.0 || !float_seed(d, &f)) {
+        *s = sqrt(d);
+        *rs = 1.0 / *s;
+        return;
+    }
+    const double y = widen(rsqrtf(f));
+    double g = d * y, h = 0.5 * y;
+    double r = fma(-g, h, 0.5);
+    g = fma(g, r, g);
+    h = fma(h, r, h);
+    r = fma(-g, h, 0.5);
+    g = fma(g, r, g);
+    h = fma(h, r, h);
+    *s = g;
+    *rs = 2.0 * h;
+}
+
+__device__ __forceinline__ float rcp_newton(float d) { return 1.0f / d; }
+
+
+// ---------------------------------------------------------------------------
 // Assembly: scatter the CSC values into the zeroed panels.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -59,7 +134,7 @@ __device__ void invert_lower_inplace(C *a, int w, bool trans, bool unit, C *col)
     for (int j = w - 1; j >= 0; --j) {
         for (int i = j + 1 + tid; i < w; i += nt) col[i] = a[trans ? j + i * w : i + j * w];
         __syncthreads();
-        const C xjj = unit ? (C)1 : (C)1 / a[j + j * w];
+        const C xjj = unit ? (C)1 : rcp_newton(a[j + j * w]);
         for (int i = j + 1 + tid; i < w; i += nt) {
             const C xii = unit ? (C)1 : a[i + i * w];
             C s = xii * col[i];
@@ -91,12 +166,151 @@ __device__ T *narrow_inplace(double *sm, int count)
 }
 
 // ---------------------------------------------------------------------------
+// Blocked right-looking Cholesky of the w x w block held in shared memory
+// (double, column-major, leading dimension w).  Columns go in blocks of kDB:
+// warp 0 factors the block column (warp-synchronous: pivot, scaling, the
+// updates inside the block), then every warp applies the rank-kDB update to
+// the trailing lower triangle.  Two block barriers per kDB columns.  A pivot
+// that is not positive is reported (replace_tau <= 0: the smallest failing
+// column goes to *err_col) or replaced by replace_tau and counted.
+// ---------------------------------------------------------------------------
+constexpr int kDB = 8;
+
+__device__ void chol_blocked(double *a, int w, double replace_tau, int64_t col0, int64_t *err_col,
+                             unsigned long long *nrepl)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int kb = 0; kb < w; kb += kDB) {
+        const int bw = min(kDB, w - kb);
+        if (warp == 0) {
+            for (int k = kb; k < kb + bw; ++k) {
+                double d = a[k + k * w];
+                const bool bad = !(d > 0.0);
+                if (bad) {
+                    if (lane == 0) {
+                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                        else atomicMin((long long *)err_col, (long long)(col0 + k));
+                    }
+                    d = replace_tau > 0.0 ? replace_tau : 1.0;
+                }
+                double inv;
+                sqrt_rsqrt(d, &d, &inv);               // L(k,k) = sqrt(pivot), inv = 1 / L(k,k)
+                __syncwarp();
+                if (lane == 0) a[k + k * w] = d;
+                for (int i = k + 1 + lane; i < w; i += 32) a[i + k * w] *= inv;
+                __syncwarp();
+                for (int j = k + 1; j < kb + bw; ++j) {
+                    const double ljk = a[j + k * w];
+                    for (int i = j + lane; i < w; i += 32) a[i + j * w] -= a[i + k * w] * ljk;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // rank-bw update; each thread carries two rows and two partial sums so
+        // that four independent FP64 chains are in flight (dependent FP64
+        // operations are far slower than independent ones on this part)
+        for (int j = kb + bw + warp; j < w; j += nw) {
+            double lj[kDB];
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) lj[c] = c < bw ? a[j + (kb + c) * w] : 0.0;
+            for (int i = j + lane; i < w; i += 64) {
+                const int i2 = i + 32;
+                const bool two = i2 < w;
+                double x0 = a[i + j * w], x1 = 0.0;
+                double y0 = two ? a[i2 + j * w] : 0.0, y1 = 0.0;
+#pragma unroll
+                for (int c = 0; c < kDB; c += 2) {
+                    if (c < bw) {
+                        x0 -= a[i + (kb + c) * w] * lj[c];
+                        if (two) y0 -= a[i2 + (kb + c) * w] * lj[c];
+                    }
+                    if (c + 1 < bw) {
+                        x1 -= a[i + (kb + c + 1) * w] * lj[c + 1];
+                        if (two) y1 -= a[i2 + (kb + c + 1) * w] * lj[c + 1];
+                    }
+                }
+                a[i + j * w] = x0 + x1;
+                if (two) a[i2 + j * w] = y0 + y1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked inversion X = L^{-1} in place (lower triangular, non-unit, column-
+// major leading dimension w) by block rows of kDB, top to bottom:
+//   T(I, J)  = sum_{K = J..I-1} L(I, K) X(K, J)       (all J < I in parallel)
+//   X(I, I)  = L(I, I)^{-1}                            (warp 0, by columns)
+//   X(I, J)  = -X(I, I) T(I, J)
+// from L X = I.  tmp holds kDB * w + kDB * kDB elements of type C.
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ void invert_lower_blocked(C *a, int w, C *tmp)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    C *Tb = tmp;                   // Tb[ii + j * kDB], j < r0
+    C *Dt = tmp + kDB * w;         // Dt[ii + jj * kDB] = X(I, I)
+    for (int r0 = 0; r0 < w; r0 += kDB) {
+        const int bh = min(kDB, w - r0);
+        for (int e = tid; e < bh * r0; e += nt) {
+            const int ii = e % bh, j = e / bh;
+            C s0 = (C)0, s1 = (C)0, s2 = (C)0, s3 = (C)0;   // four short chains
+            int k = j;
+            for (; k + 3 < r0; k += 4) {
+                s0 += a[(r0 + ii) + k * w] * a[k + j * w];
+                s1 += a[(r0 + ii) + (k + 1) * w] * a[(k + 1) + j * w];
+                s2 += a[(r0 + ii) + (k + 2) * w] * a[(k + 2) + j * w];
+                s3 += a[(r0 + ii) + (k + 3) * w] * a[(k + 3) + j * w];
+            }
+            for (; k < r0; ++k) s0 += a[(r0 + ii) + k * w] * a[k + j * w];
+            Tb[ii + j * kDB] = (s0 + s1) + (s2 + s3);
+        }
+        if (warp == 0 && lane < bh) {
+            // column jj = lane of the inverse of the bh x bh diagonal block, by a
+            // column sweep: x = e_jj; for kk: x_kk /= L_kk; x_ii -= L_ii,kk x_kk
+            const int jj = lane;
+            C rd[kDB], x[kDB];
+#pragma unroll
+            for (int q = 0; q < kDB; ++q) {
+                rd[q] = q < bh ? rcp_newton(a[(r0 + q) + (r0 + q) * w]) : (C)0;
+                x[q] = q == jj ? (C)1 : (C)0;
+            }
+#pragma unroll
+            for (int kk = 0; kk < kDB; ++kk) {
+                if (kk < bh && kk >= jj) {
+                    x[kk] *= rd[kk];
+#pragma unroll
+                    for (int ii = kk + 1; ii < kDB; ++ii)
+                        if (ii < bh) x[ii] -= a[(r0 + ii) + (r0 + kk) * w] * x[kk];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kDB; ++q)
+                if (q < bh) Dt[q + jj * kDB] = x[q];
+        }
+        __syncthreads();
+        for (int e = tid; e < bh * r0; e += nt) {
+            const int ii = e % bh, j = e / bh;
+            C acc = (C)0;
+            for (int kk = 0; kk <= ii; ++kk) acc += Dt[ii + kk * kDB] * Tb[kk + j * kDB];
+            a[(r0 + ii) + j * w] = -acc;
+        }
+        for (int e = tid; e < bh * bh; e += nt) {
+            const int ii = e % bh, jj = e / bh;
+            if (ii >= jj) a[(r0 + ii) + (r0 + jj) * w] = Dt[ii + jj * kDB];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Diagonal block, Cholesky (Sec. III step 1): one CTA per panel, the block in
-// shared memory in double, right-looking by columns.  A pivot that is not
-// positive is either reported (replace_tau <= 0: the smallest failing column
-// goes to *err_col) or replaced by replace_tau and counted.  The CTA then
-// inverts L_kk in place (arithmetic of the factor's type) and stores the
-// inverse at Dinv + pinv[panel]; the TRSM and the solves multiply by it.
+// shared memory in double; then L_kk^{-1} (arithmetic of the factor's type)
+// is stored at Dinv + pinv[panel] for the TRSM and the solves.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__restrict__ panels,
@@ -105,53 +319,24 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
                                                     int64_t *err_col, unsigned long long *nrepl)
 {
     extern __shared__ double sm[];
-    __shared__ double s_piv, s_inv;
     const double replace_tau = *replace_tau_p;
     const int pid = panels[blockIdx.x];
     const int w = p.pw[pid], h = p.ph[pid];
     T *D = L + p.pval[pid];
-    double *col = sm + w * w;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int idx = tid; idx < w * w; idx += nt) {
         int i = idx % w, j = idx / w;
         sm[idx] = (i >= j) ? (double)D[i + (int64_t)j * h] : 0.0;
     }
     __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    for (int k = 0; k < w; ++k) {
-        if (tid == 0) {
-            double d = sm[k + k * w];
-            if (!(d > 0.0)) {
-                if (replace_tau > 0.0) {
-                    d = replace_tau;
-                    atomicAdd(nrepl, 1ull);
-                } else {
-                    atomicMin((long long *)err_col, (long long)(p.pfcol[pid] + k));
-                    d = 1.0;
-                }
-            }
-            d = sqrt(d);
-            sm[k + k * w] = d;
-            s_piv = d;
-            s_inv = 1.0 / d;
-        }
-        __syncthreads();
-        const double inv = s_inv;
-        for (int i = k + 1 + tid; i < w; i += nt) sm[i + k * w] *= inv;
-        __syncthreads();
-        for (int j = k + 1 + warp; j < w; j += nw) {
-            const double ljk = sm[j + k * w];
-            for (int i = j + lane; i < w; i += 32) sm[i + j * w] -= sm[i + k * w] * ljk;
-        }
-        __syncthreads();
-    }
+    chol_blocked(sm, w, replace_tau, p.pfcol[pid], err_col, nrepl);
     for (int idx = tid; idx < w * w; idx += nt) {
         int i = idx % w, j = idx / w;
         if (i >= j) D[i + (int64_t)j * h] = (T)sm[idx];
     }
     __syncthreads();
     T *a = narrow_inplace<T>(sm, w * w);
-    invert_lower_inplace<T>(a, w, false, false, reinterpret_cast<T *>(col));
+    invert_lower_blocked<T>(a, w, reinterpret_cast<T *>(sm + (size_t)w * w));
     T *Mi = Dinv + p.pinv[pid];
     for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = a[idx];
 }
@@ -165,10 +350,10 @@ void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
     static bool once = false;
     if (!once) {
         cudaFuncSetAttribute(potrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * (kMaxWidth * kMaxWidth + kMaxWidth)));
+                             (int)(sizeof(double) * (kMaxWidth * kMaxWidth + kDB * kMaxWidth + kDB * kDB)));
         once = true;
     }
-    const size_t smem = sizeof(double) * ((size_t)wmax * wmax + wmax);
+    const size_t smem = sizeof(double) * ((size_t)wmax * wmax + kDB * wmax + kDB * kDB);
     potrf_kernel<T><<<count, threads, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl);
 }
 
@@ -212,7 +397,7 @@ __global__ void __launch_bounds__(256) getrf_kernel(DevPlan p, const int32_t *__
                 d = 1.0;
             }
             sm[k + k * w] = d;
-            s_inv = 1.0 / d;
+            s_inv = rcp_newton(d);
         }
         __syncthreads();
         const double inv = s_inv;

@@ -69,6 +69,9 @@ def test_cholesky_fp64_matches_oracle(torch, name, maker, opts):
     Lx = h.factor_on_pattern(F.sym.Lp, F.sym.Li)
     assert _rel(Lx, F.Lx) <= 1e-12
     assert np.max(np.abs(Lx - F.Lx)) <= 1e-12 * np.max(np.abs(F.Lx))
+    # the pivots (square roots taken on the GPU by Newton steps) entry by entry
+    d_gpu, d_ora = Lx[F.sym.Lp[:-1]], F.Lx[F.sym.Lp[:-1]]
+    assert np.max(np.abs(d_gpu - d_ora) / d_ora) <= 1e-13
     n = A.shape[0]
     B = inputs.rhs(n, 3, 11)
     X, info = h.solve(B)
