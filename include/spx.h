@@ -169,6 +169,31 @@ spx_status spx_get_factor(spx_handle h, const int64_t *Lp, const int32_t *Li, do
 spx_status spx_get_panels(spx_handle h, int64_t *first_col, int32_t *width, int32_t *height,
                           int32_t *level, int32_t *parent);
 
+/* Allocation-free solve.  (The paper has no counterpart; this entry point
+ * exists for callers that cannot allocate device memory when they solve:
+ * code that replays a solve inside a captured CUDA graph or a real-time
+ * loop, where cudaMalloc would stall the device or is not allowed, and hosts
+ * whose device memory belongs to another allocator.)  It runs one forward
+ * and one backward sweep through the factor of the last spx_factorize --
+ * spx_solve without refinement -- and allocates nothing: no cudaMalloc,
+ * cudaFree, graph or library call that allocates.
+ *   B, X : device arrays, column-major, leading dimensions ldb, ldx >= n;
+ *          X must not overlap B.
+ *   The sweep vectors live in one file-scope device buffer of 16 MiB that
+ *   every GPU loading the library holds until the process exits; the call
+ *   needs 4 * n * nrhs elements of the factor's type (8 bytes for an FP64
+ *   factor, 4 otherwise) and returns SPX_ERR_ARG when that exceeds 16 MiB.
+ *   All calls share that buffer and it keeps the previous call's contents:
+ *   calls whose GPU work overlaps (other streams, other handles, other
+ *   threads) race and must be ordered by the caller.
+ *   The work is enqueued on cuda_stream and the call returns without
+ *   waiting for it.  The current device must be the one the handle
+ *   factorized on.  The first call on a device looks up the buffer's device
+ *   address (cudaGetSymbolAddress); make that first call before any stream
+ *   capture. */
+spx_status spx_solve_noalloc(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
+                             int64_t ldx, void *cuda_stream);
+
 /* Message for the last failing call on h (or on handle creation when h is
  * NULL).  The string stays valid until the next call on h. */
 const char *spx_last_error(spx_handle h);

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -583,6 +584,67 @@ spx_status residual(spx_handle h, int nrhs, double *berr)
     return SPX_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free solve: the sweep vectors live in this file-scope buffer.
+// Host code must not hand the symbol itself to a kernel (in host code it is a
+// host-side stand-in); its device address is looked up once per device.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char spx_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+spx_status static_scratch_address(spx_handle h, int device, void **out)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(h, SPX_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, spx_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(h, SPX_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_scratch_addr[device] = p;
+    }
+    *out = g_scratch_addr[device];
+    return SPX_OK;
+}
+
+// One forward + backward sweep from B (original numbering) to X with the
+// sweep vectors Y, Z, Tacc, Xs carved out of `scratch`; launches only.
+template <typename T>
+void enqueue_sweep_noalloc(spx_handle h, int nrhs, const double *B, int64_t ldb, double *X,
+                           int64_t ldx, T *scratch, cudaStream_t s)
+{
+    const spx::Plan &P = h->plan;
+    const size_t len = (size_t)P.n * nrhs;
+    const T *L = (const T *)h->d_L, *U = (const T *)h->d_U, *Dinv = (const T *)h->d_Dinv;
+    T *Y = scratch, *Z = scratch + len, *Tacc = scratch + 2 * len, *Xs = scratch + 3 * len;
+    const bool lu = P.method == SPX_LU;
+    spx::launch_permute_in<T>(P.n, nrhs, B, ldb, h->d_perm, Y, s);
+    cudaMemsetAsync(Tacc, 0, sizeof(T) * len, s);
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
+        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
+        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
+        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
+        const int wmax = h->lvl_wmax[l];
+        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Y, Z, nrhs, s);
+        spx::launch_fwd_off<T>(h->dp, ch, nch, wmax, L, Z, Y, nrhs, s);
+    }
+    for (int32_t l = P.nlevels - 1; l >= 0; --l) {
+        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
+        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
+        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
+        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
+        const int wmax = h->lvl_wmax[l];
+        spx::launch_bwd_off<T>(h->dp, ch, nch, wmax, lu ? U : L, Xs, Tacc, nrhs, s);
+        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Z, Tacc, Xs, nrhs, s);
+    }
+    spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, X, ldx, s);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -965,6 +1027,36 @@ spx_status spx_get_kernel_stats(spx_handle h, spx_kernel_stats *out)
 {
     if (!h || !out) return fail(h, SPX_ERR_ARG, "NULL argument");
     *out = h->kstats;
+    return SPX_OK;
+}
+
+spx_status spx_solve_noalloc(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
+                             int64_t ldx, void *cuda_stream)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (!h->factored) return fail(h, SPX_ERR_STATE, "spx_solve_noalloc before a successful spx_factorize");
+    const spx::Plan &P = h->plan;
+    if (nrhs < 0 || (nrhs > 0 && (!B || !X))) return fail(h, SPX_ERR_ARG, "bad B/X/nrhs");
+    if (ldb < P.n || ldx < P.n) return fail(h, SPX_ERR_ARG, "leading dimension below n");
+    if (nrhs == 0) return SPX_OK;
+    const size_t esz = h->precision == SPX_FP64 ? sizeof(double) : sizeof(float);
+    const size_t need = (size_t)4 * (size_t)P.n * (size_t)nrhs * esz;
+    if (need > kStaticScratchBytes)
+        return fail(h, SPX_ERR_ARG,
+                    "4 * n * nrhs sweep elements (" + std::to_string(need) +
+                        " bytes) exceed the 16 MiB static scratch of spx_solve_noalloc");
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(h, SPX_ERR_STATE, "current device is not the handle's device");
+    void *scratch = nullptr;
+    spx_status st = static_scratch_address(h, dev, &scratch);
+    if (st != SPX_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (h->precision == SPX_FP64)
+        enqueue_sweep_noalloc<double>(h, nrhs, B, ldb, X, ldx, (double *)scratch, s);
+    else
+        enqueue_sweep_noalloc<float>(h, nrhs, B, ldb, X, ldx, (float *)scratch, s);
+    CU(cudaGetLastError());
     return SPX_OK;
 }
 

@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "SPX_OK", 1: "SPX_ERR_ARG", 2: "SPX_ERR_ALLOC", 3: "SPX_ERR_C
 EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_factorize",
             "spx_solve", "spx_get_info", "spx_get_perm", "spx_get_factor", "spx_last_error",
             "spx_free", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
-            "spx_get_panels"]
+            "spx_get_panels", "spx_solve_noalloc"]
 
 
 class spx_options(ctypes.Structure):
@@ -110,12 +110,13 @@ def load():
     lib.spx_set_profiling.argtypes = [_vp, ctypes.c_int]
     lib.spx_get_kernel_stats.argtypes = [_vp, ctypes.POINTER(spx_kernel_stats)]
     lib.spx_get_panels.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    lib.spx_solve_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _i64, _vp, _i64, _vp]
     lib.spx_free.argtypes = [_vp]
     lib.spx_free.restype = None
     lib.spx_update.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]
     for name in ("spx_analyze", "spx_factorize", "spx_solve", "spx_get_info", "spx_get_perm",
                  "spx_get_factor", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
-                 "spx_get_panels"):
+                 "spx_get_panels", "spx_solve_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
