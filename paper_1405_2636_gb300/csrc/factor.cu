@@ -240,6 +240,100 @@ __device__ void chol_blocked(double *a, int w, double replace_tau, int64_t col0,
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident variant for w <= 64 (leading dimension ld >= w).  Block
+// columns of kDB: warp 0 holds the block panel (rows kb..w-1, two rows per
+// lane) in registers and factors it with shuffles; then thread t keeps the
+// block values of its two trailing rows in registers and updates the
+// columns of its warp (j = kb + kDB + warp, + nw, ...), lower part only.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double shfl_d(double v, int src)
+{
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+__device__ void chol_reg64(double *a, int w, int ld, double replace_tau, int64_t col0,
+                           int64_t *err_col, unsigned long long *nrepl)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int kb = 0; kb < w; kb += kDB) {
+        const int bw = min(kDB, w - kb);
+        if (warp == 0) {
+            const int r0 = kb + lane, r1 = kb + lane + 32;
+            const bool h0 = r0 < w, h1 = r1 < w;
+            double p0[kDB], p1[kDB];
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                p0[c] = (h0 && c < bw) ? a[r0 + (kb + c) * ld] : 0.0;
+                p1[c] = (h1 && c < bw) ? a[r1 + (kb + c) * ld] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                if (c < bw) {
+                    const int k = kb + c;
+                    double d = shfl_d(p0[c], c);        // A(k, k): row k is lane c's r0
+                    if (!(d > 0.0)) {
+                        if (lane == 0) {
+                            if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                            else atomicMin((long long *)err_col, (long long)(col0 + k));
+                        }
+                        d = replace_tau > 0.0 ? replace_tau : 1.0;
+                    }
+                    double sq, rs;
+                    sqrt_rsqrt(d, &sq, &rs);
+                    p0[c] = (r0 > k) ? p0[c] * rs : (r0 == k ? sq : p0[c]);
+                    p1[c] *= rs;
+#pragma unroll
+                    for (int c2 = c + 1; c2 < kDB; ++c2) {
+                        if (c2 < bw) {
+                            const double lj = shfl_d(p0[c], c2);   // L(kb + c2, k)
+                            if (r0 >= kb + c2) p0[c2] -= p0[c] * lj;
+                            p1[c2] -= p1[c] * lj;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                if (c < bw) {
+                    if (h0) a[r0 + (kb + c) * ld] = p0[c];
+                    if (h1) a[r1 + (kb + c) * ld] = p1[c];
+                }
+            }
+        }
+        __syncthreads();
+        const int j0 = kb + bw;
+        if (j0 < w) {
+            // this thread's rows and their block values
+            const int i0 = j0 + lane, i1 = j0 + lane + 32;
+            const bool g0 = i0 < w, g1 = i1 < w;
+            double li0[kDB], li1[kDB];
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                li0[c] = (g0 && c < bw) ? a[i0 + (kb + c) * ld] : 0.0;
+                li1[c] = (g1 && c < bw) ? a[i1 + (kb + c) * ld] : 0.0;
+            }
+            for (int j = j0 + warp; j < w; j += nw) {
+                double lj[kDB];
+#pragma unroll
+                for (int c = 0; c < kDB; ++c) lj[c] = c < bw ? a[j + (kb + c) * ld] : 0.0;
+                double x0 = 0.0, y0 = 0.0, x1 = 0.0, y1 = 0.0;
+#pragma unroll
+                for (int c = 0; c < kDB; c += 2) {
+                    x0 += li0[c] * lj[c];
+                    y0 += li0[c + 1] * lj[c + 1];
+                    x1 += li1[c] * lj[c];
+                    y1 += li1[c + 1] * lj[c + 1];
+                }
+                if (g0 && i0 >= j) a[i0 + j * ld] -= x0 + y0;
+                if (g1 && i1 >= j) a[i1 + j * ld] -= x1 + y1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Blocked inversion X = L^{-1} in place (lower triangular, non-unit, column-
 // major leading dimension w) by block rows of kDB, top to bottom:
 //   T(I, J)  = sum_{K = J..I-1} L(I, K) X(K, J)       (all J < I in parallel)
@@ -329,7 +423,8 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
         sm[idx] = (i >= j) ? (double)D[i + (int64_t)j * h] : 0.0;
     }
     __syncthreads();
-    chol_blocked(sm, w, replace_tau, p.pfcol[pid], err_col, nrepl);
+    if (w <= 64) chol_reg64(sm, w, w, replace_tau, p.pfcol[pid], err_col, nrepl);
+    else chol_blocked(sm, w, replace_tau, p.pfcol[pid], err_col, nrepl);
     for (int idx = tid; idx < w * w; idx += nt) {
         int i = idx % w, j = idx / w;
         if (i >= j) D[i + (int64_t)j * h] = (T)sm[idx];
@@ -341,12 +436,216 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
     for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = a[idx];
 }
 
+// ---------------------------------------------------------------------------
+// Diagonal block of width <= W (W = 16, 32, 64; the block is padded with the
+// identity to W).  A dependent FP64 operation costs ~64 cycles on this part,
+// so the column chain is kept short:
+//  * the factorization runs in LDL^T form in FP64 -- per column one Newton
+//    reciprocal of the pivot, the multipliers, and the in-block updates,
+//    with no square root on the chain; warp 0 owns each 8-column block panel
+//    in registers (two rows per lane), all warps apply the trailing updates;
+//  * L = l diag(sqrt(d)) is formed afterwards, all columns in parallel;
+//  * L^{-1} = diag(1/sqrt(d)) l^{-1}: the unit-lower l is inverted by blocks
+//    (8 x 8 diagonal blocks by single lanes, then pairs of blocks merged with
+//    X21 = -C^{-1} (B A^{-1})), in the factor's arithmetic.
+// ---------------------------------------------------------------------------
+template <typename T, int W>
+__global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t *__restrict__ panels,
+                                                        T *__restrict__ L, T *__restrict__ Dinv,
+                                                        const double *replace_tau_p,
+                                                        int64_t *err_col, unsigned long long *nrepl)
+{
+    constexpr int LD = W + 1;
+    constexpr int NT = 256, NW = NT / 32;
+    extern __shared__ double sm[];
+    double *a = sm;                          // W x LD, FP64 working block
+    double *lA = a + W * LD;                 // W x kDB unscaled block columns (ld W)
+    double *dv = lA + W * kDB;               // pivots
+    double *rsv = dv + W;                    // 1 / sqrt(pivot)
+    T *x = reinterpret_cast<T *>(rsv + W);   // W x LD inverse workspace
+    T *tmp = x + W * LD;                     // (W/2)^2
+    const double replace_tau = *replace_tau_p;
+    const int pid = panels[blockIdx.x];
+    const int w = p.pw[pid], h = p.ph[pid];
+    const int64_t col0 = p.pfcol[pid];
+    T *D = L + p.pval[pid];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int idx = tid; idx < W * W; idx += NT) {
+        const int i = idx % W, j = idx / W;
+        double v = 0.0;
+        if (i < w && j < w) {
+            if (i >= j) v = (double)D[i + (int64_t)j * h];
+        } else if (i == j) {
+            v = 1.0;
+        }
+        a[i + j * LD] = v;
+    }
+    __syncthreads();
+
+    for (int kb = 0; kb < W; kb += kDB) {
+        if (warp == 0) {
+            const int r0 = kb + lane, r1 = kb + lane + 32;
+            double p0[kDB], p1[kDB];
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                p0[c] = r0 < W ? a[r0 + (kb + c) * LD] : 0.0;
+                p1[c] = r1 < W ? a[r1 + (kb + c) * LD] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                const int k = kb + c;
+                double d = shfl_d(p0[c], c);                 // A(k, k) from lane c
+                if (!(d > 0.0)) {
+                    if (lane == 0 && k < w) {
+                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                        else atomicMin((long long *)err_col, (long long)(col0 + k));
+                    }
+                    d = replace_tau > 0.0 ? replace_tau : 1.0;
+                }
+                const double r = rcp_newton(d);
+                const double u0 = r0 > k ? p0[c] : 0.0, u1 = p1[c];   // A-form of column k
+                const double l0 = u0 * r, l1 = u1 * r;                  // multipliers
+#pragma unroll
+                for (int c2 = c + 1; c2 < kDB; ++c2) {
+                    const double ac = shfl_d(u0, c2);                   // A(kb + c2, k)
+                    if (r0 >= kb + c2) p0[c2] = fma(-l0, ac, p0[c2]);
+                    p1[c2] = fma(-l1, ac, p1[c2]);
+                }
+                if (r0 < W) lA[r0 + c * W] = u0;
+                if (r1 < W) lA[r1 + c * W] = u1;
+                p0[c] = r0 > k ? l0 : (r0 == k ? 1.0 : 0.0);
+                p1[c] = l1;
+                if (lane == c) dv[k] = d;
+            }
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                if (r0 < W) a[r0 + (kb + c) * LD] = p0[c];
+                if (r1 < W) a[r1 + (kb + c) * LD] = p1[c];
+            }
+        }
+        __syncthreads();
+        const int j0 = kb + kDB;
+        if (j0 < W) {
+            const int i0 = j0 + lane, i1 = j0 + lane + 32;
+            const bool g0 = i0 < W, g1 = i1 < W;
+            double li0[kDB], li1[kDB];
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                li0[c] = g0 ? a[i0 + (kb + c) * LD] : 0.0;
+                li1[c] = g1 ? a[i1 + (kb + c) * LD] : 0.0;
+            }
+            for (int j = j0 + warp; j < W; j += NW) {
+                double aj[kDB];
+#pragma unroll
+                for (int c = 0; c < kDB; ++c) aj[c] = lA[j + c * W];
+                double x0 = 0.0, y0 = 0.0, x1 = 0.0, y1 = 0.0;
+#pragma unroll
+                for (int c = 0; c < kDB; c += 2) {
+                    x0 = fma(li0[c], aj[c], x0);
+                    y0 = fma(li0[c + 1], aj[c + 1], y0);
+                    x1 = fma(li1[c], aj[c], x1);
+                    y1 = fma(li1[c + 1], aj[c + 1], y1);
+                }
+                if (g0 && i0 >= j) a[i0 + j * LD] -= x0 + y0;
+                if (g1 && i1 >= j) a[i1 + j * LD] -= x1 + y1;
+            }
+        }
+        __syncthreads();
+    }
+
+    // L = l diag(sqrt(d)); keep 1/sqrt(d) for the inverse
+    if (tid < W) {
+        double sq, rs;
+        sqrt_rsqrt(dv[tid], &sq, &rs);
+        dv[tid] = sq;
+        rsv[tid] = rs;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < W * W; idx += NT) {
+        const int i = idx % W, j = idx / W;
+        const double l = a[i + j * LD];
+        if (i < w && j < w && i >= j) D[i + (int64_t)j * h] = (T)(i == j ? dv[j] : l * dv[j]);
+        x[i + j * LD] = (T)(i > j ? l : (i == j ? 1.0 : 0.0));
+    }
+    __syncthreads();
+
+    // unit-lower inverse: 8 x 8 diagonal blocks first
+    if (warp < W / kDB && lane < kDB) {
+        const int o = warp * kDB, jj = lane;
+        T xr[kDB];
+#pragma unroll
+        for (int q = 0; q < kDB; ++q) xr[q] = q == jj ? (T)1 : (T)0;
+#pragma unroll
+        for (int kk = 0; kk < kDB; ++kk) {
+            if (kk >= jj) {
+#pragma unroll
+                for (int ii = kk + 1; ii < kDB; ++ii) xr[ii] -= x[(o + ii) + (o + kk) * LD] * xr[kk];
+            }
+        }
+        __syncwarp(0xffu);
+#pragma unroll
+        for (int ii = 0; ii < kDB; ++ii)
+            if (ii > jj) x[(o + ii) + (o + jj) * LD] = xr[ii];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int sz = kDB; sz < W; sz *= 2) {
+        const int npair = W / (2 * sz);
+        for (int e = tid; e < npair * sz * sz; e += NT) {
+            const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
+            const int o = pr * 2 * sz;
+            T acc = (T)0;
+            for (int k = j; k < sz; ++k) acc += x[(o + sz + i) + (o + k) * LD] * x[(o + k) + (o + j) * LD];
+            tmp[pr * sz * sz + i + j * sz] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < npair * sz * sz; e += NT) {
+            const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
+            const int o = pr * 2 * sz;
+            T acc = tmp[pr * sz * sz + i + j * sz];   // C^{-1} has a unit diagonal
+            for (int k = 0; k < i; ++k) acc += x[(o + sz + i) + (o + sz + k) * LD] * tmp[pr * sz * sz + k + j * sz];
+            x[(o + sz + i) + (o + j) * LD] = -acc;
+        }
+        __syncthreads();
+    }
+    T *Mi = Dinv + p.pinv[pid];
+    for (int idx = tid; idx < w * w; idx += NT) {
+        const int i = idx % w, j = idx / w;
+        Mi[idx] = i >= j ? (T)((double)x[i + j * LD] * rsv[i]) : (T)0;
+    }
+}
+
+template <typename T, int W>
+constexpr size_t ldl_smem_bytes()
+{
+    return sizeof(double) * ((size_t)W * (W + 1) + (size_t)W * kDB + 2 * W) +
+           sizeof(T) * ((size_t)W * (W + 1) + (size_t)(W / 2) * (W / 2));
+}
+
+template <typename T, int W>
+void launch_ldl(const DevPlan &p, const int32_t *panels, int count, T *L, T *Dinv,
+                const double *replace_tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s)
+{
+    static bool once = false;
+    const size_t smem = ldl_smem_bytes<T, W>();
+    if (!once) {
+        cudaFuncSetAttribute(potrf_ldl_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        once = true;
+    }
+    potrf_ldl_kernel<T, W><<<count, 256, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl);
+}
+
 template <typename T>
 void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, int threads, T *L, T *Dinv,
                   const double *replace_tau, int64_t *err_col, unsigned long long *nrepl,
                   cudaStream_t s)
 {
     if (count <= 0) return;
+    if (wmax <= 16) return launch_ldl<T, 16>(p, panels, count, L, Dinv, replace_tau, err_col, nrepl, s);
+    if (wmax <= 32) return launch_ldl<T, 32>(p, panels, count, L, Dinv, replace_tau, err_col, nrepl, s);
+    if (wmax <= 64) return launch_ldl<T, 64>(p, panels, count, L, Dinv, replace_tau, err_col, nrepl, s);
+    (void)threads;
     static bool once = false;
     if (!once) {
         cudaFuncSetAttribute(potrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

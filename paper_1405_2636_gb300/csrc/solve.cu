@@ -60,6 +60,8 @@ void launch_permute_out(int64_t n, int nrhs, const T *Y, const int64_t *perm, do
 // ---------------------------------------------------------------------------
 // Forward, diagonal block: Z_p = Linv_p Y_p, rows [32 y, 32 y + 32) of the
 // panel per CTA (grid.y).  LU: Linv is unit (the diagonal slot holds U^{-1}).
+// The 32 rows of Linv are staged in shared memory first (coalesced bulk
+// loads), so the products never wait on one global load at a time.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) fwd_diag_kernel(DevPlan p, const int32_t *__restrict__ panels,
@@ -68,37 +70,52 @@ __global__ void __launch_bounds__(256) fwd_diag_kernel(DevPlan p, const int32_t 
                                                        int nrhs)
 {
     extern __shared__ unsigned char smraw[];
-    T *ys = reinterpret_cast<T *>(smraw);       // ys[c * w + k]
     const int pid = panels[blockIdx.x];
     const int w = p.pw[pid];
     const int i0 = blockIdx.y * kDiagRows;
     if (i0 >= w) return;
+    T *ys = reinterpret_cast<T *>(smraw);        // ys[c * w + k]
+    T *ms = ys + (size_t)w * kRhsChunk;           // ms[k * 33 + li] = Linv(i0 + li, k)
     const T *Mi = Dinv + p.pinv[pid];
     const int64_t f = p.pfcol[pid], n = p.n;
     const int tid = threadIdx.x;
     const int li = tid & 31, cg = tid >> 5;     // row within the block, column group of 8
     const int i = i0 + li;
+    const int nrow = min(kDiagRows, w - i0);
+    const int kend = min(w, i0 + kDiagRows);     // Linv(i, k) = 0 for k > i
+    for (int e = tid; e < kend * kDiagRows; e += blockDim.x) {
+        const int r = e & 31, k = e >> 5;
+        ms[k * 33 + r] = r < nrow ? Mi[(i0 + r) + (int64_t)k * w] : (T)0;
+    }
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
-        const int kend = min(w, i0 + kDiagRows);   // rows of Linv below i0+32 are not needed
         for (int e = tid; e < kend * nc; e += blockDim.x) {
             const int k = e % kend, c = e / kend;
             ys[c * w + k] = Y[f + k + (int64_t)(c0 + c) * n];
         }
         __syncthreads();
-        if (i < w) {
+        if (li < nrow) {
             for (int c = cg; c < nc; c += 8) {
-                T acc = unit ? ys[c * w + i] : (T)0;
+                const T *yc = ys + c * w;
+                T a0 = unit ? yc[i] : (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
                 const int kl = unit ? i : i + 1;
-                for (int k = 0; k < kl; ++k) acc += Mi[i + k * w] * ys[c * w + k];
-                Z[f + i + (int64_t)(c0 + c) * n] = acc;
+                int k = 0;
+                for (; k + 3 < kl; k += 4) {
+                    a0 += ms[k * 33 + li] * yc[k];
+                    a1 += ms[(k + 1) * 33 + li] * yc[k + 1];
+                    a2 += ms[(k + 2) * 33 + li] * yc[k + 2];
+                    a3 += ms[(k + 3) * 33 + li] * yc[k + 3];
+                }
+                for (; k < kl; ++k) a0 += ms[k * 33 + li] * yc[k];
+                Z[f + i + (int64_t)(c0 + c) * n] = (a0 + a1) + (a2 + a3);
             }
         }
         __syncthreads();
     }
 }
 
-// Forward, off-diagonal rows of one chunk: Y[rows(i)] -= L(i, :) Z_p.
+// Forward, off-diagonal rows of one chunk: Y[rows(i)] -= L(i, :) Z_p, with
+// the 64 x w block of L staged in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                       const T *__restrict__ L,
@@ -106,16 +123,22 @@ __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk 
                                                       int nrhs)
 {
     extern __shared__ unsigned char smraw[];
-    T *zp = reinterpret_cast<T *>(smraw);       // zp[c * w + k]
     const RowChunk ch = chunks[blockIdx.x];
     const int pid = ch.panel;
     const int w = p.pw[pid], h = p.ph[pid];
+    T *zp = reinterpret_cast<T *>(smraw);        // zp[c * w + k]
+    T *lsm = zp + (size_t)w * kRhsChunk;          // lsm[k * 64 + r]
     const T *Pn = L + p.pval[pid];
     const int64_t f = p.pfcol[pid], n = p.n;
     const int32_t *rows = p.rows + p.prow[pid];
     const int tid = threadIdx.x;
     const int r = tid & 63, g = tid >> 6;   // 64 rows x 4 column groups
     const int i = ch.r0 + r;
+    const int nr = min(64, h - ch.r0);
+    for (int e = tid; e < w * 64; e += blockDim.x) {
+        const int rr = e & 63, k = e >> 6;
+        lsm[e] = rr < nr ? Pn[ch.r0 + rr + (int64_t)k * h] : (T)0;
+    }
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < w * nc; e += blockDim.x) {
@@ -123,10 +146,10 @@ __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk 
             zp[c * w + k] = Z[f + k + (int64_t)(c0 + c) * n];
         }
         __syncthreads();
-        if (i < h) {
+        if (r < nr) {
             T acc[4] = {(T)0, (T)0, (T)0, (T)0};
             for (int k = 0; k < w; ++k) {
-                const T l = Pn[i + (int64_t)k * h];
+                const T l = lsm[k * 64 + r];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int c = g + 4 * q;
@@ -225,9 +248,18 @@ __global__ void __launch_bounds__(256) bwd_diag_kernel(DevPlan p, const int32_t 
         __syncthreads();
         if (li < nrow) {
             for (int c = cg; c < nc; c += 8) {
-                T acc = (T)0;
-                for (int k = i; k < w; ++k) acc += ms[li * (w + 1) + k] * ys[c * w + k];
-                X[f + i + (int64_t)(c0 + c) * n] = acc;
+                const T *yc = ys + c * w;
+                const T *mr = ms + li * (w + 1);
+                T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+                int k = i;
+                for (; k + 3 < w; k += 4) {
+                    a0 += mr[k] * yc[k];
+                    a1 += mr[k + 1] * yc[k + 1];
+                    a2 += mr[k + 2] * yc[k + 2];
+                    a3 += mr[k + 3] * yc[k + 3];
+                }
+                for (; k < w; ++k) a0 += mr[k] * yc[k];
+                X[f + i + (int64_t)(c0 + c) * n] = (a0 + a1) + (a2 + a3);
             }
         }
         __syncthreads();
@@ -239,8 +271,15 @@ void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, int wma
                      int unit, const T *Y, T *Z, int nrhs, cudaStream_t s)
 {
     if (count <= 0) return;
+    static bool once = false;
+    if (!once) {
+        cudaFuncSetAttribute(fwd_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * ((size_t)kMaxWidth * kRhsChunk + (size_t)kMaxWidth * 33)));
+        once = true;
+    }
     dim3 grid(count, (wmax + kDiagRows - 1) / kDiagRows);
-    fwd_diag_kernel<T><<<grid, 256, sizeof(T) * wmax * kRhsChunk, s>>>(p, panels, Dinv, unit, Y, Z, nrhs);
+    const size_t smem = sizeof(T) * ((size_t)wmax * kRhsChunk + (size_t)wmax * 33);
+    fwd_diag_kernel<T><<<grid, 256, smem, s>>>(p, panels, Dinv, unit, Y, Z, nrhs);
 }
 
 template <typename T>
@@ -248,7 +287,14 @@ void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wma
                     const T *Z, T *Y, int nrhs, cudaStream_t s)
 {
     if (count <= 0) return;
-    fwd_off_kernel<T><<<count, 256, sizeof(T) * wmax * kRhsChunk, s>>>(p, chunks, L, Z, Y, nrhs);
+    static bool once = false;
+    if (!once) {
+        cudaFuncSetAttribute(fwd_off_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * ((size_t)kMaxWidth * kRhsChunk + (size_t)kMaxWidth * 64)));
+        once = true;
+    }
+    const size_t smem = sizeof(T) * ((size_t)wmax * kRhsChunk + (size_t)wmax * 64);
+    fwd_off_kernel<T><<<count, 256, smem, s>>>(p, chunks, L, Z, Y, nrhs);
 }
 
 template <typename T>
@@ -388,5 +434,6 @@ template void launch_fwd_diag<float>(const DevPlan &, const int32_t *, int, int,
 template void launch_fwd_off<float>(const DevPlan &, const RowChunk *, int, int, const float *, const float *, float *, int, cudaStream_t);
 template void launch_bwd_off<float>(const DevPlan &, const RowChunk *, int, int, const float *, const float *, float *, int, cudaStream_t);
 template void launch_bwd_diag<float>(const DevPlan &, const int32_t *, int, int, const float *, int, const float *, const float *, float *, int, cudaStream_t);
+
 
 }  // namespace spx
