@@ -60,9 +60,11 @@ struct spx_handle_s {
     spx::TcTile *d_tctiles = nullptr;
     int kpad = 0;                     // operand-copy row length
     int64_t op_rows = 0;              // operand-copy rows (sum of panel heights)
-    void *d_opc = nullptr;            // operand copy (TF32 floats or BF16)
-    int opc_bf16 = -1;
-    alignas(64) unsigned char tmap[128];   // CUtensorMap over d_opc
+    void *d_opc = nullptr;            // operand copy (TF32 floats, BF16, or the hi half of split TF32)
+    void *d_opc_lo = nullptr;         // lo half of split TF32
+    int opc_kind = -1;                // 0 tf32, 1 bf16, 2 split tf32
+    alignas(64) unsigned char tmap[128];     // CUtensorMap over d_opc
+    alignas(64) unsigned char tmap_lo[128];  // CUtensorMap over d_opc_lo
     int *d_tcerr = nullptr;
     double upd_flops_tc = 0, upd_elems_tc = 0, upd_op_elems_tc = 0;   // share of the tensor-core tasks
 
@@ -351,9 +353,10 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
     T *L = (T *)h->d_L, *U = (T *)h->d_U, *Dinv = (T *)h->d_Dinv;
     const size_t elems = (size_t)P.pval[P.npanels];
     const bool lu = P.method == SPX_LU;
-    const bool tc = !lu && (prec == SPX_TF32 || prec == SPX_BF16) && sizeof(T) == 4;
+    const bool tc = !lu && (prec == SPX_TF32 || prec == SPX_BF16 || prec == SPX_FP32) && sizeof(T) == 4;
     void *opc = tc ? h->d_opc : nullptr;
-    const int op_bf16 = prec == SPX_BF16;
+    void *opc_lo = tc ? h->d_opc_lo : nullptr;
+    const int op_kind = prec == SPX_BF16 ? 1 : (prec == SPX_FP32 ? 2 : 0);
     int64_t &cnt = h->cnt;
     mk.mark(-1);
     init_scalars_kernel<<<1, 1, 0, s>>>(h->d_err, h->d_nrepl, h->d_anorm);
@@ -395,7 +398,7 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
         (void)np;
         mk.mark(SPX_K_DIAG);
         if (!lu) {
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LLT, opc, h->kpad, op_bf16, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LLT, opc, opc_lo, h->kpad, op_kind, s);
             cnt += nch > 0;
             mk.mark(SPX_K_TRSM);
             if (!tc) {
@@ -409,16 +412,16 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
                 const int ntt = (int)(h->tctile_ptr[l + 1] - h->tctile_ptr[l]);
                 spx::launch_update<T>(h->dp, h->d_tasks, ts, nts, L, L, L, 1, 0, s);
                 mk.mark(SPX_K_UPDATE);
-                spx::launch_update_tc(h->tmap, op_bf16, h->dp, h->d_tasks, tt, ntt, (float *)L, 1,
-                                      h->d_tcerr, s);
+                spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, tt, ntt,
+                                      (float *)L, 1, h->d_tcerr, s);
                 mk.mark(SPX_K_UPDATE_TC);
                 cnt += (nts > 0) + (ntt > 0);
             }
         } else {
             const UpdTile *tu = h->d_tilesu + h->tileu_ptr[l];
             const int ntu = (int)(h->tileu_ptr[l + 1] - h->tileu_ptr[l]);
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LU_L, nullptr, 0, 0, s);
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, U, spx::TRSM_LU_U, nullptr, 0, 0, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LU_L, nullptr, nullptr, 0, 0, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, U, spx::TRSM_LU_U, nullptr, nullptr, 0, 0, s);
             cnt += 2 * (nch > 0);
             mk.mark(SPX_K_TRSM);
             spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, U, L, 0, 0, s);
@@ -495,23 +498,28 @@ void body_factor(spx_handle h, int prec, bool)
     else enqueue_factorization<float>(h, true, mk, prec);
 }
 
-// Operand copy for the tensor-core updates, allocated (zeroed) on first use.
-spx_status ensure_operand_copy(spx_handle h, int bf16)
+// Operand copies for the tensor-core updates, allocated (zeroed) on first use.
+spx_status ensure_operand_copy(spx_handle h, int kind)
 {
-    if (h->d_opc && h->opc_bf16 == bf16) return SPX_OK;
+    if (h->d_opc && h->opc_kind == kind) return SPX_OK;
     dfree(h, h->d_opc);
-    h->d_opc = nullptr;
+    dfree(h, h->d_opc_lo);
+    h->d_opc = h->d_opc_lo = nullptr;
+    h->opc_kind = -1;
+    const int bf16 = kind == 1;
     const size_t esz = bf16 ? 2 : 4;
     const size_t bytes = (size_t)h->op_rows * h->kpad * esz;
-    char *p = nullptr;
-    spx_status st = dalloc(h, &p, bytes);
-    if (st != SPX_OK) return st;
-    CU(cudaMemset(p, 0, bytes));
-    if (spx::make_operand_map(h->tmap, p, h->op_rows, h->kpad, bf16) != 0)
-        return fail(h, SPX_ERR_CUDA, "cuTensorMapEncodeTiled failed for the operand copy");
-    h->d_opc = p;
-    h->opc_bf16 = bf16;
-    if (h->fgraph) {   // the graph captured the old descriptor and buffer
+    for (int part = 0; part < (kind == 2 ? 2 : 1); ++part) {
+        char *p = nullptr;
+        spx_status st = dalloc(h, &p, bytes);
+        if (st != SPX_OK) return st;
+        CU(cudaMemset(p, 0, bytes));
+        if (spx::make_operand_map(part ? h->tmap_lo : h->tmap, p, h->op_rows, h->kpad, bf16) != 0)
+            return fail(h, SPX_ERR_CUDA, "cuTensorMapEncodeTiled failed for the operand copy");
+        (part ? h->d_opc_lo : h->d_opc) = p;
+    }
+    h->opc_kind = kind;
+    if (h->fgraph) {   // the graph captured the old descriptors and buffers
         cudaGraphExecDestroy(h->fgraph);
         h->fgraph = nullptr;
         h->fgraph_prec = -1;
@@ -772,8 +780,9 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         }
     }
     h->factored = false;
-    if (P.method == SPX_LLT && (precision == SPX_TF32 || precision == SPX_BF16)) {
-        if ((st = ensure_operand_copy(h, precision == SPX_BF16 ? 1 : 0))) return st;
+    if (P.method == SPX_LLT && precision != SPX_FP64) {
+        if ((st = ensure_operand_copy(h, precision == SPX_BF16 ? 1 : (precision == SPX_FP32 ? 2 : 0))))
+            return st;
     }
     fence_from(h, cuda_stream);
     CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a,
@@ -819,8 +828,8 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         }
         const double e = fp64 ? 8.0 : 4.0;
         const double nfac = (P.method == SPX_LU) ? 2.0 : 1.0;
-        const bool tcm = P.method == SPX_LLT && (precision == SPX_TF32 || precision == SPX_BF16);
-        const double eop = precision == SPX_BF16 ? 2.0 : 4.0;
+        const bool tcm = P.method == SPX_LLT && precision != SPX_FP64;
+        const double eop = precision == SPX_BF16 ? 2.0 : (precision == SPX_FP32 ? 8.0 : 4.0);
         K.flops[SPX_K_DIAG] = P.diag_flops;
         K.flops[SPX_K_TRSM] = P.trsm_flops;
         K.flops[SPX_K_UPDATE] = P.update_flops - (tcm ? h->upd_flops_tc : 0.0);

@@ -755,7 +755,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                         const T *__restrict__ Dinv,
                                                         T *__restrict__ X, int mode, void *opc,
-                                                        int kpad, int op_bf16)
+                                                        void *opc_lo, int kpad, int op_kind)
 {
     extern __shared__ unsigned char smraw[];
     T *Xs = reinterpret_cast<T *>(smraw);      // Xs[k * 64 + r], k < wpad
@@ -830,8 +830,14 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                     const int j = c0 + ty + 16 * b;
                     if (j >= w) continue;
                     const int64_t o = (orow0 + r) * kpad + j;
-                    if (op_bf16) reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16((float)acc[a][b]);
-                    else reinterpret_cast<float *>(opc)[o] = round_tf32((float)acc[a][b]);
+                    const float v = (float)acc[a][b];
+                    if (op_kind == 1) {
+                        reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(v);
+                    } else {
+                        const float hi = round_tf32(v);
+                        reinterpret_cast<float *>(opc)[o] = hi;
+                        if (op_kind == 2) reinterpret_cast<float *>(opc_lo)[o] = round_tf32(v - hi);
+                    }
                 }
             }
         }
@@ -842,15 +848,19 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
         for (int e = tid; e < nr * padw; e += 256) {
             const int r = e / padw, j = w + e % padw;
             const int64_t o = (orow0 + r) * kpad + j;
-            if (op_bf16) reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(0.0f);
-            else reinterpret_cast<float *>(opc)[o] = 0.0f;
+            if (op_kind == 1) {
+                reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(0.0f);
+            } else {
+                reinterpret_cast<float *>(opc)[o] = 0.0f;
+                if (op_kind == 2) reinterpret_cast<float *>(opc_lo)[o] = 0.0f;
+            }
         }
     }
 }
 
 template <typename T>
 void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
-                 T *X, int mode, void *opc, int kpad, int op_bf16, cudaStream_t s)
+                 T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s)
 {
     if (count <= 0) return;
     static bool once = false;
@@ -860,7 +870,7 @@ void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, 
         once = true;
     }
     const size_t smem = sizeof(T) * (size_t)((wmax + 15) & ~15) * kTrsmRows;
-    trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, kpad, op_bf16);
+    trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, opc_lo, kpad, op_kind);
 }
 
 // ---------------------------------------------------------------------------
@@ -1032,8 +1042,8 @@ template void launch_potrf<double>(const DevPlan &, const int32_t *, int, int, i
 template void launch_potrf<float>(const DevPlan &, const int32_t *, int, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
 template void launch_getrf<double>(const DevPlan &, const int32_t *, int, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
 template void launch_getrf<float>(const DevPlan &, const int32_t *, int, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, void *, int, int, cudaStream_t);
-template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, void *, int, int, cudaStream_t);
+template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, void *, void *, int, int, cudaStream_t);
+template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, void *, void *, int, int, cudaStream_t);
 template void launch_update<double>(const DevPlan &, const DevTask *, const UpdTile *, int, const double *, const double *, double *, int, int, cudaStream_t);
 template void launch_update<float>(const DevPlan &, const DevTask *, const UpdTile *, int, const float *, const float *, float *, int, int, cudaStream_t);
 

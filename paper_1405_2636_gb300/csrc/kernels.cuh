@@ -68,18 +68,20 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
                   const double *tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s);
 
 // opc (may be null): K-major operand copy for the tensor-core updates, rows
-// at prow[panel] + r with kpad elements each; op_bf16 selects BF16 storage,
-// otherwise TF32-rounded FP32.
+// at prow[panel] + r with kpad elements each.  op_kind 0: TF32-rounded FP32;
+// 1: BF16; 2: split TF32, hi = tf32(x) in opc and lo = tf32(x - hi) in opc_lo.
 template <typename T>
 void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
-                 T *X, int mode, void *opc, int kpad, int op_bf16, cudaStream_t s);
+                 T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s);
 
-// Tensor-core update (update_tc.cu).  tmap: a CUtensorMap over the operand
-// copy (make_operand_map); err receives 1 if a bounded wait expired.
-size_t tc_smem_bytes();
+// Tensor-core update (update_tc.cu).  tmap / tmap_lo: CUtensorMaps over the
+// operand copies (make_operand_map; tmap_lo is used for kind 2 only); err
+// receives 1 if a bounded wait expired.
+size_t tc_smem_bytes(int kind);
 int make_operand_map(void *tmap_out, void *base, int64_t rows, int kpad, int bf16);
-void launch_update_tc(const void *tmap, int bf16, const DevPlan &p, const DevTask *tasks,
-                      const TcTile *tiles, int count, float *C, int lower, int *err, cudaStream_t s);
+void launch_update_tc(const void *tmap, const void *tmap_lo, int kind, const DevPlan &p,
+                      const DevTask *tasks, const TcTile *tiles, int count, float *C, int lower,
+                      int *err, cudaStream_t s);
 
 template <typename T>
 void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles, int count,

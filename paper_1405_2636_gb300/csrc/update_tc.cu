@@ -1,7 +1,9 @@
 // update_tc.cu -- the supernodal update (Sec. V-B) on the 5th-generation
-// tensor cores: W = A_rows(M) * A_rows(N)^T with TF32 or BF16 operands and an
-// FP32 accumulator in tensor memory, then the index-mapped scatter-subtract of
-// W into the FP32 target panel (fused epilogue, no temporary buffer).
+// tensor cores: W = A_rows(M) * A_rows(N)^T with TF32 or BF16 operands (or
+// FP32 operands split into two TF32 halves, hi*hi + hi*lo + lo*hi, for
+// FP32-level products) and an FP32 accumulator in tensor memory, then the
+// index-mapped scatter-subtract of W into the FP32 target panel (fused
+// epilogue, no temporary buffer).
 //
 // Operands come from the K-major operand copy of every panel (row r of panel
 // p at operand row prow[p] + r, Kpad elements per row, TF32-rounded or BF16),
@@ -132,20 +134,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// KIND 0: TF32 operands (32 per 128-byte row chunk); KIND 1: BF16 (64).
+// KIND 0: TF32 operands (32 per 128-byte row chunk); KIND 1: BF16 (64);
+// KIND 2: split TF32 (hi and lo copies, three MMAs per K step).
 template <int KIND>
 __global__ void __launch_bounds__(128, 1)
-    update_tc_kernel(const __grid_constant__ CUtensorMap opmap, DevPlan p,
+    update_tc_kernel(const __grid_constant__ CUtensorMap opmap,
+                     const __grid_constant__ CUtensorMap opmap_lo, DevPlan p,
                      const DevTask *__restrict__ tasks, const TcTile *__restrict__ tiles,
                      float *__restrict__ C, int lower, int *err)
 {
-    constexpr int kElems = KIND == 0 ? 32 : 64;           // K elements per stage
-    constexpr uint32_t kIdesc = make_idesc(KIND == 0 ? 2u : 1u);
+    constexpr int kElems = KIND == 1 ? 64 : 32;           // K elements per stage
+    constexpr uint32_t kIdesc = make_idesc(KIND == 1 ? 1u : 2u);
+    constexpr int kParts = KIND == 2 ? 2 : 1;              // hi (and lo) copies per operand
+    constexpr uint32_t kStageTx = 2u * kParts * kTileBytes;
     extern __shared__ unsigned char smraw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    // stage s: A_hi, B_hi (, A_lo, B_lo) tiles of kTileBytes each
     unsigned char *sA = base;
     unsigned char *sB = base + kStages * kTileBytes;
+    unsigned char *sAl = base + 2 * kStages * kTileBytes;
+    unsigned char *sBl = base + 3 * kStages * kTileBytes;
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ __align__(8) uint64_t done;
@@ -184,9 +193,13 @@ __global__ void __launch_bounds__(128, 1)
         const int ya = (int)(rbase + tl.m0), yb = (int)(rbase + tl.n0);
         bool ok = true;
         for (int kc = 0; kc < nk && kc < kStages; ++kc) {
-            mbar_expect_tx(&full[kc], 2 * kTileBytes);
+            mbar_expect_tx(&full[kc], kStageTx);
             tma_load_2d(sA + kc * kTileBytes, &opmap, &full[kc], kc * kElems, ya);
             tma_load_2d(sB + kc * kTileBytes, &opmap, &full[kc], kc * kElems, yb);
+            if (KIND == 2) {
+                tma_load_2d(sAl + kc * kTileBytes, &opmap_lo, &full[kc], kc * kElems, ya);
+                tma_load_2d(sBl + kc * kTileBytes, &opmap_lo, &full[kc], kc * kElems, yb);
+            }
         }
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % kStages;
@@ -197,19 +210,32 @@ __global__ void __launch_bounds__(128, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+            const uint32_t al = smem_u32(sAl + s * kTileBytes), bl = smem_u32(sBl + s * kTileBytes);
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)   // 32 bytes of K per MMA
-                mma<KIND>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
-                          (kc > 0 || ks > 0) ? 1u : 0u);
+            for (int ks = 0; ks < 4; ++ks) {   // 32 bytes of K per MMA
+                if (KIND == 2) {               // small products first
+                    mma<0>(tmem, sw128_desc(al + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
+                           (kc > 0 || ks > 0) ? 1u : 0u);
+                    mma<0>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(bl + 32 * ks), kIdesc, 1u);
+                    mma<0>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc, 1u);
+                } else {
+                    mma<KIND>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
+                              (kc > 0 || ks > 0) ? 1u : 0u);
+                }
+            }
             mma_commit(&empty[s]);
             if (kc + kStages < nk) {
                 if (!mbar_wait(&empty[s], ph)) {
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(&full[s], 2 * kTileBytes);
+                mbar_expect_tx(&full[s], kStageTx);
                 tma_load_2d(sA + s * kTileBytes, &opmap, &full[s], (kc + kStages) * kElems, ya);
                 tma_load_2d(sB + s * kTileBytes, &opmap, &full[s], (kc + kStages) * kElems, yb);
+                if (KIND == 2) {
+                    tma_load_2d(sAl + s * kTileBytes, &opmap_lo, &full[s], (kc + kStages) * kElems, ya);
+                    tma_load_2d(sBl + s * kTileBytes, &opmap_lo, &full[s], (kc + kStages) * kElems, yb);
+                }
             }
         }
         mma_commit(&done);   // arrives once every MMA issued above has completed
@@ -259,7 +285,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 }  // namespace
 
-size_t tc_smem_bytes() { return (size_t)2 * kStages * kTileBytes + 1024; }
+size_t tc_smem_bytes(int kind) { return (size_t)(kind == 2 ? 4 : 2) * kStages * kTileBytes + 1024; }
 
 int make_operand_map(void *tmap_out, void *base, int64_t rows, int kpad, int bf16)
 {
@@ -286,25 +312,33 @@ int make_operand_map(void *tmap_out, void *base, int64_t rows, int kpad, int bf1
     return r == CUDA_SUCCESS ? 0 : -2;
 }
 
-void launch_update_tc(const void *tmap, int bf16, const DevPlan &p, const DevTask *tasks,
-                      const TcTile *tiles, int count, float *C, int lower, int *err, cudaStream_t s)
+void launch_update_tc(const void *tmap, const void *tmap_lo, int kind, const DevPlan &p,
+                      const DevTask *tasks, const TcTile *tiles, int count, float *C, int lower,
+                      int *err, cudaStream_t s)
 {
     if (count <= 0) return;
     const CUtensorMap &m = *reinterpret_cast<const CUtensorMap *>(tmap);
-    const size_t smem = tc_smem_bytes();
-    static bool once0 = false, once1 = false;
-    if (bf16) {
-        if (!once1) {
+    const CUtensorMap &ml = *reinterpret_cast<const CUtensorMap *>(kind == 2 ? tmap_lo : tmap);
+    const size_t smem = tc_smem_bytes(kind);
+    static bool once[3] = {false, false, false};
+    if (kind == 1) {
+        if (!once[1]) {
             cudaFuncSetAttribute(update_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            once1 = true;
+            once[1] = true;
         }
-        update_tc_kernel<1><<<count, 128, smem, s>>>(m, p, tasks, tiles, C, lower, err);
+        update_tc_kernel<1><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
+    } else if (kind == 2) {
+        if (!once[2]) {
+            cudaFuncSetAttribute(update_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            once[2] = true;
+        }
+        update_tc_kernel<2><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
     } else {
-        if (!once0) {
+        if (!once[0]) {
             cudaFuncSetAttribute(update_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            once0 = true;
+            once[0] = true;
         }
-        update_tc_kernel<0><<<count, 128, smem, s>>>(m, p, tasks, tiles, C, lower, err);
+        update_tc_kernel<0><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
     }
 }
 
