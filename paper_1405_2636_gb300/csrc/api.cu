@@ -82,6 +82,12 @@ struct spx_handle_s {
     cudaGraphExec_t fgraph = nullptr;
     int fgraph_prec = -1;
 
+    // FGMRES workspace: Krylov basis V (restart+1 blocks), preconditioned
+    // directions Z (restart blocks), w, small coefficient arrays
+    int gm_m = 0, gm_nrhs = 0;
+    double *d_gV = nullptr, *d_gZ = nullptr, *d_gw = nullptr, *d_gcoef = nullptr;
+    std::vector<double> last_xinf, last_binf;   // per-column norms of the last residual
+
     // solve workspace
     int ws_nrhs = 0;
     double *d_B = nullptr, *d_X = nullptr, *d_R = nullptr, *d_D = nullptr;
@@ -579,11 +585,15 @@ spx_status residual(spx_handle h, int nrhs, double *berr)
                        cudaMemcpyDeviceToHost, h->hs));
     CU(cudaStreamSynchronize(h->hs));
     double worst = 0.0;
+    h->last_xinf.assign(nrhs, 0.0);
+    h->last_binf.assign(nrhs, 0.0);
     for (int c = 0; c < nrhs; ++c) {
         double r, x, b;
         std::memcpy(&r, &nb[3 * c], 8);
         std::memcpy(&x, &nb[3 * c + 1], 8);
         std::memcpy(&b, &nb[3 * c + 2], 8);
+        h->last_xinf[c] = x;
+        h->last_binf[c] = b;
         double den = h->anorm * x + b;
         double e = den > 0.0 ? r / den : (r > 0.0 ? INFINITY : 0.0);
         if (!(e <= worst)) worst = e;   // NaN propagates
@@ -651,6 +661,124 @@ void enqueue_sweep_noalloc(spx_handle h, int nrhs, const double *B, int64_t ldb,
         spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Z, Tacc, Xs, nrhs, s);
     }
     spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, X, ldx, s);
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES refinement (right preconditioned by the low-precision factor, FP64
+// Arnoldi with two-pass classical Gram-Schmidt, one Krylov space per right-
+// hand side, Givens rotations on the host).  Starts from d_X; returns the
+// backward error of the final iterate and the iterations taken.
+// ---------------------------------------------------------------------------
+spx_status fgmres(spx_handle h, int nrhs, const spx_refine &rf, double *berr_out, int *iters_out)
+{
+    const spx::Plan &P = h->plan;
+    const int64_t n = P.n;
+    const size_t blk = (size_t)n * nrhs;
+    const int m = std::max(1, std::min(rf.gmres_restart, 200));
+    const int maxit = std::max(1, rf.gmres_max_iter);
+    cudaStream_t s = h->hs;
+    spx_status st;
+    if (h->gm_m < m || h->gm_nrhs < nrhs) {
+        for (double **p : {&h->d_gV, &h->d_gZ, &h->d_gw, &h->d_gcoef}) {
+            dfree(h, *p);
+            *p = nullptr;
+        }
+        h->gm_m = h->gm_nrhs = 0;
+        if ((st = dalloc(h, &h->d_gV, blk * (m + 1))) || (st = dalloc(h, &h->d_gZ, blk * m)) ||
+            (st = dalloc(h, &h->d_gw, blk)) || (st = dalloc(h, &h->d_gcoef, (size_t)(m + 2) * nrhs)))
+            return st;
+        h->gm_m = m;
+        h->gm_nrhs = nrhs;
+    }
+    std::vector<double> H((size_t)nrhs * (m + 1) * m), cs((size_t)nrhs * m), sn((size_t)nrhs * m);
+    std::vector<double> g((size_t)nrhs * (m + 1)), coef((size_t)(m + 1) * nrhs), sc(nrhs);
+    std::vector<double> y((size_t)m * nrhs);
+    auto Hat = [&](int c, int i, int j) -> double & { return H[((size_t)c * (m + 1) + i) * m + j]; };
+    int total = 0;
+    double berr = INFINITY;
+    while (true) {
+        if ((st = residual(h, nrhs, &berr))) return st;
+        if (berr <= rf.tol || total >= maxit) break;
+        // beta = ||r||_2 per column; V_0 = r / beta
+        spx::launch_dots(n, nrhs, 1, h->d_R, h->d_R, h->d_gcoef, s);
+        CU(cudaMemcpyAsync(coef.data(), h->d_gcoef, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(g.begin(), g.end(), 0.0);
+        for (int c = 0; c < nrhs; ++c) {
+            const double beta = std::sqrt(std::max(coef[c], 0.0));
+            g[(size_t)c * (m + 1)] = beta;
+            sc[c] = beta > 0.0 ? 1.0 / beta : 0.0;
+        }
+        CU(cudaMemcpyAsync(h->d_gcoef, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+        spx::launch_scale_cols(n, nrhs, h->d_R, h->d_gcoef, h->d_gV, s);
+        int j = 0;
+        while (j < m && total < maxit) {
+            double *Vj = h->d_gV + blk * j, *Zj = h->d_gZ + blk * j;
+            // z_j = M^{-1} v_j through the factor; w = A z_j
+            CU(cudaMemcpyAsync(h->d_R, Vj, sizeof(double) * blk, cudaMemcpyDeviceToDevice, s));
+            CU(cudaGraphLaunch(h->sgraph, s));
+            CU(cudaMemcpyAsync(Zj, h->d_D, sizeof(double) * blk, cudaMemcpyDeviceToDevice, s));
+            spx::launch_spmv_cols(n, nrhs, h->d_csr_ptr, h->d_csr_col, h->d_csr_src, h->d_vals, Zj,
+                                  h->d_gw, s);
+            h->cnt += h->sweep_launches + 1;
+            for (int pass = 0; pass < 2; ++pass) {
+                spx::launch_dots(n, nrhs, j + 1, h->d_gV, h->d_gw, h->d_gcoef, s);
+                spx::launch_combine(n, nrhs, j + 1, h->d_gV, h->d_gcoef, -1.0, h->d_gw, s);
+                CU(cudaMemcpyAsync(coef.data(), h->d_gcoef, sizeof(double) * (j + 1) * nrhs,
+                                   cudaMemcpyDeviceToHost, s));
+                CU(cudaStreamSynchronize(s));
+                for (int c = 0; c < nrhs; ++c)
+                    for (int i = 0; i <= j; ++i) Hat(c, i, j) += coef[(size_t)i * nrhs + c];
+            }
+            spx::launch_dots(n, nrhs, 1, h->d_gw, h->d_gw, h->d_gcoef, s);
+            CU(cudaMemcpyAsync(coef.data(), h->d_gcoef, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            double worst = 0.0;
+            for (int c = 0; c < nrhs; ++c) {
+                const double hn = std::sqrt(std::max(coef[c], 0.0));
+                Hat(c, j + 1, j) = hn;
+                sc[c] = hn > 0.0 ? 1.0 / hn : 0.0;
+                // previous rotations, then a new one that zeroes H(j+1, j)
+                for (int i = 0; i < j; ++i) {
+                    const double a0 = Hat(c, i, j), a1 = Hat(c, i + 1, j);
+                    Hat(c, i, j) = cs[(size_t)c * m + i] * a0 + sn[(size_t)c * m + i] * a1;
+                    Hat(c, i + 1, j) = -sn[(size_t)c * m + i] * a0 + cs[(size_t)c * m + i] * a1;
+                }
+                const double a0 = Hat(c, j, j), a1 = Hat(c, j + 1, j);
+                const double rr = std::hypot(a0, a1);
+                const double cc = rr > 0.0 ? a0 / rr : 1.0, ss = rr > 0.0 ? a1 / rr : 0.0;
+                cs[(size_t)c * m + j] = cc;
+                sn[(size_t)c * m + j] = ss;
+                Hat(c, j, j) = rr;
+                Hat(c, j + 1, j) = 0.0;
+                const double gj = g[(size_t)c * (m + 1) + j];
+                g[(size_t)c * (m + 1) + j] = cc * gj;
+                g[(size_t)c * (m + 1) + j + 1] = -ss * gj;
+                const double den = h->anorm * h->last_xinf[c] + h->last_binf[c];
+                const double est = den > 0.0 ? std::fabs(g[(size_t)c * (m + 1) + j + 1]) / den : 0.0;
+                worst = std::max(worst, est);
+            }
+            CU(cudaMemcpyAsync(h->d_gcoef, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+            spx::launch_scale_cols(n, nrhs, h->d_gw, h->d_gcoef, h->d_gV + blk * (j + 1), s);
+            ++j;
+            ++total;
+            if (worst <= 0.1 * rf.tol) break;
+        }
+        // y = H^{-1} g (upper triangular j x j per column), x += Z y
+        for (int c = 0; c < nrhs; ++c)
+            for (int i = j - 1; i >= 0; --i) {
+                double v = g[(size_t)c * (m + 1) + i];
+                for (int k = i + 1; k < j; ++k) v -= Hat(c, i, k) * y[(size_t)k * nrhs + c];
+                const double d = Hat(c, i, i);
+                y[(size_t)i * nrhs + c] = d != 0.0 ? v / d : 0.0;
+            }
+        CU(cudaMemcpyAsync(h->d_gcoef, y.data(), sizeof(double) * j * nrhs, cudaMemcpyHostToDevice, s));
+        spx::launch_combine(n, nrhs, j, h->d_gZ, h->d_gcoef, 1.0, h->d_X, s);
+    }
+    *berr_out = berr;
+    *iters_out = total;
+    return SPX_OK;
 }
 
 }  // namespace
@@ -920,6 +1048,11 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
             const bool stalled = !(e <= 0.5 * berr);   // plain refinement stopped contracting
             berr = e;
             if (stalled) break;
+        }
+        if (rf.mode == 2 && !(berr <= rf.tol)) {
+            int git = 0;
+            if ((st = fgmres(h, nrhs, rf, &berr, &git))) return st;
+            si.gmres_iters = git;
         }
         si.backward_error = berr;
         si.converged = (rf.mode == 0) ? 1 : (berr <= rf.tol);

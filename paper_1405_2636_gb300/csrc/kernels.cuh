@@ -116,6 +116,18 @@ template <typename T>
 void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const T *Dinv,
                      int lu, const T *Z, const T *Tacc, T *X, int nrhs, cudaStream_t s);
 
+// ---- FGMRES vector kernels (FP64, n x nrhs column blocks, ld n) ----------
+void launch_spmv_cols(int64_t n, int nrhs, const int64_t *rp, const int32_t *ci, const int64_t *src,
+                      const double *vals, const double *X, double *Y, cudaStream_t s);
+// out[v * nrhs + c] = <V_v(:, c), w(:, c)> for v < nv (out zeroed inside)
+void launch_dots(int64_t n, int nrhs, int nv, const double *V, const double *w, double *out,
+                 cudaStream_t s);
+// w(:, c) += sign * sum_v coef[v * nrhs + c] V_v(:, c)
+void launch_combine(int64_t n, int nrhs, int nv, const double *V, const double *coef, double sign,
+                    double *w, cudaStream_t s);
+// v(:, c) = w(:, c) * sc[c]
+void launch_scale_cols(int64_t n, int nrhs, const double *w, const double *sc, double *v, cudaStream_t s);
+
 // ---- residuals and norms ---------------------------------------------------
 // R = B - A X for nrhs columns (A by rows, original numbering); per column
 // stores max|r|, max|x|, max|b| into norms[3*c + {0,1,2}] (bit patterns of

@@ -422,6 +422,102 @@ void launch_axpy_cols(int64_t n, int nrhs, const double *D, double *X, int64_t l
     axpy_cols_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, D, X, ldx);
 }
 
+// ---------------------------------------------------------------------------
+// Vector kernels of the FGMRES refinement (n x nrhs column blocks, FP64).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) spmv_cols_kernel(int64_t n, int nrhs, const int64_t *__restrict__ rp,
+                                                        const int32_t *__restrict__ ci,
+                                                        const int64_t *__restrict__ src,
+                                                        const double *__restrict__ vals,
+                                                        const double *__restrict__ X,
+                                                        double *__restrict__ Y)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < nrhs; ++c) {
+        double s = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) s += vals[src[e]] * X[ci[e] + c * n];
+        Y[i + c * n] = s;
+    }
+}
+
+// out[v * nrhs + c] += sum_r V_v[r, c] * w[r, c] for v < nv (V_v = V + v * n * nrhs)
+__global__ void __launch_bounds__(256) dots_kernel(int64_t n, int nrhs, int nv, const double *__restrict__ V,
+                                                   const double *__restrict__ w, double *out)
+{
+    const int c = blockIdx.y;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int v = 0; v < nv; ++v) {
+        const double *Vv = V + (int64_t)v * n * nrhs + c * n;
+        const double *wc = w + c * n;
+        double s = 0.0;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) s += Vv[r] * wc[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        __shared__ double part[8];
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += part[q];
+            atomicAdd(out + v * nrhs + c, t);
+        }
+        __syncthreads();
+    }
+}
+
+// w[r, c] += sign * sum_v coef[v * nrhs + c] * V_v[r, c]
+__global__ void __launch_bounds__(256) combine_kernel(int64_t n, int nrhs, int nv, const double *__restrict__ V,
+                                                      const double *__restrict__ coef, double sign,
+                                                      double *__restrict__ w)
+{
+    const int64_t total = n * nrhs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        double s = 0.0;
+        for (int v = 0; v < nv; ++v) s += coef[v * nrhs + c] * V[(int64_t)v * total + e];
+        w[e] += sign * s;
+    }
+}
+
+// v[r, c] = w[r, c] * s[c]
+__global__ void scale_cols_kernel(int64_t n, int nrhs, const double *__restrict__ w,
+                                  const double *__restrict__ sc, double *__restrict__ v)
+{
+    const int64_t total = n * nrhs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x)
+        v[e] = w[e] * sc[e / n];
+}
+
+void launch_spmv_cols(int64_t n, int nrhs, const int64_t *rp, const int32_t *ci, const int64_t *src,
+                      const double *vals, const double *X, double *Y, cudaStream_t s)
+{
+    spmv_cols_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nrhs, rp, ci, src, vals, X, Y);
+}
+
+void launch_dots(int64_t n, int nrhs, int nv, const double *V, const double *w, double *out,
+                 cudaStream_t s)
+{
+    int64_t bx = (n + 255) / 256;
+    if (bx > 64) bx = 64;
+    dim3 grid((unsigned)bx, (unsigned)nrhs);
+    cudaMemsetAsync(out, 0, sizeof(double) * nv * nrhs, s);
+    dots_kernel<<<grid, 256, 0, s>>>(n, nrhs, nv, V, w, out);
+}
+
+void launch_combine(int64_t n, int nrhs, int nv, const double *V, const double *coef, double sign,
+                    double *w, cudaStream_t s)
+{
+    combine_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, nv, V, coef, sign, w);
+}
+
+void launch_scale_cols(int64_t n, int nrhs, const double *w, const double *sc, double *v, cudaStream_t s)
+{
+    scale_cols_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(n, nrhs, w, sc, v);
+}
+
 template void launch_permute_in<double>(int64_t, int, const double *, int64_t, const int64_t *, double *, cudaStream_t);
 template void launch_permute_out<double>(int64_t, int, const double *, const int64_t *, double *, int64_t, cudaStream_t);
 template void launch_fwd_diag<double>(const DevPlan &, const int32_t *, int, int, const double *, int, const double *, double *, int, cudaStream_t);

@@ -61,14 +61,15 @@ def laplacian_3d(nx: int, ny: int, nz: int, shift: float = 0.0, two_d: bool = Fa
     return _finish(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
 
 
-def diffusion_3d(nx: int, ny: int, nz: int, seed: int) -> sp.csc_matrix:
-    """7-point variable-coefficient diffusion, node coefficients exp(g), g ~ N(0,1).
+def diffusion_3d(nx: int, ny: int, nz: int, seed: int, sigma: float = 1.0) -> sp.csc_matrix:
+    """7-point variable-coefficient diffusion, node coefficients exp(sigma g), g ~ N(0,1).
 
     Face coefficient between neighbours i, j is (k_i + k_j) / 2; a missing
     neighbour (Dirichlet boundary) adds k_i to the diagonal; grid spacing 1.
+    sigma > 1 gives the high-contrast variants used to exercise refinement.
     """
     n = nx * ny * nz
-    kappa = np.exp(rng(seed, STREAM_MATRIX).standard_normal(n))
+    kappa = np.exp(sigma * rng(seed, STREAM_MATRIX).standard_normal(n))
     idx = _node_index(nx, ny, nz)
     diag = np.zeros(n)
     rows, cols, vals = [], [], []

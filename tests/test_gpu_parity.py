@@ -213,3 +213,31 @@ def test_update_kernel_on_the_papers_synthetic_panels(torch):
         torch.cuda.synchronize()
         got = tC.cpu().numpy()
         assert np.max(np.abs(got - expect)) <= 1e-12 * max(1.0, np.max(np.abs(expect)))
+
+
+def test_fgmres_takes_over_when_plain_refinement_stalls(torch):
+    """High coefficient contrast (exp(3g)) with BF16 updates: plain refinement
+    stops contracting; FGMRES preconditioned by the same factor reaches 1e-12."""
+    g = 24
+    A = inputs.diffusion_3d(g, g, g, 7, sigma=3.0)
+    cp, ri, vals = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "llt", ordering=1, grid=(g, g, g), max_width=64)
+    h.factorize(vals, "bf16")
+    B = inputs.rhs(A.shape[0], 4, 7)
+    _, plain = h.solve(B, refine=spx.default_refine(tol=1e-12, mode=1, max_iter=10))
+    assert not plain["converged"]
+    X, auto = h.solve(B, refine=spx.default_refine(tol=1e-12, mode=2, max_iter=10))
+    assert auto["converged"] and auto["gmres_iters"] > 0
+    assert oracle.backward_error(A, X, B) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_fgmres_alone_reaches_target(torch, prec):
+    A = inputs.diffusion_3d(15, 14, 13, 4)
+    cp, ri, vals = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "llt", ordering=1, grid=(15, 14, 13), max_width=32)
+    h.factorize(vals, prec)
+    B = inputs.rhs(A.shape[0], 3, 4)
+    X, info = h.solve(B, refine=spx.default_refine(tol=1e-12, mode=2, max_iter=0, gmres_restart=5))
+    assert info["converged"] and info["iters"] == 0 and info["gmres_iters"] > 0
+    assert oracle.backward_error(A, X, B) <= 1e-12
