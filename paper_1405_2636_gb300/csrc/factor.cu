@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     constexpr int NT = 256, NW = NT / 32;
     extern __shared__ double sm[];
     double *a = sm;                          // W x LD, FP64 working block
-    double *lA = a + W * LD;                 // W x kDB unscaled block columns (ld W)
-    double *dv = lA + W * kDB;               // pivots
+    double *lA = a + W * LD;                 // 2 x (W x kDB) unscaled block columns (ld W)
+    double *dv = lA + 2 * W * kDB;           // pivots
     double *rsv = dv + W;                    // 1 / sqrt(pivot)
     T *x = reinterpret_cast<T *>(rsv + W);   // W x LD inverse workspace
     T *tmp = x + W * LD;                     // (W/2)^2
@@ -483,75 +483,93 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     }
     __syncthreads();
 
+    // Block panel b by warp 0 (registers, two row sets of 32), writing the
+    // multipliers into a and the unscaled block columns into lA (two buffers,
+    // one per block parity, so that the next panel can overlap the trailing
+    // update of the previous one).
+    auto panel = [&](int kb) {
+        double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
+        const int r0 = kb + lane, r1 = kb + lane + 32;
+        const bool two = kb + 32 < W;   // warp-uniform: second row set present
+        double p0[kDB], p1[kDB];
+#pragma unroll
+        for (int c = 0; c < kDB; ++c) {
+            p0[c] = r0 < W ? a[r0 + (kb + c) * LD] : 0.0;
+            p1[c] = (two && r1 < W) ? a[r1 + (kb + c) * LD] : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < kDB; ++c) {
+            const int k = kb + c;
+            double d = shfl_d(p0[c], c);                 // A(k, k) from lane c
+            if (!(d > 0.0)) {
+                if (lane == 0 && k < w) {
+                    if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                    else atomicMin((long long *)err_col, (long long)(col0 + k));
+                }
+                d = replace_tau > 0.0 ? replace_tau : 1.0;
+            }
+            const double r = rcp_newton(d);
+            const double u0 = r0 > k ? p0[c] : 0.0;
+            const double l0 = u0 * r;
+#pragma unroll
+            for (int c2 = c + 1; c2 < kDB; ++c2) {
+                const double ac = shfl_d(u0, c2);                   // A(kb + c2, k)
+                if (r0 >= kb + c2) p0[c2] = fma(-l0, ac, p0[c2]);
+                if (two) p1[c2] = fma(-(p1[c] * r), ac, p1[c2]);
+            }
+            if (r0 < W) lAb[r0 + c * W] = u0;
+            if (two && r1 < W) lAb[r1 + c * W] = p1[c];
+            p0[c] = r0 > k ? l0 : (r0 == k ? 1.0 : 0.0);
+            if (two) p1[c] = p1[c] * r;
+            if (lane == c) dv[k] = d;
+        }
+#pragma unroll
+        for (int c = 0; c < kDB; ++c) {
+            if (r0 < W) a[r0 + (kb + c) * LD] = p0[c];
+            if (two && r1 < W) a[r1 + (kb + c) * LD] = p1[c];
+        }
+    };
+    // Rank-kDB update by block kb of the lower part of columns [j0, j1),
+    // rows >= j; the (i, j) pairs are spread densely over the threads
+    // t0.. (stride ts) so that FP64 lanes are not wasted on the upper part.
+    auto update = [&](int kb, int j0, int j1, int t0, int ts) {
+        const double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
+        // pairs ordered column by column: column j holds W - j rows
+        int j = j0, rem = t0;      // pair e = t0, t0 + ts, ... decoded incrementally
+        while (j < j1 && rem >= W - j) {
+            rem -= W - j;
+            ++j;
+        }
+        for (; j < j1;) {
+            const int i = j + rem;
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+            for (int c = 0; c < kDB; c += 2) {
+                s0 = fma(a[i + (kb + c) * LD], lAb[j + c * W], s0);
+                s1 = fma(a[i + (kb + c + 1) * LD], lAb[j + (c + 1) * W], s1);
+            }
+            a[i + j * LD] -= s0 + s1;
+            rem += ts;
+            while (j < j1 && rem >= W - j) {
+                rem -= W - j;
+                ++j;
+            }
+        }
+    };
+
+    if (warp == 0) panel(0);
+    __syncthreads();
     for (int kb = 0; kb < W; kb += kDB) {
-        if (warp == 0) {
-            const int r0 = kb + lane, r1 = kb + lane + 32;
-            double p0[kDB], p1[kDB];
-#pragma unroll
-            for (int c = 0; c < kDB; ++c) {
-                p0[c] = r0 < W ? a[r0 + (kb + c) * LD] : 0.0;
-                p1[c] = r1 < W ? a[r1 + (kb + c) * LD] : 0.0;
-            }
-#pragma unroll
-            for (int c = 0; c < kDB; ++c) {
-                const int k = kb + c;
-                double d = shfl_d(p0[c], c);                 // A(k, k) from lane c
-                if (!(d > 0.0)) {
-                    if (lane == 0 && k < w) {
-                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
-                        else atomicMin((long long *)err_col, (long long)(col0 + k));
-                    }
-                    d = replace_tau > 0.0 ? replace_tau : 1.0;
-                }
-                const double r = rcp_newton(d);
-                const double u0 = r0 > k ? p0[c] : 0.0, u1 = p1[c];   // A-form of column k
-                const double l0 = u0 * r, l1 = u1 * r;                  // multipliers
-#pragma unroll
-                for (int c2 = c + 1; c2 < kDB; ++c2) {
-                    const double ac = shfl_d(u0, c2);                   // A(kb + c2, k)
-                    if (r0 >= kb + c2) p0[c2] = fma(-l0, ac, p0[c2]);
-                    p1[c2] = fma(-l1, ac, p1[c2]);
-                }
-                if (r0 < W) lA[r0 + c * W] = u0;
-                if (r1 < W) lA[r1 + c * W] = u1;
-                p0[c] = r0 > k ? l0 : (r0 == k ? 1.0 : 0.0);
-                p1[c] = l1;
-                if (lane == c) dv[k] = d;
-            }
-#pragma unroll
-            for (int c = 0; c < kDB; ++c) {
-                if (r0 < W) a[r0 + (kb + c) * LD] = p0[c];
-                if (r1 < W) a[r1 + (kb + c) * LD] = p1[c];
-            }
+        const int nb = kb + kDB;                 // next block
+        if (nb < W) {
+            // columns of the next block first, by every thread
+            update(kb, nb, nb + kDB, tid, NT);
+            __syncthreads();
+            // warp 0 factors the next block while the others finish this block's update
+            if (warp == 0) panel(nb);
+            else update(kb, nb + kDB, W, tid - 32, NT - 32);
+            __syncthreads();
         }
-        __syncthreads();
-        const int j0 = kb + kDB;
-        if (j0 < W) {
-            const int i0 = j0 + lane, i1 = j0 + lane + 32;
-            const bool g0 = i0 < W, g1 = i1 < W;
-            double li0[kDB], li1[kDB];
-#pragma unroll
-            for (int c = 0; c < kDB; ++c) {
-                li0[c] = g0 ? a[i0 + (kb + c) * LD] : 0.0;
-                li1[c] = g1 ? a[i1 + (kb + c) * LD] : 0.0;
-            }
-            for (int j = j0 + warp; j < W; j += NW) {
-                double aj[kDB];
-#pragma unroll
-                for (int c = 0; c < kDB; ++c) aj[c] = lA[j + c * W];
-                double x0 = 0.0, y0 = 0.0, x1 = 0.0, y1 = 0.0;
-#pragma unroll
-                for (int c = 0; c < kDB; c += 2) {
-                    x0 = fma(li0[c], aj[c], x0);
-                    y0 = fma(li0[c + 1], aj[c + 1], y0);
-                    x1 = fma(li1[c], aj[c], x1);
-                    y1 = fma(li1[c + 1], aj[c + 1], y1);
-                }
-                if (g0 && i0 >= j) a[i0 + j * LD] -= x0 + y0;
-                if (g1 && i1 >= j) a[i1 + j * LD] -= x1 + y1;
-            }
-        }
-        __syncthreads();
     }
 
     // L = l diag(sqrt(d)); keep 1/sqrt(d) for the inverse
@@ -564,9 +582,9 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     __syncthreads();
     for (int idx = tid; idx < W * W; idx += NT) {
         const int i = idx % W, j = idx / W;
-        const double l = a[i + j * LD];
-        if (i < w && j < w && i >= j) D[i + (int64_t)j * h] = (T)(i == j ? dv[j] : l * dv[j]);
-        x[i + j * LD] = (T)(i > j ? l : (i == j ? 1.0 : 0.0));
+        const T l = (T)a[i + j * LD];
+        if (i < w && j < w && i >= j) D[i + (int64_t)j * h] = i == j ? (T)dv[j] : l * (T)dv[j];
+        x[i + j * LD] = i > j ? l : (i == j ? (T)1 : (T)0);
     }
     __syncthreads();
 
@@ -612,14 +630,14 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     T *Mi = Dinv + p.pinv[pid];
     for (int idx = tid; idx < w * w; idx += NT) {
         const int i = idx % w, j = idx / w;
-        Mi[idx] = i >= j ? (T)((double)x[i + j * LD] * rsv[i]) : (T)0;
+        Mi[idx] = i >= j ? x[i + j * LD] * (T)rsv[i] : (T)0;
     }
 }
 
 template <typename T, int W>
 constexpr size_t ldl_smem_bytes()
 {
-    return sizeof(double) * ((size_t)W * (W + 1) + (size_t)W * kDB + 2 * W) +
+    return sizeof(double) * ((size_t)W * (W + 1) + (size_t)2 * W * kDB + 2 * W) +
            sizeof(T) * ((size_t)W * (W + 1) + (size_t)(W / 2) * (W / 2));
 }
 
