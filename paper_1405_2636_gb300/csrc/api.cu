@@ -962,7 +962,8 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         K.flops[SPX_K_TRSM] = P.trsm_flops;
         K.flops[SPX_K_UPDATE] = P.update_flops - (tcm ? h->upd_flops_tc : 0.0);
         K.flops[SPX_K_UPDATE_TC] = tcm ? h->upd_flops_tc : 0.0;
-        K.bytes[SPX_K_ASSEMBLE] = (double)P.nnz_a * 16.0 + (double)elems * e * nfac * 2.0;
+        // zero fill of the factor (one write) + the scatter (value and map read, one write)
+        K.bytes[SPX_K_ASSEMBLE] = (double)P.nnz_a * (16.0 + e * nfac) + (double)elems * e * nfac;
         K.bytes[SPX_K_DIAG] = P.diag_elems * e;
         K.bytes[SPX_K_TRSM] = P.trsm_elems * e;
         K.bytes[SPX_K_UPDATE] = (P.update_elems - (tcm ? h->upd_op_elems_tc + h->upd_elems_tc : 0.0)) * e;
