@@ -241,6 +241,107 @@ spx_status spx_update(int64_t m, int64_t nb_rows, int64_t k, const double *A, in
                       double *C, int64_t ldc, const int32_t *rowmap, const int32_t *colmap,
                       int lower, void *cuda_stream);
 
+/* ---- Batched static-pivot LU of many small independent systems ----------
+ *
+ * The factorization of Sec. III (static pivoting, panels, updates with the
+ * scatter fused as in Sec. V-B) applied to a batch of unrelated systems, for
+ * workloads of thousands of small systems where one system cannot fill the
+ * GPU.  Each system has its own CSC pattern, values and one right-hand side;
+ * systems with identical patterns (and grid) share one analysis.  One
+ * persistent kernel, captured in a CUDA graph, factorizes every system and
+ * solves it with FP64 iterative refinement: each CTA takes whole systems
+ * from a device queue, largest first, so no CTA waits on another.
+ *
+ * Batched arrays are concatenations over the systems in order:
+ *   colptr : n_s + 1 entries per system, each starting at 0 (int64);
+ *   rowind, values : colptr_s[n_s] entries per system;
+ *   B, X   : n_s entries per system (one right-hand side each). */
+typedef struct spx_batch_s *spx_batch;
+
+typedef struct {
+    int32_t nsys;           /* systems */
+    int32_t nclasses;       /* distinct patterns analysed */
+    int64_t n_total;        /* sum of n */
+    int64_t n_max;          /* largest n */
+    int64_t nnz_total;      /* sum of nnz(A) */
+    int64_t nnz_l_total;    /* sum of exact nnz(L) (diagonal included) */
+    int64_t factor_elems;   /* stored elements of L plus U^T over all systems */
+    double flops;           /* exact-pattern LU flops over all systems: sum 2(c_j-1)^2+(c_j-1) */
+    int32_t precision;      /* spx_precision of the last run */
+    int32_t ctas_per_sm;    /* launch configuration in use ... */
+    int32_t leaf_width;     /* panels at most this wide go one per warp (0: none) */
+    int32_t rows_per_thread;/* rows of the update tile per thread (1, 2 or 4) */
+    double tuned_ms;        /* run time of the configuration spx_batch_tune chose (0: not tuned) */
+    double analyze_ms;      /* host time of spx_batch_analyze */
+    double run_ms;          /* device time of the last spx_batch_run (the persistent launch) */
+    int64_t max_pivot_repl; /* largest number of static pivot replacements in one system */
+    int32_t not_converged;  /* systems of the last run that missed the target */
+    int32_t max_iters;      /* most refinement steps one system took */
+    double max_backward_error;  /* largest final backward error over the systems */
+} spx_batch_info;
+
+/* Host-only analysis of a batch.  n: host int64[nsys]; colptr, rowind: host
+ * concatenations as above (copied).  grid: NULL, or host int32[3 * nsys]
+ * (nx, ny, nz per system) for the grid ordering rule.  opt: NULL or options
+ * (ordering, dof, amalg_ratio, pivot_tau, max_width <= 64; perm and
+ * lower_only are not allowed).  Every system is analysed for LU on the
+ * pattern of A + A^T. */
+spx_status spx_batch_analyze(int32_t nsys, const int64_t *n, const int64_t *colptr,
+                             const int32_t *rowind, const int32_t *grid, const spx_options *opt,
+                             spx_batch *out);
+
+/* Factorize every system and solve it, in one persistent launch.
+ *   values : concatenated CSC values; B, X: concatenated right-hand sides and
+ *            solutions; host memory (on_device = 0: copied in and out inside
+ *            the call) or device memory (on_device = 1).  B == NULL:
+ *            factorize only (X untouched).
+ *   precision : SPX_FP64 or SPX_FP32, the arithmetic of the stored factor,
+ *            the panel updates and the sweeps; residuals b - A x and the
+ *            corrections x += d are FP64.
+ *   refine : NULL or mode 0: one solve; else up to max_iter corrections per
+ *            system, stopping at backward error <= tol.
+ * Returns SPX_ERR_ZERO_PIVOT if a system met a zero pivot with pivot_tau = 0,
+ * SPX_ERR_NOT_CONVERGED if refinement was asked and a system missed tol;
+ * spx_batch_system_info tells which. */
+spx_status spx_batch_run(spx_batch b, const double *values, const double *B, double *X,
+                         int on_device, spx_precision precision, const spx_refine *refine,
+                         void *cuda_stream);
+
+/* Autotuner: runs spx_batch_run on these arguments for candidate launch
+ * configurations -- panels per warp up to width 0/4/8/16 (the leaf-versus-
+ * top schedule), 1/2/4 update rows per thread (the update tile), CTAs per SM
+ * -- times each with CUDA events and keeps the fastest for later runs.  X
+ * holds a valid result afterwards. */
+spx_status spx_batch_tune(spx_batch b, const double *values, const double *B, double *X,
+                          int on_device, spx_precision precision, const spx_refine *refine,
+                          void *cuda_stream);
+
+/* Set the launch configuration by hand (0 keeps the current value of
+ * ctas_per_sm / rows_per_thread; leaf_width 0 disables the per-warp mode). */
+spx_status spx_batch_set_config(spx_batch b, int32_t ctas_per_sm, int32_t leaf_width,
+                                int32_t rows_per_thread);
+
+spx_status spx_batch_get_info(spx_batch b, spx_batch_info *info);
+
+/* Per-system results of the last run, host arrays of nsys entries (any may
+ * be NULL): refinement steps, final backward error, 1 if it met tol, static
+ * pivot replacements, permuted column of the first zero pivot (-1: none). */
+spx_status spx_batch_system_info(spx_batch b, int32_t *iters, double *berr, int32_t *converged,
+                                 int32_t *npivot_repl, int64_t *bad_col);
+
+/* Ordering (new -> old) of system s, host int64[n_s]. */
+spx_status spx_batch_get_perm(spx_batch b, int32_t s, int64_t *perm);
+
+/* Factor of system s on a caller-given lower pattern (Lp, Li; CSC of the
+ * permuted matrix, as spx_get_factor): Lx (unit diagonal) and Ut = U^T. */
+spx_status spx_batch_get_factor(spx_batch b, int32_t s, const int64_t *Lp, const int32_t *Li,
+                                double *Lx, double *Ut);
+
+const char *spx_batch_last_error(spx_batch b);
+
+/* Release a batch handle.  NULL-safe. */
+void spx_batch_free(spx_batch b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -241,6 +241,27 @@ DIFFUSION3D_64 = Workload("diffusion3d_64^3", (64, 64, 64), 1, 16, 2)
 ELASTICITY27_40 = Workload("elasticity27_40^3x3", (40, 40, 40), 3, 1, 3)
 
 
+def batched_convection_diffusion(count: int, seed: int, k_lo: int = 12, k_hi: int = 80):
+    """The batched workload: ``count`` independent 2-D convection-diffusion
+    systems, side k ~ U{k_lo..k_hi} per system (n = k^2), each with its own
+    wind angle and mesh Peclet number and one right-hand side ~ U(-1, 1).
+
+    System s draws from seed ``seed * 1_000_003 + s``.  Returns (list of
+    csc matrices, list of sides, concatenated right-hand sides).
+    """
+    sides = rng(seed, STREAM_EXTRA).integers(k_lo, k_hi + 1, size=count)
+    mats, rhss = [], []
+    for s, k in enumerate(sides):
+        sseed = seed * 1_000_003 + s
+        A, _ = convection_diffusion_2d(int(k), sseed)
+        mats.append(A)
+        rhss.append(rhs(A.shape[0], 1, sseed).ravel())
+    return mats, [int(k) for k in sides], (np.concatenate(rhss) if rhss else np.zeros(0))
+
+
+BATCHED_CD_4096 = {"name": "batched_convdiff2d_4096x_k12-80", "count": 4096, "seed": 4}
+
+
 def gapped_update_case(m: int, k: int, nb: int, seed: int, avg_block: int = 200):
     """The kernel-study input of Sec. V-B: C = C - A B^T with B the first nb rows
     of A; C is a panel twice as tall as A whose rows are cut into random blocks

@@ -32,7 +32,10 @@ STATUS_NAMES = {0: "SPX_OK", 1: "SPX_ERR_ARG", 2: "SPX_ERR_ALLOC", 3: "SPX_ERR_C
 EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_factorize",
             "spx_solve", "spx_get_info", "spx_get_perm", "spx_get_factor", "spx_last_error",
             "spx_free", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
-            "spx_get_panels", "spx_solve_noalloc"]
+            "spx_get_panels", "spx_solve_noalloc",
+            "spx_batch_analyze", "spx_batch_run", "spx_batch_tune", "spx_batch_set_config",
+            "spx_batch_get_info", "spx_batch_system_info", "spx_batch_get_perm",
+            "spx_batch_get_factor", "spx_batch_last_error", "spx_batch_free"]
 
 
 class spx_options(ctypes.Structure):
@@ -80,6 +83,21 @@ class spx_kernel_stats(ctypes.Structure):
                     "bytes": self.bytes[i]} for i, c in enumerate(KERNEL_CLASSES)}
 
 
+class spx_batch_info(ctypes.Structure):
+    _fields_ = [("nsys", ctypes.c_int32), ("nclasses", ctypes.c_int32)] + [
+        (name, ctypes.c_int64) for name in ("n_total", "n_max", "nnz_total", "nnz_l_total",
+                                            "factor_elems")] + [
+        ("flops", ctypes.c_double)] + [
+        (name, ctypes.c_int32) for name in ("precision", "ctas_per_sm", "leaf_width",
+                                            "rows_per_thread")] + [
+        (name, ctypes.c_double) for name in ("tuned_ms", "analyze_ms", "run_ms")] + [
+        ("max_pivot_repl", ctypes.c_int64), ("not_converged", ctypes.c_int32),
+        ("max_iters", ctypes.c_int32), ("max_backward_error", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -114,9 +132,25 @@ def load():
     lib.spx_free.argtypes = [_vp]
     lib.spx_free.restype = None
     lib.spx_update.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]
+    lib.spx_batch_analyze.argtypes = [ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.POINTER(spx_options),
+                                      ctypes.POINTER(_vp)]
+    lib.spx_batch_run.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(spx_refine), _vp]
+    lib.spx_batch_tune.argtypes = lib.spx_batch_run.argtypes
+    lib.spx_batch_set_config.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.spx_batch_get_info.argtypes = [_vp, ctypes.POINTER(spx_batch_info)]
+    lib.spx_batch_system_info.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    lib.spx_batch_get_perm.argtypes = [_vp, ctypes.c_int32, _vp]
+    lib.spx_batch_get_factor.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    lib.spx_batch_last_error.argtypes = [_vp]
+    lib.spx_batch_last_error.restype = ctypes.c_char_p
+    lib.spx_batch_free.argtypes = [_vp]
+    lib.spx_batch_free.restype = None
     for name in ("spx_analyze", "spx_factorize", "spx_solve", "spx_get_info", "spx_get_perm",
                  "spx_get_factor", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
-                 "spx_get_panels", "spx_solve_noalloc"):
+                 "spx_get_panels", "spx_solve_noalloc", "spx_batch_analyze", "spx_batch_run",
+                 "spx_batch_tune", "spx_batch_set_config", "spx_batch_get_info",
+                 "spx_batch_system_info", "spx_batch_get_perm", "spx_batch_get_factor"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -298,3 +332,122 @@ def update(m, nb_rows, k, A, lda, C, ldc, rowmap, colmap, lower=True, stream=Non
     st = load().spx_update(m, nb_rows, k, _ptr(A), lda, _ptr(C), ldc, _ptr(rowmap), _ptr(colmap),
                            1 if lower else 0, _stream_ptr(stream))
     _check(st, None)
+
+
+# ---------------------------------------------------------------------------
+# Batched static-pivot LU (spx_batch_*)
+# ---------------------------------------------------------------------------
+def _bcheck(status: int, handle=None):
+    if status != SPX_OK:
+        msg = load().spx_batch_last_error(handle)
+        raise SpxError(status, msg.decode() if msg else "")
+
+
+class Batch:
+    """Many small independent systems, factorized and solved in one launch."""
+
+    def __init__(self, raw: int, ns: np.ndarray, nnzs: np.ndarray):
+        self._h = raw
+        self.ns = ns
+        self.nnzs = nnzs
+        self.nsys = len(ns)
+        self.n_total = int(ns.sum())
+        self.nnz_total = int(nnzs.sum())
+
+    def free(self):
+        if self._h:
+            load().spx_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _args(self, values, B, X):
+        dev = _is_device(values)
+        if not dev:
+            values = np.ascontiguousarray(values, dtype=np.float64)
+            if B is not None:
+                B = np.ascontiguousarray(B, dtype=np.float64)
+                if X is None:
+                    X = np.empty(self.n_total, dtype=np.float64)
+        elif B is not None and X is None:
+            import torch
+            X = torch.empty(self.n_total, dtype=torch.float64, device=values.device)
+        return dev, values, B, X
+
+    def run(self, values, B=None, X=None, precision="fp32", refine=None, stream=None):
+        """Factorize all systems and (B given) solve each; returns (X, status name)."""
+        dev, values, B, X = self._args(values, B, X)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        rptr = ctypes.byref(refine) if refine is not None else None
+        st = load().spx_batch_run(self._h, _ptr(values), _ptr(B), _ptr(X), 1 if dev else 0, prec,
+                                  rptr, _stream_ptr(stream))
+        if st not in (SPX_OK, SPX_ERR_NOT_CONVERGED):
+            _bcheck(st, self._h)
+        return X, STATUS_NAMES[st]
+
+    def tune(self, values, B, X=None, precision="fp32", refine=None, stream=None):
+        dev, values, B, X = self._args(values, B, X)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        rptr = ctypes.byref(refine) if refine is not None else None
+        st = load().spx_batch_tune(self._h, _ptr(values), _ptr(B), _ptr(X), 1 if dev else 0, prec,
+                                   rptr, _stream_ptr(stream))
+        if st not in (SPX_OK, SPX_ERR_NOT_CONVERGED):
+            _bcheck(st, self._h)
+        return X, STATUS_NAMES[st]
+
+    def set_config(self, ctas_per_sm=0, leaf_width=8, rows_per_thread=0):
+        _bcheck(load().spx_batch_set_config(self._h, ctas_per_sm, leaf_width, rows_per_thread),
+                self._h)
+
+    def info(self) -> dict:
+        i = spx_batch_info()
+        _bcheck(load().spx_batch_get_info(self._h, ctypes.byref(i)), self._h)
+        return i.as_dict()
+
+    def system_info(self) -> dict:
+        out = {"iters": np.empty(self.nsys, np.int32), "berr": np.empty(self.nsys, np.float64),
+               "converged": np.empty(self.nsys, np.int32),
+               "npivot_repl": np.empty(self.nsys, np.int32), "bad_col": np.empty(self.nsys, np.int64)}
+        _bcheck(load().spx_batch_system_info(self._h, *[_ptr(out[k]) for k in
+                                                        ("iters", "berr", "converged",
+                                                         "npivot_repl", "bad_col")]), self._h)
+        return out
+
+    def perm(self, s: int) -> np.ndarray:
+        p = np.empty(int(self.ns[s]), dtype=np.int64)
+        _bcheck(load().spx_batch_get_perm(self._h, s, _ptr(p)), self._h)
+        return p
+
+    def factor_on_pattern(self, s: int, Lp: np.ndarray, Li: np.ndarray):
+        Lp = np.ascontiguousarray(Lp, dtype=np.int64)
+        Li = np.ascontiguousarray(Li, dtype=np.int32)
+        Lx = np.empty(len(Li), dtype=np.float64)
+        Ut = np.empty(len(Li), dtype=np.float64)
+        _bcheck(load().spx_batch_get_factor(self._h, s, _ptr(Lp), _ptr(Li), _ptr(Lx), _ptr(Ut)),
+                self._h)
+        return Lx, Ut
+
+
+def batch_analyze(systems, grids=None, **opts) -> Batch:
+    """spx_batch_analyze on a list of (colptr, rowind) host CSC patterns.
+    grids: None or a list of (nx, ny, nz) per system (grid ordering rule)."""
+    ns = np.array([len(cp) - 1 for cp, _ in systems], dtype=np.int64)
+    nnzs = np.array([int(cp[-1]) for cp, _ in systems], dtype=np.int64)
+    colptr = np.ascontiguousarray(np.concatenate([np.asarray(cp, np.int64) for cp, _ in systems])
+                                  if systems else np.zeros(0, np.int64))
+    rowind = np.ascontiguousarray(np.concatenate([np.asarray(ri, np.int32) for _, ri in systems])
+                                  if systems else np.zeros(0, np.int32))
+    g = None
+    if grids is not None:
+        g = np.ascontiguousarray(np.array([list(x) + [1] * (3 - len(x)) for x in grids],
+                                          dtype=np.int32).ravel())
+    o = default_options(**opts)
+    raw = _vp()
+    st = load().spx_batch_analyze(len(ns), _ptr(ns), _ptr(colptr), _ptr(rowind), _ptr(g),
+                                  ctypes.byref(o), ctypes.byref(raw))
+    _bcheck(st, None)
+    return Batch(raw.value, ns, nnzs)
