@@ -13,8 +13,10 @@ Pins (see the ``tests/test_oracle_*.py`` files): dense Cholesky / LU by
 brute force for n <= 200, ||A - L L^T||_F / ||A||_F <= 1e-14, the closed-form
 Cholesky factor of the 1-D Laplacian, the closed-form spectrum of the 2-D
 5-point Laplacian (log-determinant), column counts from two independent
-algorithms, a hand-ordered nested dissection of small grids and a
-hand-computed static-pivot replacement.
+algorithms, a hand-ordered nested dissection of small grids, a
+hand-computed static-pivot replacement, and for the selected inverse the
+dense inverse by brute force, the closed-form inverse of the 1-D Laplacian
+and trace(A Z) = n.
 """
 from __future__ import annotations
 
@@ -71,6 +73,7 @@ def _load():
             ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, ctypes.c_int64, _f64p, ctypes.c_int64,
         ]
         lib.ora_spmv.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p]
+        lib.ora_selinv.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p]
         _lib = lib
     return _lib
 
@@ -285,6 +288,44 @@ def solve(F: Factor, B: np.ndarray) -> np.ndarray:
     out = np.empty_like(X)
     out[F.perm, :] = X
     return out.ravel() if one else out
+
+
+def logdet(F: Factor) -> float:
+    """log det A = 2 sum_j log L(j, j) for a Cholesky factor."""
+    if F.method != "llt":
+        raise ValueError("logdet of a Cholesky factor only")
+    return float(2.0 * np.sum(np.log(F.Lx[F.sym.Lp[:-1]])))
+
+
+def selected_inverse(F: Factor) -> np.ndarray:
+    """Entries of (P A P^T)^{-1} on the pattern of L (Takahashi recurrence)."""
+    if F.method != "llt":
+        raise ValueError("selected inverse of a Cholesky factor only")
+    s = F.sym
+    Zx = np.zeros(len(F.Lx), dtype=np.float64)
+    rc = _load().ora_selinv(s.n, _p(s.Lp, _i64p), _p(s.Li, _i32p), _p(F.Lx, _f64p), _p(Zx, _f64p))
+    if rc != 0:
+        raise RuntimeError("pattern of L is not closed under the recurrence")
+    return Zx
+
+
+def logdet_gradient(A, F: Factor) -> np.ndarray:
+    """d log det A / d A_ij = (A^{-1})_ji for every stored entry of A, in
+    A's CSC order (entries treated as independent)."""
+    A = _csc(A)
+    Zx = selected_inverse(F)
+    s = F.sym
+    Z = sp.csc_matrix((Zx, s.Li, s.Lp), shape=(s.n, s.n))
+    iperm = np.empty_like(F.perm)
+    iperm[F.perm] = np.arange(len(F.perm))
+    coo = A.tocoo()
+    pi, pj = iperm[coo.row], iperm[coo.col]
+    r, c = np.maximum(pi, pj), np.minimum(pi, pj)
+    vals = np.asarray(Z[r, c]).ravel()
+    out = np.empty(A.nnz)
+    # tocoo of a canonical CSC keeps the CSC order
+    out[:] = vals
+    return out
 
 
 def spmv(A, x: np.ndarray) -> np.ndarray:

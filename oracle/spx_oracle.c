@@ -512,6 +512,58 @@ int ora_lu(int64_t n, const int64_t *Ap, const int32_t *Ai, const double *Ax, co
 }
 
 /* ------------------------------------------------------------------------ */
+/* Selected inverse of A = L L^T on the pattern of L (the Takahashi
+ * recurrence; the gradient of log det A is A^{-T} on A's pattern).  From
+ * Z = A^{-1} = L^{-T} L^{-1}, L^T Z is lower triangular with diagonal
+ * 1 / L(j,j); reading its entries (j, i), i >= j, gives, for the rows S of
+ * column j below the diagonal, processed for j = n-1 down to 0:
+ *   Z(i, j) = -(1 / L(j,j)) sum_{k in S} L(k, j) Z(k, i)      (i in S)
+ *   Z(j, j) = 1 / L(j,j)^2 - (1 / L(j,j)) sum_{k in S} L(k, j) Z(k, j)
+ * Every Z(k, i) with k, i in S lies in the pattern of L (columns of S are
+ * ancestors of j and S is a clique in the filled graph) and belongs to a
+ * column > j, already final.  Zx is returned on the pattern of L (lower
+ * entries, same positions as Lx).  Returns 0, or -1 if a needed entry is
+ * missing from the pattern.                                                 */
+/* ------------------------------------------------------------------------ */
+
+static int64_t ora_find(const int64_t *Lp, const int32_t *Li, int64_t col, int64_t row)
+{
+    int64_t lo = Lp[col], hi = Lp[col + 1] - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (Li[mid] == row) return mid;
+        if (Li[mid] < row) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+int ora_selinv(int64_t n, const int64_t *Lp, const int32_t *Li, const double *Lx, double *Zx)
+{
+    for (int64_t j = n - 1; j >= 0; --j) {
+        const int64_t p0 = Lp[j], p1 = Lp[j + 1];   /* p0: the diagonal */
+        const double d = Lx[p0];
+        /* off-diagonal entries first; they only read columns > j */
+        for (int64_t pi = p0 + 1; pi < p1; ++pi) {
+            const int64_t i = Li[pi];
+            double s = 0.0;
+            for (int64_t pk = p0 + 1; pk < p1; ++pk) {
+                const int64_t k = Li[pk];
+                const int64_t c = k < i ? k : i, r = k < i ? i : k;
+                const int64_t q = ora_find(Lp, Li, c, r);
+                if (q < 0) return -1;
+                s += Lx[pk] * Zx[q];
+            }
+            Zx[pi] = -s / d;
+        }
+        double s = 0.0;
+        for (int64_t pk = p0 + 1; pk < p1; ++pk) s += Lx[pk] * Zx[pk];
+        Zx[p0] = 1.0 / (d * d) - s / d;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Triangular solves on the factors (forward then backward substitution), in
  * the permuted numbering, nrhs columns of leading dimension ldb, in place. */
 /* ------------------------------------------------------------------------ */

@@ -88,6 +88,44 @@ def diffusion_3d(nx: int, ny: int, nz: int, seed: int, sigma: float = 1.0) -> sp
     return _finish(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
 
 
+def diffusion_3d_kappa(nx: int, ny: int, nz: int, seed: int, sigma: float = 1.0) -> np.ndarray:
+    """The node coefficients exp(sigma g) that diffusion_3d draws for this seed."""
+    return np.exp(sigma * rng(seed, STREAM_MATRIX).standard_normal(nx * ny * nz))
+
+
+def diffusion_3d_coefficient_map(nx: int, ny: int, nz: int):
+    """The values of diffusion_3d are linear in the node coefficients kappa:
+    returns (colptr, rowind, M) with the CSC pattern of diffusion_3d and a
+    sparse M (nnz x n) such that its values are M @ kappa."""
+    n = nx * ny * nz
+    idx = _node_index(nx, ny, nz)
+    R, C, node, coef = [], [], [], []
+
+    def add(r, c, m, v):
+        R.append(r); C.append(c); node.append(m); coef.append(np.full(r.size, v))
+
+    for ax in (2, 1, 0):
+        a = np.take(idx, np.arange(idx.shape[ax] - 1), axis=ax).ravel()
+        b = np.take(idx, np.arange(1, idx.shape[ax]), axis=ax).ravel()
+        for (r, c) in ((a, b), (b, a)):
+            add(r, c, a, -0.5); add(r, c, b, -0.5)
+        for r in (a, b):
+            add(r, r, a, 0.5); add(r, r, b, 0.5)
+        lo = np.take(idx, [0], axis=ax).ravel()
+        hi = np.take(idx, [idx.shape[ax] - 1], axis=ax).ravel()
+        add(lo, lo, lo, 1.0); add(hi, hi, hi, 1.0)
+    R = np.concatenate(R); C = np.concatenate(C)
+    key = C * n + R
+    uniq = np.unique(key)
+    pos = np.searchsorted(uniq, key)
+    M = sp.csr_matrix((np.concatenate(coef), (pos, np.concatenate(node))), shape=(uniq.size, n))
+    M.sum_duplicates()
+    rowind = (uniq % n).astype(np.int32)
+    colptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(uniq // n, minlength=n), out=colptr[1:])
+    return colptr, rowind, M
+
+
 def _haar_rotations(g: np.random.Generator, count: int) -> np.ndarray:
     """count x 3 x 3 rotations: QR of a Gaussian, signs fixed, det +1."""
     z = g.standard_normal((count, 3, 3))
