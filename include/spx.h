@@ -194,6 +194,44 @@ spx_status spx_get_panels(spx_handle h, int64_t *first_col, int32_t *width, int3
 spx_status spx_solve_noalloc(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
                              int64_t ldx, void *cuda_stream);
 
+/* ---- Differentiation: log-determinant, selected inverse, adjoints -------
+ *
+ * For a solve x = A^{-1} b with loss gradient g = dL/dx, the adjoint reuses
+ * the stored factor: lambda = A^{-T} g (spx_solve on g; A is symmetric for
+ * a Cholesky factor), dL/db = lambda and dL/dA = -lambda x^T, needed only on
+ * A's pattern (spx_solve_grad).  For log det A = 2 sum_j log L(j,j)
+ * (spx_logdet), d log det A / dA = A^{-T}, again only on A's pattern: the
+ * selected inverse Z = (P A P^T)^{-1} on the structure of L (Takahashi's
+ * recurrence, by panels from the root down, gathering the entries it needs
+ * through the same row maps as the updates of Sec. V-B) gives it
+ * (spx_selected_inverse, spx_logdet_grad).  Gradients are with respect to
+ * the stored CSC values, each entry independent, in the analysed pattern's
+ * order. */
+
+/* log det A of the last Cholesky factorization (FP64 sum; an FP32 factor
+ * gives an FP32-accurate value). */
+spx_status spx_logdet(spx_handle h, double *logdet);
+
+/* Selected inverse of the last Cholesky factorization, kept on the device;
+ * needs an SPX_FP64 factor and panels at most 64 wide (max_width <= 64). */
+spx_status spx_selected_inverse(spx_handle h, void *cuda_stream);
+
+/* Entries of the selected inverse on a caller-given lower pattern of the
+ * permuted matrix (Lp, Li as for spx_get_factor), into host Zx. */
+spx_status spx_get_selected_inverse(spx_handle h, const int64_t *Lp, const int32_t *Li, double *Zx);
+
+/* grad[e] = (A^{-1})_{ji} for every stored entry e = (i, j) of A (nnz
+ * doubles, host or device per on_device); computes the selected inverse
+ * first if needed. */
+spx_status spx_logdet_grad(spx_handle h, double *grad, int on_device, void *cuda_stream);
+
+/* grad[e] = -sum_r Lam(i, r) X(j, r) for every stored entry e = (i, j) of A:
+ * the adjoint of X = A^{-1} B with respect to A's values, given Lam =
+ * A^{-T} dL/dX.  Lam, X: n x nrhs column-major (ldl, ldx >= n); grad: nnz
+ * doubles; all host or all device per on_device. */
+spx_status spx_solve_grad(spx_handle h, int32_t nrhs, const double *Lam, int64_t ldl, const double *X,
+                          int64_t ldx, double *grad, int on_device, void *cuda_stream);
+
 /* Message for the last failing call on h (or on handle creation when h is
  * NULL).  The string stays valid until the next call on h. */
 const char *spx_last_error(spx_handle h);

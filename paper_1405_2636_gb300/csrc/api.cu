@@ -96,6 +96,17 @@ struct spx_handle_s {
     cudaGraphExec_t sgraph = nullptr;
     int sgraph_nrhs = -1, sgraph_prec = -1;
 
+    // selected inverse and adjoints: Z on the panel structure (FP64), the
+    // scaled panels L_RJ L_JJ^{-1}, tasks by source panel, and the position
+    // in Z of every input entry
+    bool zready = false;
+    double *d_Zsel = nullptr, *d_Lh = nullptr;
+    int32_t *d_srctask_ptr = nullptr, *d_srctask_idx = nullptr;
+    int64_t *d_zmap = nullptr;
+    double *d_scalar = nullptr;
+    double *d_gtmp = nullptr, *d_lam = nullptr, *d_xg = nullptr;
+    int64_t gtmp_len = 0;
+
     // profiling and launch accounting
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -908,6 +919,7 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         }
     }
     h->factored = false;
+    h->zready = false;
     if (P.method == SPX_LLT && precision != SPX_FP64) {
         if ((st = ensure_operand_copy(h, precision == SPX_BF16 ? 1 : (precision == SPX_FP32 ? 2 : 0))))
             return st;
@@ -1200,6 +1212,189 @@ spx_status spx_solve_noalloc(spx_handle h, int32_t nrhs, const double *B, int64_
     else
         enqueue_sweep_noalloc<float>(h, nrhs, B, ldb, X, ldx, (float *)scratch, s);
     CU(cudaGetLastError());
+    return SPX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// log-determinant, selected inverse and the adjoints of solve / logdet
+// ---------------------------------------------------------------------------
+namespace {
+
+spx_status ensure_scalar(spx_handle h)
+{
+    if (h->d_scalar) return SPX_OK;
+    return dalloc(h, &h->d_scalar, 4);
+}
+
+// grad workspace of len doubles (host-buffer calls)
+spx_status ensure_gtmp(spx_handle h, int64_t len)
+{
+    if (h->gtmp_len >= len) return SPX_OK;
+    dfree(h, h->d_gtmp);
+    h->d_gtmp = nullptr;
+    h->gtmp_len = 0;
+    spx_status st = dalloc(h, &h->d_gtmp, (size_t)len);
+    if (st == SPX_OK) h->gtmp_len = len;
+    return st;
+}
+
+// offset in the panel storage of the lower entry (max(pi,pj), min(pi,pj))
+// of every input entry, in the input's CSC order
+spx_status build_zmap(spx_handle h, const int64_t *colptr_unused)
+{
+    (void)colptr_unused;
+    if (h->d_zmap) return SPX_OK;
+    const spx::Plan &P = h->plan;
+    std::vector<int64_t> zmap((size_t)P.nnz_a, 0);
+    for (int64_t i = 0; i < P.n; ++i)
+        for (int64_t e = P.csr_ptr[i]; e < P.csr_ptr[i + 1]; ++e) {
+            const int64_t j = P.csr_col[e];
+            const int64_t a = std::max(P.iperm[i], P.iperm[j]), b = std::min(P.iperm[i], P.iperm[j]);
+            const int32_t pb = P.col2panel[b];
+            const int32_t *rb = P.rows.data() + P.prow[pb], *re = P.rows.data() + P.prow[pb + 1];
+            const int32_t *it = std::lower_bound(rb, re, (int32_t)a);
+            if (it == re || *it != a) return fail(h, SPX_ERR_ARG, "input entry outside the factor structure");
+            zmap[(size_t)P.csr_src[e]] = P.pval[pb] + (b - P.pfcol[pb]) * P.ph[pb] + (it - rb);
+        }
+    return upload(h, &h->d_zmap, zmap);
+}
+
+}  // namespace
+
+spx_status spx_logdet(spx_handle h, double *logdet)
+{
+    if (!h || !logdet) return fail(h, SPX_ERR_ARG, "NULL argument");
+    if (!h->factored) return fail(h, SPX_ERR_STATE, "no factor");
+    if (h->plan.method != SPX_LLT) return fail(h, SPX_ERR_ARG, "log det of a Cholesky factor only");
+    spx_status st;
+    if ((st = ensure_scalar(h))) return st;
+    if (h->precision == SPX_FP64) spx::launch_logdet<double>(h->dp, (const double *)h->d_L, h->d_scalar, h->hs);
+    else spx::launch_logdet<float>(h->dp, (const float *)h->d_L, h->d_scalar, h->hs);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(logdet, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
+    return SPX_OK;
+}
+
+spx_status spx_selected_inverse(spx_handle h, void *cuda_stream)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (!h->factored) return fail(h, SPX_ERR_STATE, "no factor");
+    if (h->plan.method != SPX_LLT || h->precision != SPX_FP64)
+        return fail(h, SPX_ERR_ARG, "the selected inverse needs an FP64 Cholesky factor");
+    if (h->zready) return SPX_OK;
+    const spx::Plan &P = h->plan;
+    const size_t elems = (size_t)P.pval[P.npanels];
+    spx_status st;
+    if (!h->d_Zsel) {
+        if ((st = dalloc(h, &h->d_Zsel, elems)) || (st = dalloc(h, &h->d_Lh, elems))) return st;
+        std::vector<int32_t> ptr(P.npanels + 1, 0), idx(P.tasks.size());
+        for (const auto &t : P.tasks) ptr[t.src + 1]++;
+        for (int32_t q = 0; q < P.npanels; ++q) ptr[q + 1] += ptr[q];
+        std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+        for (size_t t = 0; t < P.tasks.size(); ++t) idx[fill[P.tasks[t].src]++] = (int32_t)t;
+        if ((st = upload(h, &h->d_srctask_ptr, ptr)) || (st = upload(h, &h->d_srctask_idx, idx))) return st;
+    }
+    fence_from(h, cuda_stream);
+    const int wmax = *std::max_element(h->lvl_wmax.begin(), h->lvl_wmax.end());
+    if (wmax > 64) return fail(h, SPX_ERR_ARG, "the selected inverse takes panels up to 64 wide (max_width <= 64)");
+    CU(cudaMemcpyAsync(h->d_Lh, h->d_L, elems * sizeof(double), cudaMemcpyDeviceToDevice, h->hs));
+    spx::launch_trsm<double>(h->dp, h->d_chunks, (int)h->chunk_ptr[P.nlevels], wmax,
+                             (const double *)h->d_Dinv, h->d_Lh, spx::TRSM_RIGHT_LINV, nullptr, nullptr, 0, 0,
+                             h->hs);
+    for (int32_t l = P.nlevels - 1; l >= 0; --l) {
+        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
+        spx::launch_selinv_off(h->dp, h->d_chunks + h->chunk_ptr[l], nch, h->d_srctask_ptr, h->d_srctask_idx,
+                               h->d_tasks, h->d_Lh, h->d_Zsel, h->hs);
+        spx::launch_selinv_diag(h->dp, h->d_level_panels + P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l],
+                                h->lvl_wmax[l], (const double *)h->d_Dinv, h->d_Lh, h->d_Zsel, h->hs);
+    }
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->hs));
+    h->zready = true;
+    return SPX_OK;
+}
+
+spx_status spx_get_selected_inverse(spx_handle h, const int64_t *Lp, const int32_t *Li, double *Zx)
+{
+    if (!h || !Lp || !Li || !Zx) return fail(h, SPX_ERR_ARG, "NULL argument");
+    if (!h->zready) return fail(h, SPX_ERR_STATE, "no selected inverse (call spx_selected_inverse)");
+    const spx::Plan &P = h->plan;
+    const size_t elems = (size_t)P.pval[P.npanels];
+    std::vector<double> hz(elems);
+    CU(cudaMemcpy(hz.data(), h->d_Zsel, elems * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < P.n; ++j) {
+        const int32_t pj = P.col2panel[j];
+        const int32_t *rb = P.rows.data() + P.prow[pj], *re = P.rows.data() + P.prow[pj + 1];
+        for (int64_t q = Lp[j]; q < Lp[j + 1]; ++q) {
+            const int64_t i = Li[q];
+            if (i < j || i >= P.n) return fail(h, SPX_ERR_ARG, "pattern entry above the diagonal");
+            const int32_t *it = std::lower_bound(rb, re, (int32_t)i);
+            if (it == re || *it != i) return fail(h, SPX_ERR_ARG, "pattern entry outside the panel structure");
+            Zx[q] = hz[P.pval[pj] + (j - P.pfcol[pj]) * P.ph[pj] + (it - rb)];
+        }
+    }
+    return SPX_OK;
+}
+
+spx_status spx_logdet_grad(spx_handle h, double *grad, int on_device, void *cuda_stream)
+{
+    if (!h || !grad) return fail(h, SPX_ERR_ARG, "NULL argument");
+    spx_status st;
+    if (!h->zready && (st = spx_selected_inverse(h, cuda_stream))) return st;
+    if ((st = build_zmap(h, nullptr))) return st;
+    const int64_t nnz = h->plan.nnz_a;
+    double *dst = grad;
+    if (!on_device) {
+        if ((st = ensure_gtmp(h, nnz))) return st;
+        dst = h->d_gtmp;
+    }
+    fence_from(h, cuda_stream);
+    spx::launch_gather(nnz, h->d_zmap, h->d_Zsel, dst, h->hs);
+    CU(cudaGetLastError());
+    if (!on_device) CU(cudaMemcpyAsync(grad, dst, sizeof(double) * nnz, cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
+    return SPX_OK;
+}
+
+spx_status spx_solve_grad(spx_handle h, int32_t nrhs, const double *Lam, int64_t ldl, const double *X,
+                          int64_t ldx, double *grad, int on_device, void *cuda_stream)
+{
+    if (!h || !Lam || !X || !grad) return fail(h, SPX_ERR_ARG, "NULL argument");
+    const spx::Plan &P = h->plan;
+    if (nrhs < 1 || ldl < P.n || ldx < P.n) return fail(h, SPX_ERR_ARG, "bad nrhs or leading dimension");
+    spx_status st = ensure_device(h);
+    if (st != SPX_OK) return st;
+    fence_from(h, cuda_stream);
+    const double *dl = Lam, *dx = X;
+    double *dg = grad;
+    if (!on_device) {
+        // host buffers: three device vectors of `need` doubles (Lam, X, grad)
+        const int64_t need = std::max<int64_t>((int64_t)P.n * nrhs, P.nnz_a);
+        if (!h->d_lam || h->gtmp_len < need) {
+            dfree(h, h->d_lam);
+            dfree(h, h->d_xg);
+            dfree(h, h->d_gtmp);
+            h->d_lam = h->d_xg = h->d_gtmp = nullptr;
+            h->gtmp_len = 0;
+            if ((st = dalloc(h, &h->d_lam, (size_t)need)) || (st = dalloc(h, &h->d_xg, (size_t)need)) ||
+                (st = dalloc(h, &h->d_gtmp, (size_t)need)))
+                return st;
+            h->gtmp_len = need;
+        }
+        CU(cudaMemcpy2DAsync(h->d_lam, P.n * sizeof(double), Lam, ldl * sizeof(double), P.n * sizeof(double), nrhs,
+                             cudaMemcpyHostToDevice, h->hs));
+        CU(cudaMemcpy2DAsync(h->d_xg, P.n * sizeof(double), X, ldx * sizeof(double), P.n * sizeof(double), nrhs,
+                             cudaMemcpyHostToDevice, h->hs));
+        dl = h->d_lam;
+        dx = h->d_xg;
+        ldl = ldx = P.n;
+        dg = h->d_gtmp;
+    }
+    spx::launch_solve_grad(P.n, nrhs, h->d_csr_ptr, h->d_csr_col, h->d_csr_src, dl, ldl, dx, ldx, dg, h->hs);
+    CU(cudaGetLastError());
+    if (!on_device) CU(cudaMemcpyAsync(grad, dg, sizeof(double) * P.nnz_a, cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
     return SPX_OK;
 }
 

@@ -759,6 +759,7 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
 //   LLT : B = L^{-T}           (B(k,j) = Linv(j,k))
 //   LU_L: B = U^{-1}           (B(k,j) = Uinv(k,j))
 //   LU_U: B = L^{-T}, unit L   (B(k,j) = Linv(j,k), 1 on the diagonal)
+//   RIGHT_LINV: B = L^{-1}     (B(k,j) = Linv(k,j); the selected inversion's L_RJ L_JJ^{-1})
 // The CTA copies its rows to shared memory first, so writing them back in
 // place is safe; 64 x 64 output tiles, 4 x 4 per thread, K-chunks of 16.
 // ---------------------------------------------------------------------------
@@ -805,7 +806,8 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                 const int k = k0 + kk, j = c0 + jj;
                 T v = (T)0;
                 if (k < w && j < w) {
-                    if (mode == TRSM_LU_L) v = (k <= j) ? Mi[k + j * w] : (T)0;
+                    if (mode == TRSM_RIGHT_LINV) v = (k >= j) ? Mi[k + j * w] : (T)0;
+                    else if (mode == TRSM_LU_L) v = (k <= j) ? Mi[k + j * w] : (T)0;
                     else if (j > k) v = Mi[j + k * w];
                     else if (j == k) v = (mode == TRSM_LU_U) ? (T)1 : Mi[j + k * w];
                 }

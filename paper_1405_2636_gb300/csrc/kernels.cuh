@@ -50,7 +50,8 @@ constexpr int kTrsmRows = 64;
 enum TrsmMode : int {
     TRSM_LLT = 0,        // X <- X L^{-T}, L = lower(D)            (Cholesky)
     TRSM_LU_L = 1,       // X <- X U^{-1}, U = upper(D)            (LU, L panel)
-    TRSM_LU_U = 2        // X <- X L^{-T}, L = unit lower(D)       (LU, U^T panel)
+    TRSM_LU_U = 2,       // X <- X L^{-T}, L = unit lower(D)       (LU, U^T panel)
+    TRSM_RIGHT_LINV = 3  // X <- X L^{-1}, L = lower(D)            (selected inversion)
 };
 
 // ---- factorization -------------------------------------------------------
@@ -140,5 +141,18 @@ void launch_row_abs_sum_max(int64_t n, const int64_t *rp, const int64_t *src, co
                             unsigned long long *out, cudaStream_t s);
 void launch_axpy_cols(int64_t n, int nrhs, const double *D, double *X, int64_t ldx,
                       cudaStream_t s);
+
+// ---- selected inversion, log-determinant, adjoints (selinv.cu) ----------
+void launch_selinv_off(const DevPlan &p, const RowChunk *chunks, int count, const int32_t *task_ptr,
+                       const int32_t *task_idx, const DevTask *tasks, const double *Lh, double *Z,
+                       cudaStream_t s);
+void launch_selinv_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const double *Dinv,
+                        const double *Lh, double *Z, cudaStream_t s);
+template <typename T>
+void launch_logdet(const DevPlan &p, const T *L, double *out, cudaStream_t s);
+void launch_gather(int64_t nnz, const int64_t *zmap, const double *Z, double *grad, cudaStream_t s);
+void launch_solve_grad(int64_t n, int nrhs, const int64_t *rp, const int32_t *ci, const int64_t *src,
+                       const double *Lam, int64_t ldl, const double *X, int64_t ldx, double *grad,
+                       cudaStream_t s);
 
 }  // namespace spx

@@ -35,7 +35,9 @@ EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_fac
             "spx_get_panels", "spx_solve_noalloc",
             "spx_batch_analyze", "spx_batch_run", "spx_batch_tune", "spx_batch_set_config",
             "spx_batch_get_info", "spx_batch_system_info", "spx_batch_get_perm",
-            "spx_batch_get_factor", "spx_batch_last_error", "spx_batch_free"]
+            "spx_batch_get_factor", "spx_batch_last_error", "spx_batch_free",
+            "spx_logdet", "spx_selected_inverse", "spx_get_selected_inverse", "spx_logdet_grad",
+            "spx_solve_grad"]
 
 
 class spx_options(ctypes.Structure):
@@ -144,13 +146,20 @@ def load():
     lib.spx_batch_get_factor.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
     lib.spx_batch_last_error.argtypes = [_vp]
     lib.spx_batch_last_error.restype = ctypes.c_char_p
+    lib.spx_logdet.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    lib.spx_selected_inverse.argtypes = [_vp, _vp]
+    lib.spx_get_selected_inverse.argtypes = [_vp, _vp, _vp, _vp]
+    lib.spx_logdet_grad.argtypes = [_vp, _vp, ctypes.c_int, _vp]
+    lib.spx_solve_grad.argtypes = [_vp, ctypes.c_int32, _vp, _i64, _vp, _i64, _vp, ctypes.c_int, _vp]
     lib.spx_batch_free.argtypes = [_vp]
     lib.spx_batch_free.restype = None
     for name in ("spx_analyze", "spx_factorize", "spx_solve", "spx_get_info", "spx_get_perm",
                  "spx_get_factor", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
                  "spx_get_panels", "spx_solve_noalloc", "spx_batch_analyze", "spx_batch_run",
                  "spx_batch_tune", "spx_batch_set_config", "spx_batch_get_info",
-                 "spx_batch_system_info", "spx_batch_get_perm", "spx_batch_get_factor"):
+                 "spx_batch_system_info", "spx_batch_get_perm", "spx_batch_get_factor",
+                 "spx_logdet", "spx_selected_inverse", "spx_get_selected_inverse",
+                 "spx_logdet_grad", "spx_solve_grad"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -297,6 +306,52 @@ class Handle:
         p = np.empty(self.n, dtype=np.int64)
         _check(load().spx_get_perm(self._h, _ptr(p)), self._h)
         return p
+
+    # -- differentiation -------------------------------------------------------
+    def logdet(self) -> float:
+        v = ctypes.c_double()
+        _check(load().spx_logdet(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def selected_inverse(self, stream=None):
+        _check(load().spx_selected_inverse(self._h, _stream_ptr(stream)), self._h)
+
+    def selected_inverse_on_pattern(self, Lp: np.ndarray, Li: np.ndarray) -> np.ndarray:
+        Lp = np.ascontiguousarray(Lp, dtype=np.int64)
+        Li = np.ascontiguousarray(Li, dtype=np.int32)
+        Zx = np.empty(len(Li), dtype=np.float64)
+        _check(load().spx_get_selected_inverse(self._h, _ptr(Lp), _ptr(Li), _ptr(Zx)), self._h)
+        return Zx
+
+    def logdet_grad(self, out=None, stream=None):
+        """(A^{-1})_{ji} for every stored entry (i, j), in CSC order."""
+        if out is None:
+            out = np.empty(self.nnz, dtype=np.float64)
+        _check(load().spx_logdet_grad(self._h, _ptr(out), 1 if _is_device(out) else 0,
+                                      _stream_ptr(stream)), self._h)
+        return out
+
+    def solve_grad(self, Lam, X, out=None, stream=None):
+        """-sum_r Lam(i, r) X(j, r) for every stored entry (i, j).  Lam, X:
+        (n,) or column-major (n, nrhs), both host or both CUDA tensors."""
+        dev = _is_device(Lam)
+        if dev:
+            nrhs = 1 if Lam.dim() == 1 else Lam.shape[1]
+            ldl = self.n if Lam.dim() == 1 else Lam.stride(1)
+            ldx = self.n if X.dim() == 1 else X.stride(1)
+            if out is None:
+                import torch
+                out = torch.empty(self.nnz, dtype=torch.float64, device=Lam.device)
+        else:
+            Lam = np.asfortranarray(Lam, dtype=np.float64)
+            X = np.asfortranarray(X, dtype=np.float64)
+            nrhs = 1 if Lam.ndim == 1 else Lam.shape[1]
+            ldl = ldx = self.n
+            if out is None:
+                out = np.empty(self.nnz, dtype=np.float64)
+        _check(load().spx_solve_grad(self._h, nrhs, _ptr(Lam), ldl, _ptr(X), ldx, _ptr(out),
+                                     1 if dev else 0, _stream_ptr(stream)), self._h)
+        return out
 
     def factor_on_pattern(self, Lp: np.ndarray, Li: np.ndarray, lu: bool = False):
         Lp = np.ascontiguousarray(Lp, dtype=np.int64)
