@@ -101,7 +101,7 @@ struct spx_handle_s {
     // in Z of every input entry
     bool zready = false;
     double *d_Zsel = nullptr, *d_Lh = nullptr;
-    int32_t *d_srctask_ptr = nullptr, *d_srctask_idx = nullptr;
+    int32_t *d_row_task = nullptr;
     int64_t *d_zmap = nullptr;
     double *d_scalar = nullptr;
     double *d_gtmp = nullptr, *d_lam = nullptr, *d_xg = nullptr;
@@ -1288,26 +1288,43 @@ spx_status spx_selected_inverse(spx_handle h, void *cuda_stream)
     spx_status st;
     if (!h->d_Zsel) {
         if ((st = dalloc(h, &h->d_Zsel, elems)) || (st = dalloc(h, &h->d_Lh, elems))) return st;
-        std::vector<int32_t> ptr(P.npanels + 1, 0), idx(P.tasks.size());
-        for (const auto &t : P.tasks) ptr[t.src + 1]++;
-        for (int32_t q = 0; q < P.npanels; ++q) ptr[q + 1] += ptr[q];
-        std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
-        for (size_t t = 0; t < P.tasks.size(); ++t) idx[fill[P.tasks[t].src]++] = (int32_t)t;
-        if ((st = upload(h, &h->d_srctask_ptr, ptr)) || (st = upload(h, &h->d_srctask_idx, idx))) return st;
+        // the task whose facing rows hold each off-diagonal row of a panel
+        std::vector<int32_t> row_task((size_t)P.prow[P.npanels], -1);
+        for (size_t t = 0; t < P.tasks.size(); ++t) {
+            const spx::Task &tk = P.tasks[t];
+            for (int32_t r = tk.r0; r < tk.r1; ++r) row_task[(size_t)P.prow[tk.src] + r] = (int32_t)t;
+        }
+        for (int32_t q = 0; q < P.npanels; ++q)
+            for (int32_t r = P.pw[q]; r < P.ph[q]; ++r)
+                if (row_task[(size_t)P.prow[q] + r] < 0) return fail(h, SPX_ERR_ARG, "row without an update task");
+        if ((st = upload(h, &h->d_row_task, row_task))) return st;
     }
     fence_from(h, cuda_stream);
     const int wmax = *std::max_element(h->lvl_wmax.begin(), h->lvl_wmax.end());
     if (wmax > 64) return fail(h, SPX_ERR_ARG, "the selected inverse takes panels up to 64 wide (max_width <= 64)");
     CU(cudaMemcpyAsync(h->d_Lh, h->d_L, elems * sizeof(double), cudaMemcpyDeviceToDevice, h->hs));
+    CU(cudaMemsetAsync(h->d_Zsel, 0, elems * sizeof(double), h->hs));   // split-K partial sums add into it
     spx::launch_trsm<double>(h->dp, h->d_chunks, (int)h->chunk_ptr[P.nlevels], wmax,
                              (const double *)h->d_Dinv, h->d_Lh, spx::TRSM_RIGHT_LINV, nullptr, nullptr, 0, 0,
                              h->hs);
+    // split-K so that a level keeps about two CTAs per SM busy near the root
+    int nsm = 0;
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int want = 2 * nsm;
     for (int32_t l = P.nlevels - 1; l >= 0; --l) {
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
-        spx::launch_selinv_off(h->dp, h->d_chunks + h->chunk_ptr[l], nch, h->d_srctask_ptr, h->d_srctask_idx,
-                               h->d_tasks, h->d_Lh, h->d_Zsel, h->hs);
-        spx::launch_selinv_diag(h->dp, h->d_level_panels + P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l],
-                                h->lvl_wmax[l], (const double *)h->d_Dinv, h->d_Lh, h->d_Zsel, h->hs);
+        const int npl = P.level_ptr[l + 1] - P.level_ptr[l];
+        int max_rchunks = 1;   // most 16-row chunks of R in a panel of the level
+        for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q) {
+            const int32_t k = P.level_panels[q];
+            max_rchunks = std::max(max_rchunks, (P.ph[k] - P.pw[k] + 15) / 16);
+        }
+        const int so = nch > 0 ? std::min(max_rchunks, std::max(1, (want + nch - 1) / nch)) : 1;
+        const int sd = std::min((max_rchunks + 1) / 2, std::max(1, (want + npl - 1) / std::max(npl, 1)));
+        spx::launch_selinv_off(h->dp, h->d_chunks + h->chunk_ptr[l], nch, so, h->d_row_task, h->d_tasks,
+                               h->d_Lh, h->d_Zsel, h->hs);
+        spx::launch_selinv_diag(h->dp, h->d_level_panels + P.level_ptr[l], npl, sd, h->lvl_wmax[l],
+                                (const double *)h->d_Dinv, h->d_Lh, h->d_Zsel, h->hs);
     }
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(h->hs));

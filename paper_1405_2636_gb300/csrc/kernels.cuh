@@ -143,11 +143,13 @@ void launch_axpy_cols(int64_t n, int nrhs, const double *D, double *X, int64_t l
                       cudaStream_t s);
 
 // ---- selected inversion, log-determinant, adjoints (selinv.cu) ----------
-void launch_selinv_off(const DevPlan &p, const RowChunk *chunks, int count, const int32_t *task_ptr,
-                       const int32_t *task_idx, const DevTask *tasks, const double *Lh, double *Z,
+// row_task[prow[p] + r]: the update task of panel p whose facing rows hold
+// row r (r >= width of p)
+void launch_selinv_off(const DevPlan &p, const RowChunk *chunks, int count, int nsplit,
+                       const int32_t *row_task, const DevTask *tasks, const double *Lh, double *Z,
                        cudaStream_t s);
-void launch_selinv_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const double *Dinv,
-                        const double *Lh, double *Z, cudaStream_t s);
+void launch_selinv_diag(const DevPlan &p, const int32_t *panels, int count, int nsplit, int wmax,
+                        const double *Dinv, const double *Lh, double *Z, cudaStream_t s);
 template <typename T>
 void launch_logdet(const DevPlan &p, const T *L, double *out, cudaStream_t s);
 void launch_gather(int64_t nnz, const int64_t *zmap, const double *Z, double *grad, cudaStream_t s);

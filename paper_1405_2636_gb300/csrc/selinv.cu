@@ -20,33 +20,64 @@
 namespace spx {
 
 // ---------------------------------------------------------------------------
-// Z_RJ for rows [r0, r0+64) of one panel: -sum over the panel's tasks of
-//   part A (rows i in [r0t, h)):  Z(i, j) Lh(j, :),  j in F_t
-//   part B (rows i in F_t):       Z(j, i) Lh(j, :),  j in [r1t, h)
-// which together cover every (i, j) of R x R once.  64 x WC output tile
-// (WC = 16, 32 or 64 columns, the panel width rounded up), 4 x WC/16 per
-// thread, K-chunks of 16 staged in shared memory.
+// Z_RJ for rows [r0, r0+64) of one panel: Z_RJ(i, :) = -sum_{j in R}
+// Z(i, j) Lh(j, :).  Row j of R faces the task t(j) (row_task), whose target
+// panel q holds the column of row j.  The entry Z(i, j) is stored
+//   in q = tgt(t(j)) at row relmap_t(j)(i), column row(j) - fcol(q)  if i >= r0(t(j)),
+//   else (i lies in an earlier facing block, j below it) in tgt(t(i)) at
+//   row relmap_t(i)(j), column row(i) - fcol(tgt(t(i))).
+// 64 x WC output tile (WC = 16, 32 or 64, the panel width rounded up),
+// 4 x WC/16 outputs per thread, K = the rows of R in chunks of 16 staged in
+// shared memory.  Split-K near the root, where a level holds one panel:
+// gridDim.y CTAs share a row chunk, each taking a contiguous part of R, and
+// add their partial sums into Z (zeroed beforehand).
 // ---------------------------------------------------------------------------
 template <int WC>
 __device__ __forceinline__ void selinv_off_tile(const DevPlan &p, int pid, int w, int h, int i0, int i1,
-                                                const int32_t *__restrict__ task_ptr,
-                                                const int32_t *__restrict__ task_idx,
+                                                const int32_t *__restrict__ row_task,
                                                 const DevTask *__restrict__ tasks,
                                                 const double *__restrict__ Lh, double *__restrict__ Z,
-                                                double (*As)[65], double (*Bs)[65])
+                                                double (*As)[65], double (*Bs)[65], int split, int nsplit)
 {
     constexpr int NB = WC / 16;
     const int64_t base = p.pval[pid];
     const double *Lp = Lh + base;
     const int32_t *srow = p.rows + p.prow[pid];
+    const int32_t *rt = row_task + p.prow[pid];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double acc[4][NB];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < NB; ++b) acc[a][b] = 0.0;
-
-    auto fma_chunk = [&]() {
+    // this CTA's part of R: 16-row aligned segment [kb, ke)
+    const int nk = (h - w + 15) / 16;
+    const int per = (nk + nsplit - 1) / nsplit;
+    const int kb = w + 16 * min(nk, split * per), ke = min(h, w + 16 * min(nk, (split + 1) * per));
+    for (int k0 = kb; k0 < ke; k0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int r = e & 63, kk = e >> 6;
+            const int i = i0 + r, j = k0 + kk;
+            double v = 0.0;
+            if (i < i1 && j < ke) {
+                const DevTask tj = tasks[rt[j]];
+                if (i >= tj.r0) {
+                    v = Z[p.pval[tj.tgt] + p.relmap[tj.relmap_off + i - tj.r0] +
+                          (int64_t)(srow[j] - p.pfcol[tj.tgt]) * p.ph[tj.tgt]];
+                } else {
+                    const DevTask ti = tasks[rt[i]];
+                    v = Z[p.pval[ti.tgt] + p.relmap[ti.relmap_off + j - ti.r0] +
+                          (int64_t)(srow[i] - p.pfcol[ti.tgt]) * p.ph[ti.tgt]];
+                }
+            }
+            As[kk][r] = v;
+        }
+        for (int e = tid; e < 16 * WC; e += 256) {
+            const int c = e % WC, kk = e / WC;
+            const int j = k0 + kk;
+            Bs[kk][c] = (j < ke && c < w) ? Lp[j + (int64_t)c * h] : 0.0;
+        }
+        __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             double av[4], bv[NB];
@@ -59,51 +90,7 @@ __device__ __forceinline__ void selinv_off_tile(const DevPlan &p, int pid, int w
 #pragma unroll
                 for (int b = 0; b < NB; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
         }
-    };
-    auto load_b = [&](int k0, int kend) {
-        for (int e = tid; e < 16 * WC; e += 256) {
-            const int c = e % WC, kk = e / WC;
-            const int j = k0 + kk;
-            Bs[kk][c] = (j < kend && c < w) ? Lp[j + (int64_t)c * h] : 0.0;
-        }
-    };
-
-    for (int q = task_ptr[pid]; q < task_ptr[pid + 1]; ++q) {
-        const DevTask tk = tasks[task_idx[q]];
-        const int hq = p.ph[tk.tgt];
-        const int64_t fq = p.pfcol[tk.tgt];
-        const double *Zq = Z + p.pval[tk.tgt];
-        const int32_t *rmap = p.relmap + tk.relmap_off - tk.r0;
-        const int a0 = max(i0, tk.r0);
-        if (a0 < i1) {
-            for (int k0 = tk.r0; k0 < tk.r1; k0 += 16) {
-                for (int e = tid; e < 16 * 64; e += 256) {
-                    const int r = e & 63, kk = e >> 6;
-                    const int i = i0 + r, j = k0 + kk;
-                    As[kk][r] = (i >= a0 && i < i1 && j < tk.r1)
-                                    ? Zq[rmap[i] + (int64_t)(srow[j] - fq) * hq] : 0.0;
-                }
-                load_b(k0, tk.r1);
-                __syncthreads();
-                fma_chunk();
-                __syncthreads();
-            }
-        }
-        const int b0 = max(i0, tk.r0), b1 = min(i1, tk.r1);
-        if (b0 < b1) {
-            for (int k0 = tk.r1; k0 < h; k0 += 16) {
-                for (int e = tid; e < 16 * 64; e += 256) {
-                    const int kk = e & 15, r = e >> 4;   // consecutive threads: consecutive j
-                    const int i = i0 + r, j = k0 + kk;
-                    As[kk][r] = (i >= b0 && i < b1 && j < h)
-                                    ? Zq[rmap[j] + (int64_t)(srow[i] - fq) * hq] : 0.0;
-                }
-                load_b(k0, h);
-                __syncthreads();
-                fma_chunk();
-                __syncthreads();
-            }
-        }
+        __syncthreads();
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -112,14 +99,15 @@ __device__ __forceinline__ void selinv_off_tile(const DevPlan &p, int pid, int w
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int c = ty + 16 * b;
-            if (c < w) Z[base + i + (int64_t)c * h] = -acc[a][b];
+            if (c >= w) continue;
+            if (nsplit == 1) Z[base + i + (int64_t)c * h] = -acc[a][b];
+            else atomicAdd(&Z[base + i + (int64_t)c * h], -acc[a][b]);
         }
     }
 }
 
 __global__ void __launch_bounds__(256) selinv_off_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
-                                                         const int32_t *__restrict__ task_ptr,
-                                                         const int32_t *__restrict__ task_idx,
+                                                         const int32_t *__restrict__ row_task,
                                                          const DevTask *__restrict__ tasks,
                                                          const double *__restrict__ Lh,
                                                          double *__restrict__ Z)
@@ -130,14 +118,16 @@ __global__ void __launch_bounds__(256) selinv_off_kernel(DevPlan p, const RowChu
     const int pid = ch.panel;
     const int w = p.pw[pid], h = p.ph[pid];
     const int i0 = ch.r0, i1 = min(h, ch.r0 + 64);
-    if (w <= 16) selinv_off_tile<16>(p, pid, w, h, i0, i1, task_ptr, task_idx, tasks, Lh, Z, As, Bs);
-    else if (w <= 32) selinv_off_tile<32>(p, pid, w, h, i0, i1, task_ptr, task_idx, tasks, Lh, Z, As, Bs);
-    else selinv_off_tile<64>(p, pid, w, h, i0, i1, task_ptr, task_idx, tasks, Lh, Z, As, Bs);
+    const int sp = blockIdx.y, ns = gridDim.y;
+    if (w <= 16) selinv_off_tile<16>(p, pid, w, h, i0, i1, row_task, tasks, Lh, Z, As, Bs, sp, ns);
+    else if (w <= 32) selinv_off_tile<32>(p, pid, w, h, i0, i1, row_task, tasks, Lh, Z, As, Bs, sp, ns);
+    else selinv_off_tile<64>(p, pid, w, h, i0, i1, row_task, tasks, Lh, Z, As, Bs, sp, ns);
 }
 
 // ---------------------------------------------------------------------------
 // Z_JJ = Linv^T Linv - Lh^T Z_RJ for one panel (w <= 64), lower pairs (a, b)
-// computed once and written to both triangles.
+// computed once and written to both triangles.  Split-K as above: gridDim.y
+// CTAs per panel take every gridDim.y-th chunk of 32 rows of R.
 // ---------------------------------------------------------------------------
 constexpr int kSelDiagPairs = 9;   // ceil(64 * 65 / 2 / 256)
 
@@ -155,6 +145,7 @@ __global__ void __launch_bounds__(256) selinv_diag_kernel(DevPlan p, const int32
     double *Zs = Ls + 32 * w;        // 32 x w: Z_RJ rows of the current chunk
     const double *Mi = Dinv + p.pinv[pid];
     const int tid = threadIdx.x;
+    const int sp = blockIdx.y, ns = gridDim.y;   // this CTA takes every ns-th chunk of 32 rows
     for (int e = tid; e < w * w; e += 256) Di[e] = Mi[e];
     const int npair = w * (w + 1) / 2;
     int pa[kSelDiagPairs], pb[kSelDiagPairs];
@@ -172,14 +163,14 @@ __global__ void __launch_bounds__(256) selinv_diag_kernel(DevPlan p, const int32
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kSelDiagPairs; ++q) {
-        if (tid + 256 * q >= npair) continue;
+        if (tid + 256 * q >= npair || sp != 0) continue;
         const int a = pa[q], b = pb[q];   // a >= b: Linv(k, a) Linv(k, b) is nonzero for k >= a
         double s = 0.0;
 #pragma unroll 1
         for (int k = a; k < w; ++k) s = fma(Di[k + a * w], Di[k + b * w], s);
         acc[q] = s;
     }
-    for (int c0 = w; c0 < h; c0 += 32) {
+    for (int c0 = w + 32 * sp; c0 < h; c0 += 32 * ns) {
         const int m = min(32, h - c0);
         __syncthreads();
         for (int e = tid; e < 32 * w; e += 256) {
@@ -206,21 +197,26 @@ __global__ void __launch_bounds__(256) selinv_diag_kernel(DevPlan p, const int32
     for (int q = 0; q < kSelDiagPairs; ++q) {
         if (tid + 256 * q >= npair) continue;
         const int a = pa[q], b = pb[q];
-        Z[base + a + (int64_t)b * h] = acc[q];
-        Z[base + b + (int64_t)a * h] = acc[q];
+        if (ns == 1) {
+            Z[base + a + (int64_t)b * h] = acc[q];
+            Z[base + b + (int64_t)a * h] = acc[q];
+        } else {   // partial sums over row chunks; Z starts zeroed
+            atomicAdd(&Z[base + a + (int64_t)b * h], acc[q]);
+            if (a != b) atomicAdd(&Z[base + b + (int64_t)a * h], acc[q]);
+        }
     }
 }
 
-void launch_selinv_off(const DevPlan &p, const RowChunk *chunks, int count, const int32_t *task_ptr,
-                       const int32_t *task_idx, const DevTask *tasks, const double *Lh, double *Z,
+void launch_selinv_off(const DevPlan &p, const RowChunk *chunks, int count, int nsplit,
+                       const int32_t *row_task, const DevTask *tasks, const double *Lh, double *Z,
                        cudaStream_t s)
 {
     if (count <= 0) return;
-    selinv_off_kernel<<<count, 256, 0, s>>>(p, chunks, task_ptr, task_idx, tasks, Lh, Z);
+    selinv_off_kernel<<<dim3(count, nsplit), 256, 0, s>>>(p, chunks, row_task, tasks, Lh, Z);
 }
 
-void launch_selinv_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const double *Dinv,
-                        const double *Lh, double *Z, cudaStream_t s)
+void launch_selinv_diag(const DevPlan &p, const int32_t *panels, int count, int nsplit, int wmax,
+                        const double *Dinv, const double *Lh, double *Z, cudaStream_t s)
 {
     if (count <= 0) return;
     const size_t smem = sizeof(double) * ((size_t)wmax * wmax + 64 * (size_t)wmax);
@@ -230,7 +226,7 @@ void launch_selinv_diag(const DevPlan &p, const int32_t *panels, int count, int 
                              (int)(sizeof(double) * (64 * 64 + 64 * 64)));
         once = true;
     }
-    selinv_diag_kernel<<<count, 256, smem, s>>>(p, panels, Dinv, Lh, Z);
+    selinv_diag_kernel<<<dim3(count, nsplit), 256, smem, s>>>(p, panels, Dinv, Lh, Z);
 }
 
 // ---------------------------------------------------------------------------
