@@ -16,7 +16,10 @@ Cholesky factor of the 1-D Laplacian, the closed-form spectrum of the 2-D
 algorithms, a hand-ordered nested dissection of small grids, a
 hand-computed static-pivot replacement, and for the selected inverse the
 dense inverse by brute force, the closed-form inverse of the 1-D Laplacian
-and trace(A Z) = n.
+and trace(A Z) = n; for LDL^T the reconstruction P A P^T = L D L^T by brute
+force, Sylvester's law of inertia against dense eigenvalues, the Cholesky
+factor as L sqrt(D) on SPD matrices, the closed-form LDL^T of the 1-D
+Laplacian and a hand-computed static-pivot replacement.
 """
 from __future__ import annotations
 
@@ -74,6 +77,11 @@ def _load():
         ]
         lib.ora_spmv.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p]
         lib.ora_selinv.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p]
+        lib.ora_ldlt.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _i64p, _i32p, ctypes.c_double,
+                                 _f64p, _i64p]
+        lib.ora_solve_ldlt.argtypes = [
+            ctypes.c_int64, _i64p, _i32p, _f64p, ctypes.c_int64, _f64p, ctypes.c_int64,
+        ]
         _lib = lib
     return _lib
 
@@ -202,10 +210,10 @@ class NotPositiveDefinite(ArithmeticError):
 
 @dataclass
 class Factor:
-    method: str              # "llt" or "lu"
+    method: str              # "llt", "lu" or "ldlt"
     perm: np.ndarray         # new -> old
     sym: Symbolic
-    Lx: np.ndarray           # L values in the pattern (LU: unit diagonal stored as 1)
+    Lx: np.ndarray           # L values in the pattern (LU: unit diagonal stored as 1; LDL^T: D on the diagonal)
     Ut: Optional[np.ndarray] = None   # LU: U transposed in L's pattern
     nrepl: int = 0           # LU: static pivot replacements
     tau: float = 0.0
@@ -267,6 +275,30 @@ def lu(A, perm: np.ndarray, tau: Optional[float] = None) -> Factor:
     return Factor("lu", perm, s, Lx, Ut, int(nrepl[0]), float(tau))
 
 
+def ldlt(A, perm: np.ndarray, tau: Optional[float] = None) -> Factor:
+    """P A P^T = L D L^T with static pivoting, unit L; Lx holds D on its diagonal."""
+    A = _csc(A)
+    perm = np.ascontiguousarray(perm, dtype=np.int64)
+    if tau is None:
+        tau = static_pivot_threshold(A)
+    Pa = permute(A, perm)
+    s = symbolic(symmetrized_pattern(Pa))
+    Ap, Ai, Ax = _arrays(Pa)
+    Lx = np.zeros(int(s.Lp[-1]), dtype=np.float64)
+    nrepl = np.zeros(1, dtype=np.int64)
+    rc = _load().ora_ldlt(s.n, _p(Ap, _i64p), _p(Ai, _i32p), _p(Ax, _f64p), _p(s.Lp, _i64p),
+                          _p(s.Li, _i32p), float(tau), _p(Lx, _f64p), _p(nrepl, _i64p))
+    if rc != 0:
+        raise ZeroDivisionError(f"zero pivot in column {-rc - 1}")
+    return Factor("ldlt", perm, s, Lx, None, int(nrepl[0]), float(tau))
+
+
+def inertia(F: Factor) -> tuple:
+    """(positive, negative) pivots of an LDL^T factor."""
+    d = F.Lx[F.sym.Lp[:-1]]
+    return int(np.sum(d > 0)), int(np.sum(d < 0))
+
+
 def solve(F: Factor, B: np.ndarray) -> np.ndarray:
     """x with A x = b, in the original numbering (B: n or n x nrhs)."""
     B = np.asarray(B, dtype=np.float64)
@@ -278,6 +310,10 @@ def solve(F: Factor, B: np.ndarray) -> np.ndarray:
     lib = _load()
     if F.method == "llt":
         lib.ora_solve_cholesky(
+            s.n, _p(s.Lp, _i64p), _p(s.Li, _i32p), _p(F.Lx, _f64p), nrhs, _p(X, _f64p), s.n
+        )
+    elif F.method == "ldlt":
+        lib.ora_solve_ldlt(
             s.n, _p(s.Lp, _i64p), _p(s.Li, _i32p), _p(F.Lx, _f64p), nrhs, _p(X, _f64p), s.n
         )
     else:

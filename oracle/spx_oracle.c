@@ -564,6 +564,83 @@ int ora_selinv(int64_t n, const int64_t *Lp, const int32_t *Li, const double *Lx
 }
 
 /* ------------------------------------------------------------------------ */
+/* Numerical LDL^T with static pivoting (the L D L^T variant of the
+ * factorization, Sec. V-B: the update becomes C = C - L D L^T).  Left-looking
+ * column j, on the lower pattern:
+ *   w = A(j:n, j);  for every k < j with L(j,k) != 0, in ascending k:
+ *   w(i) -= L(i,k) * d_k * L(j,k) for i >= j;
+ *   d_j = w(j), replaced by sign(d_j) * tau when |d_j| < tau (+tau for 0)
+ *   and counted; L(i,j) = w(i) / d_j for i > j.
+ * L is unit lower; the stored diagonal slot of Lx holds d_j.  With tau = 0 a
+ * zero pivot returns -(j+1).  Ap/Ai/Ax is the permuted matrix; only its
+ * lower triangle is read.                                                   */
+/* ------------------------------------------------------------------------ */
+
+int ora_ldlt(int64_t n, const int64_t *Ap, const int32_t *Ai, const double *Ax, const int64_t *Lp,
+             const int32_t *Li, double tau, double *Lx, int64_t *nrepl)
+{
+    int64_t *Rp;
+    int32_t *Rk;
+    ora_row_lists(n, Lp, Li, &Rp, &Rk);
+    double *w = (double *)calloc((size_t)(n + 1), sizeof(double));
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int rc = 0;
+    *nrepl = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p)
+            if (Ai[p] >= j) w[Ai[p]] += Ax[p];
+        for (int64_t r = Rp[j]; r < Rp[j + 1]; ++r) {
+            int64_t k = Rk[r];
+            int64_t p = next[k];           /* position of row j in column k */
+            double f = Lx[Lp[k]] * Lx[p];  /* d_k L(j,k) */
+            for (int64_t q = p; q < Lp[k + 1]; ++q) w[Li[q]] -= Lx[q] * f;
+            next[k] = p + 1;
+        }
+        double d = w[j];
+        if (tau > 0.0) {
+            if (fabs(d) < tau) {
+                d = d < 0.0 ? -tau : tau;
+                (*nrepl)++;
+            }
+        } else if (d == 0.0) {
+            rc = (int)-(j + 1);
+            break;
+        }
+        Lx[Lp[j]] = d;
+        w[j] = 0.0;
+        for (int64_t p = Lp[j] + 1; p < Lp[j + 1]; ++p) {
+            Lx[p] = w[Li[p]] / d;
+            w[Li[p]] = 0.0;
+        }
+        next[j] = Lp[j] + 1;
+    }
+    free(next);
+    free(w);
+    free(Rk);
+    free(Rp);
+    return rc;
+}
+
+/* L D L^T x = b: forward substitution with the unit L, division by D,
+ * backward substitution with L^T; in place, permuted numbering.            */
+int ora_solve_ldlt(int64_t n, const int64_t *Lp, const int32_t *Li, const double *Lx, int64_t nrhs,
+                   double *X, int64_t ldx)
+{
+    for (int64_t c = 0; c < nrhs; ++c) {
+        double *x = X + c * ldx;
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t p = Lp[j] + 1; p < Lp[j + 1]; ++p) x[Li[p]] -= Lx[p] * x[j];
+        for (int64_t j = 0; j < n; ++j) x[j] /= Lx[Lp[j]];
+        for (int64_t j = n - 1; j >= 0; --j) {
+            double s = x[j];
+            for (int64_t p = Lp[j] + 1; p < Lp[j + 1]; ++p) s -= Lx[p] * x[Li[p]];
+            x[j] = s;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Triangular solves on the factors (forward then backward substitution), in
  * the permuted numbering, nrhs columns of leading dimension ldb, in place. */
 /* ------------------------------------------------------------------------ */

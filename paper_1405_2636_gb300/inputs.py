@@ -88,6 +88,24 @@ def diffusion_3d(nx: int, ny: int, nz: int, seed: int, sigma: float = 1.0) -> sp
     return _finish(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
 
 
+def quasi_definite_3d(nx: int, ny: int, nz: int, seed: int, shift: float = 0.1) -> sp.csc_matrix:
+    """Symmetric indefinite, quasi-definite: two unknowns per grid node (u, p),
+    [[K, B^T], [B, -C]] interleaved node by node (unknown 2 a is u_a, 2 a + 1
+    is p_a), K the 7-point diffusion operator of this seed, C = shift x the
+    diffusion operator of seed + 1, and B ~ U(-0.5, 0.5) on the 7-point
+    stencil.  Every symmetric ordering of it has an LDL^T factorization
+    without pivoting, with n/2 positive and n/2 negative pivots."""
+    K = diffusion_3d(nx, ny, nz, seed).tocoo()
+    C = diffusion_3d(nx, ny, nz, seed + 1).tocoo()
+    g = rng(seed, STREAM_EXTRA)
+    bvals = g.uniform(-0.5, 0.5, size=K.nnz)
+    n = 2 * nx * ny * nz
+    rows = np.concatenate([2 * K.row, 2 * C.row + 1, 2 * K.row + 1, 2 * K.col])
+    cols = np.concatenate([2 * K.col, 2 * C.col + 1, 2 * K.col, 2 * K.row + 1])
+    vals = np.concatenate([K.data, -shift * C.data, bvals, bvals])
+    return _finish(rows, cols, vals, n)
+
+
 def diffusion_3d_kappa(nx: int, ny: int, nz: int, seed: int, sigma: float = 1.0) -> np.ndarray:
     """The node coefficients exp(sigma g) that diffusion_3d draws for this seed."""
     return np.exp(sigma * rng(seed, STREAM_MATRIX).standard_normal(nx * ny * nz))
