@@ -373,6 +373,55 @@ def run_differentiation(torch, spx, inputs, steps: int) -> dict:
                       "CUDA events for the selected inverse"}
 
 
+def run_ldlt(torch, spx, inputs, steps: int) -> dict:
+    """Symmetric indefinite (quasi-definite) 40^3 x 2-dof system: LDL^T with
+    the C = C - L D L^T updates, FP64 against the mixed modes with refinement
+    to 1e-12, one right-hand side block of 16."""
+    dims = (40, 40, 40)
+    A = inputs.quasi_definite_3d(*dims, 7)
+    cp, ri, vals = inputs.csc_arrays(A)
+    n = A.shape[0]
+    B = inputs.rhs(n, NRHS, 7)
+    h = spx.analyze(cp, ri, "ldlt", ordering=spx.SPX_ORDER_GRID, grid=dims, dof=2, max_width=64)
+    flops = h.info()["flops"]
+    vd = torch.from_numpy(vals).cuda()
+    Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+    Xd = torch.empty((NRHS, n), dtype=torch.float64, device="cuda").t()
+    out = {}
+    for mode in ("fp64", "fp32", "tf32", "bf16"):
+        ref = None if mode == "fp64" else spx.default_refine(tol=TARGET_BERR)
+        times, fms, sms = [], [], []
+        for it in range(max(3, steps) + 1):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.factorize(vd, mode)
+            _, si = h.solve(Bd, Xd, refine=ref)
+            e1.record()
+            torch.cuda.synchronize()
+            if it > 0:
+                times.append(e0.elapsed_time(e1))
+                fms.append(h.info()["factor_ms"])
+                sms.append(h.info()["solve_ms"])
+        X = Xd.cpu().numpy()
+        R = B - A @ X
+        den = abs(A).sum(axis=1).max() * np.abs(X).max(axis=0) + np.abs(B).max(axis=0)
+        info = h.info()
+        out[mode] = {"ms_per_step": statistics.median(times), "factor_ms": statistics.median(fms),
+                     "solve_ms": statistics.median(sms),
+                     "time_to_solve_gflops": flops / (statistics.median(times) / 1e3) / 1e9,
+                     "host_backward_error": float(np.max(np.abs(R).max(axis=0) / den)),
+                     "refine_iters": si["iters"], "negative_pivots": info["npivot_neg"],
+                     "pivot_replacements": info["npivot_repl"]}
+    h.free()
+    return {"workload": "quasi-definite [[K, B^T], [B, -C]] 40^3 x 2 dof, 16 rhs, LDL^T",
+            "n": n, "nnz_a": int(cp[-1]), "flops_exact": flops,
+            "target_backward_error": TARGET_BERR, "modes": out,
+            "speedup_best_mixed_over_fp64": out["fp64"]["ms_per_step"] /
+            min(out[m]["ms_per_step"] for m in ("fp32", "tf32", "bf16"))}
+
+
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
@@ -516,6 +565,7 @@ def main():
     if not args.no_extra:
         extra["batched_lu"] = run_batched(torch, spx, inputs, args.steps)
         extra["differentiation"] = run_differentiation(torch, spx, inputs, args.steps)
+        extra["ldlt"] = run_ldlt(torch, spx, inputs, args.steps)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_rate((32, 32, 32), 8.0)

@@ -49,7 +49,11 @@ typedef enum {
     SPX_ERR_STATE = 8           /* call out of order (e.g. solve before factorize) */
 } spx_status;
 
-typedef enum { SPX_LLT = 0, SPX_LU = 1 } spx_method;
+/* SPX_LLT: Cholesky (SPD).  SPX_LU: static-pivot LU on the pattern of
+ * A + A^T.  SPX_LDLT: symmetric indefinite L D L^T with static pivoting, unit
+ * L; its updates compute C = C - L D L^T (Sec. V-B) from a stored D L^T
+ * operand; panels at most 64 wide (max_width is clamped to 64). */
+typedef enum { SPX_LLT = 0, SPX_LU = 1, SPX_LDLT = 2 } spx_method;
 
 /* Arithmetic of the bulk panel updates.  SPX_FP64 stores and updates the
  * factor in double precision.  The other modes store the factor in single
@@ -121,6 +125,8 @@ typedef struct {
     double analyze_ms;      /* host time of spx_analyze */
     double factor_ms;       /* device time of the last spx_factorize (assembly included) */
     double solve_ms;        /* device time of the last spx_solve */
+    int64_t npivot_neg;     /* LDL^T: negative pivots of the last factorization (the inertia, when
+                               no pivot was replaced) */
 } spx_info;
 
 /* Host-only analysis (Sec. III: ordering, elimination tree, symbolic

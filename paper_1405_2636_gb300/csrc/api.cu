@@ -72,6 +72,8 @@ struct spx_handle_s {
     int precision = -1;
     bool factored = false;
     void *d_L = nullptr, *d_U = nullptr, *d_Dinv = nullptr;
+    void *d_W = nullptr;                     // LDL^T: the D L^T rows (the update's B operand)
+    unsigned long long *d_nneg = nullptr;    // LDL^T: negative pivots
     int factor_prec_alloc = -1;
     double *d_vals = nullptr;
     double *d_tau = nullptr;                 // [0] pivot threshold used by the diagonal kernels
@@ -279,7 +281,7 @@ spx_status ensure_device(spx_handle h)
             const int32_t hk = P.ph[tk.src];
             for (int32_t m0 = tk.r0; m0 < hk; m0 += T)
                 for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += T) {
-                    if (P.method == SPX_LLT && m0 + T <= n0) continue;
+                    if (P.method != SPX_LU && m0 + T <= n0) continue;
                     tiles.push_back(UpdTile{t, m0, n0, 0});
                 }
             if (P.method == SPX_LU)
@@ -293,7 +295,7 @@ spx_status ensure_device(spx_handle h)
     if ((st = upload(h, &h->d_chunks, chunks)) || (st = upload(h, &h->d_tiles, tiles)) ||
         (st = upload(h, &h->d_tilesu, tilesu)))
         return st;
-    if (P.method == SPX_LLT) {
+    if (P.method != SPX_LU) {
         std::vector<UpdTile> small;
         std::vector<spx::TcTile> tct;
         h->tcsmall_ptr.assign(P.nlevels + 1, 0);
@@ -333,6 +335,7 @@ spx_status ensure_device(spx_handle h)
         h->op_rows = P.prow[P.npanels];
     }
     if ((st = dalloc(h, &h->d_tcerr, 1))) return st;
+    if ((st = dalloc(h, &h->d_nneg, 1))) return st;
     if ((st = dalloc(h, &h->d_vals, (size_t)P.nnz_a)) || (st = dalloc(h, &h->d_tau, 1)) ||
         (st = dalloc(h, &h->d_anorm, 1)) || (st = dalloc(h, &h->d_err, 1)) ||
         (st = dalloc(h, &h->d_nrepl, 1)))
@@ -362,6 +365,23 @@ struct Marks {
     }
 };
 
+// Which symmetric factorizations send their wide updates to the tensor
+// cores, and in which operand form (see launch_update_tc): Cholesky in TF32,
+// BF16 or split TF32 (FP32 mode); LDL^T in TF32 or BF16 with a separate
+// D L^T operand (its FP32 mode stays on the CUDA cores).
+bool uses_tensor_cores(int method, int prec)
+{
+    if (method == SPX_LU) return false;
+    if (method == SPX_LDLT) return prec == SPX_TF32 || prec == SPX_BF16;
+    return prec == SPX_TF32 || prec == SPX_BF16 || prec == SPX_FP32;
+}
+
+int operand_kind(int method, int prec)
+{
+    if (method == SPX_LDLT) return prec == SPX_BF16 ? 4 : 3;
+    return prec == SPX_BF16 ? 1 : (prec == SPX_FP32 ? 2 : 0);
+}
+
 template <typename T>
 void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
 {
@@ -370,17 +390,20 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
     T *L = (T *)h->d_L, *U = (T *)h->d_U, *Dinv = (T *)h->d_Dinv;
     const size_t elems = (size_t)P.pval[P.npanels];
     const bool lu = P.method == SPX_LU;
-    const bool tc = !lu && (prec == SPX_TF32 || prec == SPX_BF16 || prec == SPX_FP32) && sizeof(T) == 4;
+    const bool ldlt = P.method == SPX_LDLT;
+    const bool tc = uses_tensor_cores(P.method, prec) && sizeof(T) == 4;
     void *opc = tc ? h->d_opc : nullptr;
     void *opc_lo = tc ? h->d_opc_lo : nullptr;
-    const int op_kind = prec == SPX_BF16 ? 1 : (prec == SPX_FP32 ? 2 : 0);
+    const int op_kind = operand_kind(P.method, prec);
+    T *W = (T *)h->d_W;
     int64_t &cnt = h->cnt;
     mk.mark(-1);
     init_scalars_kernel<<<1, 1, 0, s>>>(h->d_err, h->d_nrepl, h->d_anorm);
     cudaMemsetAsync(h->d_tcerr, 0, sizeof(int), s);
+    cudaMemsetAsync(h->d_nneg, 0, sizeof(unsigned long long), s);
     spx::launch_row_abs_sum_max(P.n, h->d_csr_ptr, h->d_csr_src, h->d_vals, h->d_anorm, s);
     const double sqrt_eps = std::sqrt(std::ldexp(1.0, -52));
-    if (lu)
+    if (lu || ldlt)
         set_tau_kernel<<<1, 1, 0, s>>>(h->d_anorm, h->pivot_tau_opt, sqrt_eps, h->d_tau);
     else
         set_tau_kernel<<<1, 1, 0, s>>>(h->d_anorm, mixed ? -1.0 : 0.0, sqrt_eps, h->d_tau);
@@ -403,7 +426,10 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
             const int32_t b = h->cls_ptr[(size_t)l * kNumClasses + c + 1];
             if (b <= a) continue;
             const int cw = std::min(kClassWidth[c], wmax);
-            if (!lu)
+            if (ldlt)
+                spx::launch_ldlt_diag<T>(h->dp, h->d_level_panels + a, b - a, cw, L, Dinv, h->d_tau, h->d_err,
+                                         h->d_nrepl, h->d_nneg, s);
+            else if (!lu)
                 spx::launch_potrf<T>(h->dp, h->d_level_panels + a, b - a, cw, kClassThreads[c], L,
                                      Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
             else
@@ -415,11 +441,13 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
         (void)np;
         mk.mark(SPX_K_DIAG);
         if (!lu) {
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LLT, opc, opc_lo, h->kpad, op_kind, s);
+            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, ldlt ? spx::TRSM_LDLT : spx::TRSM_LLT, opc, opc_lo,
+                                h->kpad, op_kind, s, W);
             cnt += nch > 0;
             mk.mark(SPX_K_TRSM);
+            const T *Bop = ldlt ? W : L;   // LDL^T: C -= L (D L^T)
             if (!tc) {
-                spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, L, L, 1, 0, s);
+                spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, Bop, L, 1, 0, s);
                 cnt += ntl > 0;
                 mk.mark(SPX_K_UPDATE);
             } else {
@@ -427,7 +455,7 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
                 const int nts = (int)(h->tcsmall_ptr[l + 1] - h->tcsmall_ptr[l]);
                 const spx::TcTile *tt = h->d_tctiles + h->tctile_ptr[l];
                 const int ntt = (int)(h->tctile_ptr[l + 1] - h->tctile_ptr[l]);
-                spx::launch_update<T>(h->dp, h->d_tasks, ts, nts, L, L, L, 1, 0, s);
+                spx::launch_update<T>(h->dp, h->d_tasks, ts, nts, L, Bop, L, 1, 0, s);
                 mk.mark(SPX_K_UPDATE);
                 spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, tt, ntt,
                                       (float *)L, 1, h->d_tcerr, s);
@@ -467,7 +495,7 @@ void enqueue_sweep(spx_handle h, int nrhs)
         const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
         const int wmax = h->lvl_wmax[l];
-        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Y, Z, nrhs, s);
+        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, P.method != SPX_LLT ? 1 : 0, Y, Z, nrhs, s);
         spx::launch_fwd_off<T>(h->dp, ch, nch, wmax, L, Z, Y, nrhs, s);
         k += (np > 0) + (nch > 0);
     }
@@ -478,7 +506,8 @@ void enqueue_sweep(spx_handle h, int nrhs)
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
         const int wmax = h->lvl_wmax[l];
         spx::launch_bwd_off<T>(h->dp, ch, nch, wmax, lu ? U : L, Xs, Tacc, nrhs, s);
-        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Z, Tacc, Xs, nrhs, s);
+        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : (P.method == SPX_LDLT ? 2 : 0), Z, Tacc,
+                                Xs, nrhs, s);
         k += (np > 0) + (nch > 0);
     }
     spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, h->d_D, P.n, s);
@@ -523,10 +552,10 @@ spx_status ensure_operand_copy(spx_handle h, int kind)
     dfree(h, h->d_opc_lo);
     h->d_opc = h->d_opc_lo = nullptr;
     h->opc_kind = -1;
-    const int bf16 = kind == 1;
+    const int bf16 = kind == 1 || kind == 4;
     const size_t esz = bf16 ? 2 : 4;
     const size_t bytes = (size_t)h->op_rows * h->kpad * esz;
-    for (int part = 0; part < (kind == 2 ? 2 : 1); ++part) {
+    for (int part = 0; part < (kind >= 2 ? 2 : 1); ++part) {
         char *p = nullptr;
         spx_status st = dalloc(h, &p, bytes);
         if (st != SPX_OK) return st;
@@ -659,7 +688,7 @@ void enqueue_sweep_noalloc(spx_handle h, int nrhs, const double *B, int64_t ldb,
         const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
         const int wmax = h->lvl_wmax[l];
-        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Y, Z, nrhs, s);
+        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, P.method != SPX_LLT ? 1 : 0, Y, Z, nrhs, s);
         spx::launch_fwd_off<T>(h->dp, ch, nch, wmax, L, Z, Y, nrhs, s);
     }
     for (int32_t l = P.nlevels - 1; l >= 0; --l) {
@@ -669,7 +698,8 @@ void enqueue_sweep_noalloc(spx_handle h, int nrhs, const double *B, int64_t ldb,
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
         const int wmax = h->lvl_wmax[l];
         spx::launch_bwd_off<T>(h->dp, ch, nch, wmax, lu ? U : L, Xs, Tacc, nrhs, s);
-        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : 0, Z, Tacc, Xs, nrhs, s);
+        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : (P.method == SPX_LDLT ? 2 : 0), Z, Tacc,
+                                Xs, nrhs, s);
     }
     spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, X, ldx, s);
 }
@@ -829,15 +859,16 @@ spx_status spx_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, 
     if (!out) return fail(h, SPX_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!colptr || !rowind) return fail(h, SPX_ERR_ARG, "colptr/rowind is NULL");
-    if (method != SPX_LLT && method != SPX_LU) return fail(h, SPX_ERR_ARG, "unknown method");
+    if (method != SPX_LLT && method != SPX_LU && method != SPX_LDLT) return fail(h, SPX_ERR_ARG, "unknown method");
     spx_options o;
     spx_default_options(&o);
     if (opt) o = *opt;
     if (o.max_width <= 0) o.max_width = 128;
+    if (method == SPX_LDLT && o.max_width > 64) o.max_width = 64;   // the LDL^T diagonal kernel
     if (o.max_width > spx::kMaxWidth)
         return fail(h, SPX_ERR_ARG, "max_width above " + std::to_string(spx::kMaxWidth));
     if (o.amalg_ratio < 0) o.amalg_ratio = 0.12;
-    if (o.lower_only && method == SPX_LU) return fail(h, SPX_ERR_ARG, "lower_only needs SPX_LLT");
+    if (o.lower_only && method == SPX_LU) return fail(h, SPX_ERR_ARG, "lower_only needs a symmetric method");
     h = new (std::nothrow) spx_handle_s();
     if (!h) return fail(nullptr, SPX_ERR_ALLOC, "out of host memory");
     spx::AnalyzeOptions ao;
@@ -852,7 +883,9 @@ spx_status spx_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, 
     ao.lower_only = o.lower_only;
     std::string msg;
     try {
-        msg = spx::analyze(n, colptr, rowind, (int)method, ao, h->plan);
+        // LDL^T has the symbolic structure of the Cholesky factorization
+        msg = spx::analyze(n, colptr, rowind, method == SPX_LU ? (int)SPX_LU : (int)SPX_LLT, ao, h->plan);
+        h->plan.method = method;
     } catch (const std::bad_alloc &) {
         msg = "out of host memory during analysis";
     }
@@ -906,6 +939,13 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         h->d_L = pl;
         if ((st = dalloc(h, &pd, (size_t)h->dinv_elems * esz))) return st;
         h->d_Dinv = pd;
+        dfree(h, h->d_W);
+        h->d_W = nullptr;
+        if (P.method == SPX_LDLT) {
+            char *pw = nullptr;
+            if ((st = dalloc(h, &pw, elems * esz))) return st;
+            h->d_W = pw;
+        }
         if (P.method == SPX_LU) {
             char *pu = nullptr;
             if ((st = dalloc(h, &pu, elems * esz))) return st;
@@ -920,9 +960,8 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     }
     h->factored = false;
     h->zready = false;
-    if (P.method == SPX_LLT && precision != SPX_FP64) {
-        if ((st = ensure_operand_copy(h, precision == SPX_BF16 ? 1 : (precision == SPX_FP32 ? 2 : 0))))
-            return st;
+    if (uses_tensor_cores(P.method, precision)) {
+        if ((st = ensure_operand_copy(h, operand_kind(P.method, precision)))) return st;
     }
     fence_from(h, cuda_stream);
     CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a,
@@ -953,7 +992,9 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     CU(cudaMemcpyAsync(&nrepl, h->d_nrepl, sizeof(nrepl), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaMemcpyAsync(&abits, h->d_anorm, sizeof(abits), cudaMemcpyDeviceToHost, h->hs));
     int tcerr = 0;
+    unsigned long long nneg = 0;
     CU(cudaMemcpyAsync(&tcerr, h->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&nneg, h->d_nneg, sizeof(nneg), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaStreamSynchronize(h->hs));
     if (tcerr) return fail(h, SPX_ERR_TIMEOUT, "a tensor-core update tile gave up waiting on its pipeline");
     float ms = 0.f;
@@ -968,8 +1009,9 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         }
         const double e = fp64 ? 8.0 : 4.0;
         const double nfac = (P.method == SPX_LU) ? 2.0 : 1.0;
-        const bool tcm = P.method == SPX_LLT && precision != SPX_FP64;
+        const bool tcm = uses_tensor_cores(P.method, precision);
         const double eop = precision == SPX_BF16 ? 2.0 : (precision == SPX_FP32 ? 8.0 : 4.0);
+        // (LDL^T reads its B operand from a second copy of the same size: the bytes are the same)
         K.flops[SPX_K_DIAG] = P.diag_flops;
         K.flops[SPX_K_TRSM] = P.trsm_flops;
         K.flops[SPX_K_UPDATE] = P.update_flops - (tcm ? h->upd_flops_tc : 0.0);
@@ -999,8 +1041,9 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     h->info.factor_ms = ms;
     h->info.precision = precision;
     h->info.npivot_repl = (int64_t)nrepl;
+    h->info.npivot_neg = P.method == SPX_LDLT ? (int64_t)nneg : 0;
     h->info.bad_col = (bad == LLONG_MAX) ? -1 : bad;
-    h->info.factor_bytes = (int64_t)(elems * esz * (P.method == SPX_LU ? 2 : 1));
+    h->info.factor_bytes = (int64_t)(elems * esz * (P.method == SPX_LLT ? 1 : 2));
     h->precision = precision;
     if (bad != LLONG_MAX) {
         return fail(h, P.method == SPX_LLT ? SPX_ERR_NOT_SPD : SPX_ERR_ZERO_PIVOT,

@@ -453,7 +453,8 @@ template <typename T, int W>
 __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t *__restrict__ panels,
                                                         T *__restrict__ L, T *__restrict__ Dinv,
                                                         const double *replace_tau_p,
-                                                        int64_t *err_col, unsigned long long *nrepl)
+                                                        int64_t *err_col, unsigned long long *nrepl,
+                                                        int ldlt, unsigned long long *nneg)
 {
     constexpr int LD = W + 1;
     constexpr int NT = 256, NW = NT / 32;
@@ -501,12 +502,23 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
         for (int c = 0; c < kDB; ++c) {
             const int k = kb + c;
             double d = shfl_d(p0[c], c);                 // A(k, k) from lane c
-            if (!(d > 0.0)) {
-                if (lane == 0 && k < w) {
-                    if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
-                    else atomicMin((long long *)err_col, (long long)(col0 + k));
+            if (!ldlt) {                                  // Cholesky: positive pivots
+                if (!(d > 0.0)) {
+                    if (lane == 0 && k < w) {
+                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                        else atomicMin((long long *)err_col, (long long)(col0 + k));
+                    }
+                    d = replace_tau > 0.0 ? replace_tau : 1.0;
                 }
-                d = replace_tau > 0.0 ? replace_tau : 1.0;
+            } else {                                      // LDL^T: static pivoting
+                if (!(fabs(d) >= replace_tau) || (replace_tau <= 0.0 && d == 0.0)) {
+                    if (lane == 0 && k < w) {
+                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                        else atomicMin((long long *)err_col, (long long)(col0 + k));
+                    }
+                    d = replace_tau > 0.0 ? (d < 0.0 ? -replace_tau : replace_tau) : 1.0;
+                }
+                if (lane == 0 && k < w && d < 0.0) atomicAdd(nneg, 1ull);
             }
             const double r = rcp_newton(d);
             const double u0 = r0 > k ? p0[c] : 0.0;
@@ -572,18 +584,24 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
         }
     }
 
-    // L = l diag(sqrt(d)); keep 1/sqrt(d) for the inverse
+    // Cholesky: L = l diag(sqrt(d)), keep 1/sqrt(d) for the inverse.
+    // LDL^T: store l (unit) with d on the diagonal, keep 1/d.
     if (tid < W) {
-        double sq, rs;
-        sqrt_rsqrt(dv[tid], &sq, &rs);
-        dv[tid] = sq;
-        rsv[tid] = rs;
+        if (ldlt) {
+            rsv[tid] = rcp_newton(dv[tid]);
+        } else {
+            double sq, rs;
+            sqrt_rsqrt(dv[tid], &sq, &rs);
+            dv[tid] = sq;
+            rsv[tid] = rs;
+        }
     }
     __syncthreads();
     for (int idx = tid; idx < W * W; idx += NT) {
         const int i = idx % W, j = idx / W;
         const T l = (T)a[i + j * LD];
-        if (i < w && j < w && i >= j) D[i + (int64_t)j * h] = i == j ? (T)dv[j] : l * (T)dv[j];
+        if (i < w && j < w && i >= j)
+            D[i + (int64_t)j * h] = i == j ? (T)dv[j] : (ldlt ? l : l * (T)dv[j]);
         x[i + j * LD] = i > j ? l : (i == j ? (T)1 : (T)0);
     }
     __syncthreads();
@@ -627,10 +645,13 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
         }
         __syncthreads();
     }
+    // Cholesky: L^{-1} = diag(1/sqrt(d)) l^{-1}.  LDL^T: l^{-1} below the
+    // diagonal (unit), 1/d on it.
     T *Mi = Dinv + p.pinv[pid];
     for (int idx = tid; idx < w * w; idx += NT) {
         const int i = idx % w, j = idx / w;
-        Mi[idx] = i >= j ? x[i + j * LD] * (T)rsv[i] : (T)0;
+        if (ldlt) Mi[idx] = i > j ? x[i + j * LD] : (i == j ? (T)rsv[i] : (T)0);
+        else Mi[idx] = i >= j ? x[i + j * LD] * (T)rsv[i] : (T)0;
     }
 }
 
@@ -643,7 +664,8 @@ constexpr size_t ldl_smem_bytes()
 
 template <typename T, int W>
 void launch_ldl(const DevPlan &p, const int32_t *panels, int count, T *L, T *Dinv,
-                const double *replace_tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s)
+                const double *replace_tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s,
+                int ldlt = 0, unsigned long long *nneg = nullptr)
 {
     static bool once = false;
     const size_t smem = ldl_smem_bytes<T, W>();
@@ -651,7 +673,22 @@ void launch_ldl(const DevPlan &p, const int32_t *panels, int count, T *L, T *Din
         cudaFuncSetAttribute(potrf_ldl_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         once = true;
     }
-    potrf_ldl_kernel<T, W><<<count, 256, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl);
+    potrf_ldl_kernel<T, W><<<count, 256, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl, ldlt,
+                                                    nneg);
+}
+
+// LDL^T diagonal blocks (panels at most 64 wide): l with d on the diagonal,
+// l^{-1} with 1/d on its diagonal at Dinv; static pivoting with threshold
+// *tau (<= 0: a zero pivot is an error); negative pivots counted in *nneg.
+template <typename T>
+void launch_ldlt_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+                      const double *tau, int64_t *err_col, unsigned long long *nrepl,
+                      unsigned long long *nneg, cudaStream_t s)
+{
+    if (count <= 0) return;
+    if (wmax <= 16) return launch_ldl<T, 16>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, 1, nneg);
+    if (wmax <= 32) return launch_ldl<T, 32>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, 1, nneg);
+    launch_ldl<T, 64>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, 1, nneg);
 }
 
 template <typename T>
@@ -774,7 +811,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                         const T *__restrict__ Dinv,
                                                         T *__restrict__ X, int mode, void *opc,
-                                                        void *opc_lo, int kpad, int op_kind)
+                                                        void *opc_lo, int kpad, int op_kind,
+                                                        T *__restrict__ Wout)
 {
     extern __shared__ unsigned char smraw[];
     T *Xs = reinterpret_cast<T *>(smraw);      // Xs[k * 64 + r], k < wpad
@@ -809,7 +847,7 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                     if (mode == TRSM_RIGHT_LINV) v = (k >= j) ? Mi[k + j * w] : (T)0;
                     else if (mode == TRSM_LU_L) v = (k <= j) ? Mi[k + j * w] : (T)0;
                     else if (j > k) v = Mi[j + k * w];
-                    else if (j == k) v = (mode == TRSM_LU_U) ? (T)1 : Mi[j + k * w];
+                    else if (j == k) v = (mode == TRSM_LU_U || mode == TRSM_LDLT) ? (T)1 : Mi[j + k * w];
                 }
                 Bs[kk][jj] = v;
             }
@@ -827,6 +865,35 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                     for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
             }
             __syncthreads();
+        }
+        if (mode == TRSM_LDLT) {
+            // acc = X l^{-T} is the D L^T buffer row (Sec. V-B: the update then
+            // multiplies L by it); L = acc D^{-1} goes back in place
+            T *Wg = Wout + p.pval[pid] + ch.r0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int j = c0 + ty + 16 * b;
+                const T dinv = j < w ? Mi[j + j * w] : (T)0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int r = tx + 16 * a;
+                    if (r >= nr || j >= w) continue;
+                    Wg[r + (int64_t)j * h] = acc[a][b];
+                    const T l = acc[a][b] * dinv;
+                    Xg[r + (int64_t)j * h] = l;
+                    if (opc) {   // A operand: L; B operand: D L^T
+                        const int64_t o = (p.prow[pid] + ch.r0 + r) * kpad + j;
+                        if (op_kind == 4) {
+                            reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16((float)l);
+                            reinterpret_cast<__nv_bfloat16 *>(opc_lo)[o] = __float2bfloat16((float)acc[a][b]);
+                        } else {
+                            reinterpret_cast<float *>(opc)[o] = round_tf32((float)l);
+                            reinterpret_cast<float *>(opc_lo)[o] = round_tf32((float)acc[a][b]);
+                        }
+                    }
+                }
+            }
+            continue;
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -868,11 +935,12 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
         for (int e = tid; e < nr * padw; e += 256) {
             const int r = e / padw, j = w + e % padw;
             const int64_t o = (orow0 + r) * kpad + j;
-            if (op_kind == 1) {
+            if (op_kind == 1 || op_kind == 4) {
                 reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(0.0f);
+                if (op_kind == 4) reinterpret_cast<__nv_bfloat16 *>(opc_lo)[o] = __float2bfloat16(0.0f);
             } else {
                 reinterpret_cast<float *>(opc)[o] = 0.0f;
-                if (op_kind == 2) reinterpret_cast<float *>(opc_lo)[o] = 0.0f;
+                if (op_kind == 2 || op_kind == 3) reinterpret_cast<float *>(opc_lo)[o] = 0.0f;
             }
         }
     }
@@ -880,7 +948,7 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
 
 template <typename T>
 void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
-                 T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s)
+                 T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s, T *Wout)
 {
     if (count <= 0) return;
     static bool once = false;
@@ -890,7 +958,7 @@ void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, 
         once = true;
     }
     const size_t smem = sizeof(T) * (size_t)((wmax + 15) & ~15) * kTrsmRows;
-    trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, opc_lo, kpad, op_kind);
+    trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, opc_lo, kpad, op_kind, Wout);
 }
 
 // ---------------------------------------------------------------------------
@@ -1062,8 +1130,10 @@ template void launch_potrf<double>(const DevPlan &, const int32_t *, int, int, i
 template void launch_potrf<float>(const DevPlan &, const int32_t *, int, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
 template void launch_getrf<double>(const DevPlan &, const int32_t *, int, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
 template void launch_getrf<float>(const DevPlan &, const int32_t *, int, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
-template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, void *, void *, int, int, cudaStream_t);
-template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, void *, void *, int, int, cudaStream_t);
+template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, void *, void *, int, int, cudaStream_t, double *);
+template void launch_ldlt_diag<double>(const DevPlan &, const int32_t *, int, int, double *, double *, const double *, int64_t *, unsigned long long *, unsigned long long *, cudaStream_t);
+template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, void *, void *, int, int, cudaStream_t, float *);
+template void launch_ldlt_diag<float>(const DevPlan &, const int32_t *, int, int, float *, float *, const double *, int64_t *, unsigned long long *, unsigned long long *, cudaStream_t);
 template void launch_update<double>(const DevPlan &, const DevTask *, const UpdTile *, int, const double *, const double *, double *, int, int, cudaStream_t);
 template void launch_update<float>(const DevPlan &, const DevTask *, const UpdTile *, int, const float *, const float *, float *, int, int, cudaStream_t);
 

@@ -51,7 +51,8 @@ enum TrsmMode : int {
     TRSM_LLT = 0,        // X <- X L^{-T}, L = lower(D)            (Cholesky)
     TRSM_LU_L = 1,       // X <- X U^{-1}, U = upper(D)            (LU, L panel)
     TRSM_LU_U = 2,       // X <- X L^{-T}, L = unit lower(D)       (LU, U^T panel)
-    TRSM_RIGHT_LINV = 3  // X <- X L^{-1}, L = lower(D)            (selected inversion)
+    TRSM_RIGHT_LINV = 3, // X <- X L^{-1}, L = lower(D)            (selected inversion)
+    TRSM_LDLT = 4        // W = X l^{-T} (unit l) to Wout, X <- W D^{-1}   (LDL^T)
 };
 
 // ---- factorization -------------------------------------------------------
@@ -71,9 +72,20 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
 // opc (may be null): K-major operand copy for the tensor-core updates, rows
 // at prow[panel] + r with kpad elements each.  op_kind 0: TF32-rounded FP32;
 // 1: BF16; 2: split TF32, hi = tf32(x) in opc and lo = tf32(x - hi) in opc_lo.
+// op_kind 3 / 4 (LDL^T): TF32 / BF16 copies of L in opc and of D L^T in
+// opc_lo.  Wout: the D L^T rows in the factor's type (TRSM_LDLT only).
 template <typename T>
 void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
-                 T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s);
+                 T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s,
+                 T *Wout = nullptr);
+
+// LDL^T diagonal blocks, panels at most 64 wide (factor.cu): l with d on the
+// diagonal, l^{-1} with 1/d on its diagonal at Dinv; static pivoting with
+// threshold *tau; negative pivots counted in *nneg.
+template <typename T>
+void launch_ldlt_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, T *L, T *Dinv,
+                      const double *tau, int64_t *err_col, unsigned long long *nrepl,
+                      unsigned long long *nneg, cudaStream_t s);
 
 // Tensor-core update (update_tc.cu).  tmap / tmap_lo: CUtensorMaps over the
 // operand copies (make_operand_map; tmap_lo is used for kind 2 only); err

@@ -208,7 +208,9 @@ __global__ void __launch_bounds__(256) bwd_off_kernel(DevPlan p, const RowChunk 
 }
 
 // Backward, diagonal block: X_p = M (Z_p - Tacc_p) with M = Linv^T (Cholesky)
-// or U^{-1} (LU), rows [32 y, 32 y + 32) per CTA.
+// or U^{-1} (LU), rows [32 y, 32 y + 32) per CTA.  LDL^T (lu == 2):
+// X_p = l^{-T} (D^{-1} Z_p - Tacc_p), the unit l^{-1} below the diagonal of
+// Dinv and 1/d on it.
 template <typename T>
 __global__ void __launch_bounds__(256) bwd_diag_kernel(DevPlan p, const int32_t *__restrict__ panels,
                                                        const T *__restrict__ Dinv, int lu,
@@ -232,10 +234,10 @@ __global__ void __launch_bounds__(256) bwd_diag_kernel(DevPlan p, const int32_t 
     // M(i, k) for k >= i: Cholesky Linv(k, i) = Mi[k + i w]; LU Uinv(i, k) = Mi[i + k w]
     for (int e = tid; e < nrow * w; e += blockDim.x) {
         int a, k;
-        if (lu) { a = e % nrow; k = e / nrow; } else { k = e % w; a = e / w; }
+        if (lu == 1) { a = e % nrow; k = e / nrow; } else { k = e % w; a = e / w; }
         const int ii = i0 + a;
         T v = (T)0;
-        if (k >= ii) v = lu ? Mi[ii + k * w] : Mi[k + ii * w];
+        if (k >= ii) v = lu == 1 ? Mi[ii + k * w] : (lu == 2 && k == ii ? (T)1 : Mi[k + ii * w]);
         ms[a * (w + 1) + k] = v;
     }
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(256) bwd_diag_kernel(DevPlan p, const int32_t 
         for (int e = tid; e < w * nc; e += blockDim.x) {
             const int k = e % w, c = e / w;
             const int64_t g = f + k + (int64_t)(c0 + c) * n;
-            ys[c * w + k] = Z[g] - Tacc[g];
+            ys[c * w + k] = (lu == 2 ? Z[g] * Mi[k + k * w] : Z[g]) - Tacc[g];
         }
         __syncthreads();
         if (li < nrow) {

@@ -135,7 +135,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 }
 
 // KIND 0: TF32 operands (32 per 128-byte row chunk); KIND 1: BF16 (64);
-// KIND 2: split TF32 (hi and lo copies, three MMAs per K step).
+// KIND 2: split TF32 (hi and lo copies, three MMAs per K step);
+// KIND 3 / 4: TF32 / BF16 for LDL^T -- A rows from the L copy (opmap), B rows
+// from the D L^T copy (opmap_lo), so that the product is L D L^T (Sec. V-B).
 template <int KIND>
 __global__ void __launch_bounds__(128, 1)
     update_tc_kernel(const __grid_constant__ CUtensorMap opmap,
@@ -143,8 +145,10 @@ __global__ void __launch_bounds__(128, 1)
                      const DevTask *__restrict__ tasks, const TcTile *__restrict__ tiles,
                      float *__restrict__ C, int lower, int *err)
 {
-    constexpr int kElems = KIND == 1 ? 64 : 32;           // K elements per stage
-    constexpr uint32_t kIdesc = make_idesc(KIND == 1 ? 1u : 2u);
+    constexpr int kBase = KIND == 3 ? 0 : (KIND == 4 ? 1 : KIND);   // operand type of the MMA
+    constexpr bool kSepB = KIND >= 3;                      // B from the second copy
+    constexpr int kElems = kBase == 1 ? 64 : 32;           // K elements per stage
+    constexpr uint32_t kIdesc = make_idesc(kBase == 1 ? 1u : 2u);
     constexpr int kParts = KIND == 2 ? 2 : 1;              // hi (and lo) copies per operand
     constexpr uint32_t kStageTx = 2u * kParts * kTileBytes;
     extern __shared__ unsigned char smraw[];
@@ -192,10 +196,11 @@ __global__ void __launch_bounds__(128, 1)
         const int64_t rbase = p.prow[src];
         const int ya = (int)(rbase + tl.m0), yb = (int)(rbase + tl.n0);
         bool ok = true;
+        const CUtensorMap *mapb = kSepB ? &opmap_lo : &opmap;
         for (int kc = 0; kc < nk && kc < kStages; ++kc) {
             mbar_expect_tx(&full[kc], kStageTx);
             tma_load_2d(sA + kc * kTileBytes, &opmap, &full[kc], kc * kElems, ya);
-            tma_load_2d(sB + kc * kTileBytes, &opmap, &full[kc], kc * kElems, yb);
+            tma_load_2d(sB + kc * kTileBytes, mapb, &full[kc], kc * kElems, yb);
             if (KIND == 2) {
                 tma_load_2d(sAl + kc * kTileBytes, &opmap_lo, &full[kc], kc * kElems, ya);
                 tma_load_2d(sBl + kc * kTileBytes, &opmap_lo, &full[kc], kc * kElems, yb);
@@ -219,8 +224,8 @@ __global__ void __launch_bounds__(128, 1)
                     mma<0>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(bl + 32 * ks), kIdesc, 1u);
                     mma<0>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc, 1u);
                 } else {
-                    mma<KIND>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
-                              (kc > 0 || ks > 0) ? 1u : 0u);
+                    mma<kBase>(tmem, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
+                               (kc > 0 || ks > 0) ? 1u : 0u);
                 }
             }
             mma_commit(&empty[s]);
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(128, 1)
                 }
                 mbar_expect_tx(&full[s], kStageTx);
                 tma_load_2d(sA + s * kTileBytes, &opmap, &full[s], (kc + kStages) * kElems, ya);
-                tma_load_2d(sB + s * kTileBytes, &opmap, &full[s], (kc + kStages) * kElems, yb);
+                tma_load_2d(sB + s * kTileBytes, mapb, &full[s], (kc + kStages) * kElems, yb);
                 if (KIND == 2) {
                     tma_load_2d(sAl + s * kTileBytes, &opmap_lo, &full[s], (kc + kStages) * kElems, ya);
                     tma_load_2d(sBl + s * kTileBytes, &opmap_lo, &full[s], (kc + kStages) * kElems, yb);
@@ -318,10 +323,18 @@ void launch_update_tc(const void *tmap, const void *tmap_lo, int kind, const Dev
 {
     if (count <= 0) return;
     const CUtensorMap &m = *reinterpret_cast<const CUtensorMap *>(tmap);
-    const CUtensorMap &ml = *reinterpret_cast<const CUtensorMap *>(kind == 2 ? tmap_lo : tmap);
+    const CUtensorMap &ml = *reinterpret_cast<const CUtensorMap *>(kind >= 2 ? tmap_lo : tmap);
     const size_t smem = tc_smem_bytes(kind);
-    static bool once[3] = {false, false, false};
-    if (kind == 1) {
+    static bool once[5] = {false, false, false, false, false};
+    if (kind == 3 || kind == 4) {
+        if (!once[kind]) {
+            cudaFuncSetAttribute(kind == 3 ? update_tc_kernel<3> : update_tc_kernel<4>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            once[kind] = true;
+        }
+        if (kind == 3) update_tc_kernel<3><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
+        else update_tc_kernel<4><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
+    } else if (kind == 1) {
         if (!once[1]) {
             cudaFuncSetAttribute(update_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             once[1] = true;

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libspx.so")
 
 SPX_OK, SPX_ERR_ARG, SPX_ERR_ALLOC, SPX_ERR_CUDA, SPX_ERR_NOT_SPD = 0, 1, 2, 3, 4
 SPX_ERR_ZERO_PIVOT, SPX_ERR_TIMEOUT, SPX_ERR_NOT_CONVERGED, SPX_ERR_STATE = 5, 6, 7, 8
-SPX_LLT, SPX_LU = 0, 1
+SPX_LLT, SPX_LU, SPX_LDLT = 0, 1, 2
+METHODS = {"llt": SPX_LLT, "lu": SPX_LU, "ldlt": SPX_LDLT}
 SPX_FP64, SPX_FP32, SPX_TF32, SPX_BF16 = 0, 1, 2, 3
 SPX_ORDER_AUTO, SPX_ORDER_GRID, SPX_ORDER_GRAPH, SPX_ORDER_GIVEN, SPX_ORDER_NATURAL = 0, 1, 2, 3, 4
 
@@ -67,7 +68,8 @@ class spx_info(ctypes.Structure):
         ("method", ctypes.c_int32), ("precision", ctypes.c_int32)] + [
         (name, ctypes.c_double) for name in ("flops", "flops_stored", "update_flops")] + [
         ("launches_factor", ctypes.c_int64), ("launches_solve", ctypes.c_int64)] + [
-        (name, ctypes.c_double) for name in ("analyze_ms", "factor_ms", "solve_ms")]
+        (name, ctypes.c_double) for name in ("analyze_ms", "factor_ms", "solve_ms")] + [
+        ("npivot_neg", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -375,7 +377,7 @@ def analyze(colptr: np.ndarray, rowind: np.ndarray, method: str = "llt", perm=No
         o.perm = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         o.ordering = SPX_ORDER_GIVEN
     raw = _vp()
-    m = SPX_LLT if method == "llt" else SPX_LU
+    m = METHODS[method]
     st = load().spx_analyze(n, _ptr(colptr), _ptr(rowind), m, ctypes.byref(o), ctypes.byref(raw))
     _check(st, None)
     del keep
