@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) fwd_diag_kernel(DevPlan p, const int32_t 
                                                        int nrhs)
 {
     extern __shared__ unsigned char smraw[];
+    pdl_trigger();
     const int pid = panels[blockIdx.x];
     const int w = p.pw[pid];
     const int i0 = blockIdx.y * kDiagRows;
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(256) fwd_diag_kernel(DevPlan p, const int32_t 
         const int r = e & 31, k = e >> 5;
         ms[k * 33 + r] = r < nrow ? Mi[(i0 + r) + (int64_t)k * w] : (T)0;
     }
+    pdl_wait();   // Y comes from the previous level's kernels
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < kend * nc; e += blockDim.x) {
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk 
                                                       int nrhs)
 {
     extern __shared__ unsigned char smraw[];
+    pdl_trigger();
     const RowChunk ch = chunks[blockIdx.x];
     const int pid = ch.panel;
     const int w = p.pw[pid], h = p.ph[pid];
@@ -139,6 +142,7 @@ __global__ void __launch_bounds__(256) fwd_off_kernel(DevPlan p, const RowChunk 
         const int rr = e & 63, k = e >> 6;
         lsm[e] = rr < nr ? Pn[ch.r0 + rr + (int64_t)k * h] : (T)0;
     }
+    pdl_wait();   // Z from the diagonal kernel just before
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < w * nc; e += blockDim.x) {
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(256) bwd_off_kernel(DevPlan p, const RowChunk 
                                                       T *__restrict__ Tacc, int nrhs)
 {
     extern __shared__ unsigned char smraw[];
+    pdl_trigger();
     T *ls = reinterpret_cast<T *>(smraw);            // ls[k * 65 + r]
     const RowChunk ch = chunks[blockIdx.x];
     const int pid = ch.panel;
@@ -189,6 +194,7 @@ __global__ void __launch_bounds__(256) bwd_off_kernel(DevPlan p, const RowChunk 
         const int r = e & 63, k = e >> 6;
         ls[k * 65 + r] = r < nr ? Pn[ch.r0 + r + (int64_t)k * h] : (T)0;
     }
+    pdl_wait();   // X of the rows below comes from earlier levels
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < 64 * nc; e += blockDim.x) {
@@ -219,6 +225,7 @@ __global__ void __launch_bounds__(256) bwd_diag_kernel(DevPlan p, const int32_t 
                                                        T *__restrict__ X, int nrhs)
 {
     extern __shared__ unsigned char smraw[];
+    pdl_trigger();
     T *ys = reinterpret_cast<T *>(smraw);          // ys[c * w + k]
     const int pid = panels[blockIdx.x];
     const int w = p.pw[pid];
@@ -240,6 +247,7 @@ __global__ void __launch_bounds__(256) bwd_diag_kernel(DevPlan p, const int32_t 
         if (k >= ii) v = lu == 1 ? Mi[ii + k * w] : (lu == 2 && k == ii ? (T)1 : Mi[k + ii * w]);
         ms[a * (w + 1) + k] = v;
     }
+    pdl_wait();   // Z, Tacc and X from earlier kernels
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
         const int nc = min(kRhsChunk, nrhs - c0);
         for (int e = tid; e < w * nc; e += blockDim.x) {
@@ -281,7 +289,9 @@ void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, int wma
     }
     dim3 grid(count, (wmax + kDiagRows - 1) / kDiagRows);
     const size_t smem = sizeof(T) * ((size_t)wmax * kRhsChunk + (size_t)wmax * 33);
-    fwd_diag_kernel<T><<<grid, 256, smem, s>>>(p, panels, Dinv, unit, Y, Z, nrhs);
+    static const bool carveout_once = set_max_carveout(fwd_diag_kernel<T>);
+    (void)carveout_once;
+    launch_pdl(sizeof(T) == 4, fwd_diag_kernel<T>, grid, dim3(256), smem, s, p, panels, Dinv, unit, Y, Z, nrhs);
 }
 
 template <typename T>
@@ -296,7 +306,9 @@ void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wma
         once = true;
     }
     const size_t smem = sizeof(T) * ((size_t)wmax * kRhsChunk + (size_t)wmax * 64);
-    fwd_off_kernel<T><<<count, 256, smem, s>>>(p, chunks, L, Z, Y, nrhs);
+    static const bool carveout_once = set_max_carveout(fwd_off_kernel<T>);
+    (void)carveout_once;
+    launch_pdl(sizeof(T) == 4, fwd_off_kernel<T>, dim3(count), dim3(256), smem, s, p, chunks, L, Z, Y, nrhs);
 }
 
 template <typename T>
@@ -311,7 +323,9 @@ void launch_bwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wma
         once = true;
     }
     const size_t smem = sizeof(T) * ((size_t)wmax * 65 + 64 * kRhsChunk);
-    bwd_off_kernel<T><<<count, 256, smem, s>>>(p, chunks, Lop, X, Tacc, nrhs);
+    static const bool carveout_once = set_max_carveout(bwd_off_kernel<T>);
+    (void)carveout_once;
+    launch_pdl(sizeof(T) == 4, bwd_off_kernel<T>, dim3(count), dim3(256), smem, s, p, chunks, Lop, X, Tacc, nrhs);
 }
 
 template <typename T>
@@ -327,7 +341,9 @@ void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, int wma
     }
     dim3 grid(count, (wmax + kDiagRows - 1) / kDiagRows);
     const size_t smem = sizeof(T) * ((size_t)wmax * kRhsChunk + kDiagRows * (wmax + 1));
-    bwd_diag_kernel<T><<<grid, 256, smem, s>>>(p, panels, Dinv, lu, Z, Tacc, X, nrhs);
+    static const bool carveout_once = set_max_carveout(bwd_diag_kernel<T>);
+    (void)carveout_once;
+    launch_pdl(sizeof(T) == 4, bwd_diag_kernel<T>, grid, dim3(256), smem, s, p, panels, Dinv, lu, Z, Tacc, X, nrhs);
 }
 
 // ---------------------------------------------------------------------------
