@@ -449,12 +449,12 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
 //    (8 x 8 diagonal blocks by single lanes, then pairs of blocks merged with
 //    X21 = -C^{-1} (B A^{-1})), in the factor's arithmetic.
 // ---------------------------------------------------------------------------
-template <typename T, int W>
+template <typename T, int W, bool ldlt>
 __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t *__restrict__ panels,
                                                         T *__restrict__ L, T *__restrict__ Dinv,
                                                         const double *replace_tau_p,
                                                         int64_t *err_col, unsigned long long *nrepl,
-                                                        int ldlt, unsigned long long *nneg)
+                                                        unsigned long long *nneg)
 {
     constexpr int LD = W + 1;
     constexpr int NT = 256, NW = NT / 32;
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
         for (int c = 0; c < kDB; ++c) {
             const int k = kb + c;
             double d = shfl_d(p0[c], c);                 // A(k, k) from lane c
-            if (!ldlt) {                                  // Cholesky: positive pivots
+            if constexpr (!ldlt) {                        // Cholesky: positive pivots
                 if (!(d > 0.0)) {
                     if (lane == 0 && k < w) {
                         if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     // Cholesky: L = l diag(sqrt(d)), keep 1/sqrt(d) for the inverse.
     // LDL^T: store l (unit) with d on the diagonal, keep 1/d.
     if (tid < W) {
-        if (ldlt) {
+        if constexpr (ldlt) {
             rsv[tid] = rcp_newton(dv[tid]);
         } else {
             double sq, rs;
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     T *Mi = Dinv + p.pinv[pid];
     for (int idx = tid; idx < w * w; idx += NT) {
         const int i = idx % w, j = idx / w;
-        if (ldlt) Mi[idx] = i > j ? x[i + j * LD] : (i == j ? (T)rsv[i] : (T)0);
+        if constexpr (ldlt) Mi[idx] = i > j ? x[i + j * LD] : (i == j ? (T)rsv[i] : (T)0);
         else Mi[idx] = i >= j ? x[i + j * LD] * (T)rsv[i] : (T)0;
     }
 }
@@ -662,19 +662,19 @@ constexpr size_t ldl_smem_bytes()
            sizeof(T) * ((size_t)W * (W + 1) + (size_t)(W / 2) * (W / 2));
 }
 
-template <typename T, int W>
+template <typename T, int W, bool ldlt = false>
 void launch_ldl(const DevPlan &p, const int32_t *panels, int count, T *L, T *Dinv,
                 const double *replace_tau, int64_t *err_col, unsigned long long *nrepl, cudaStream_t s,
-                int ldlt = 0, unsigned long long *nneg = nullptr)
+                unsigned long long *nneg = nullptr)
 {
     static bool once = false;
     const size_t smem = ldl_smem_bytes<T, W>();
     if (!once) {
-        cudaFuncSetAttribute(potrf_ldl_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(potrf_ldl_kernel<T, W, ldlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         once = true;
     }
-    potrf_ldl_kernel<T, W><<<count, 256, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl, ldlt,
-                                                    nneg);
+    potrf_ldl_kernel<T, W, ldlt><<<count, 256, smem, s>>>(p, panels, L, Dinv, replace_tau, err_col, nrepl, nneg);
 }
 
 // LDL^T diagonal blocks (panels at most 64 wide): l with d on the diagonal,
@@ -686,9 +686,9 @@ void launch_ldlt_diag(const DevPlan &p, const int32_t *panels, int count, int wm
                       unsigned long long *nneg, cudaStream_t s)
 {
     if (count <= 0) return;
-    if (wmax <= 16) return launch_ldl<T, 16>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, 1, nneg);
-    if (wmax <= 32) return launch_ldl<T, 32>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, 1, nneg);
-    launch_ldl<T, 64>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, 1, nneg);
+    if (wmax <= 16) return launch_ldl<T, 16, true>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, nneg);
+    if (wmax <= 32) return launch_ldl<T, 32, true>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, nneg);
+    launch_ldl<T, 64, true>(p, panels, count, L, Dinv, tau, err_col, nrepl, s, nneg);
 }
 
 template <typename T>
