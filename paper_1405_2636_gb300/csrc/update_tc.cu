@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(128, 1)
     __shared__ __align__(8) uint64_t done;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
+    __shared__ int64_t s_coff[kN];   // target column offset of each facing row of the tile
 
     const TcTile tl = tiles[blockIdx.x];
     const DevTask tk = tasks[tl.task];
@@ -246,6 +247,13 @@ __global__ void __launch_bounds__(128, 1)
         mma_commit(&done);   // arrives once every MMA issued above has completed
         if (!ok) s_fail = 1;
     }
+    // while the MMAs run: the target column offset of each of the tile's
+    // facing rows, so that the epilogue scatters without global lookups
+    {
+        const int j = tl.n0 + (int)threadIdx.x;
+        if (threadIdx.x < kN)
+            s_coff[threadIdx.x] = j < tk.r1 ? (int64_t)(p.rows[p.prow[src] + j] - p.pfcol[tgt]) * p.ph[tgt] : 0;
+    }
     __syncwarp();
     const bool got = mbar_wait(&done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -253,10 +261,7 @@ __global__ void __launch_bounds__(128, 1)
     if (!got || s_fail) {
         if (threadIdx.x == 0) atomicExch(err, 1);
     } else {
-        const int hT = p.ph[tgt];
         float *Ct = C + p.pval[tgt];
-        const int64_t fcolT = p.pfcol[tgt];
-        const int32_t *srow = p.rows + p.prow[src];
         const int32_t *rmap = p.relmap + tk.relmap_off - tk.r0;
         const int i = tl.m0 + warp * 32 + lane;
         const bool row_ok = i < h;
@@ -269,10 +274,7 @@ __global__ void __launch_bounds__(128, 1)
             for (int cc = 0; cc < 16; ++cc) {
                 const int j = tl.n0 + c0 + cc;
                 if (j >= jend) break;
-                if (row_ok && (!lower || i >= j)) {
-                    const int64_t coff = (int64_t)(srow[j] - fcolT) * hT;
-                    atomicAdd(Ct + roff + coff, -__uint_as_float(v[cc]));
-                }
+                if (row_ok && (!lower || i >= j)) atomicAdd(Ct + roff + s_coff[c0 + cc], -__uint_as_float(v[cc]));
             }
         }
     }
