@@ -978,7 +978,7 @@ template <>
 __device__ __forceinline__ void atomic_sub<float>(float *addr, float v) { atomicAdd(addr, -v); }
 
 template <typename T>
-__global__ void __launch_bounds__(256) update_kernel(DevPlan p, const DevTask *__restrict__ tasks,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(DevPlan p, const DevTask *__restrict__ tasks,
                                                      const UpdTile *__restrict__ tiles,
                                                      const T *__restrict__ Aop,
                                                      const T *__restrict__ Bop, T *__restrict__ C,
