@@ -472,15 +472,24 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     T *D = L + p.pval[pid];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int idx = tid; idx < W * W; idx += NT) {
-        const int i = idx % W, j = idx / W;
-        double v = 0.0;
-        if (i < w && j < w) {
-            if (i >= j) v = (double)D[i + (int64_t)j * h];
-        } else if (i == j) {
-            v = 1.0;
+    // the block, padded with the identity to W: every load of a thread is
+    // issued before its first store, so the loads overlap
+    {
+        constexpr int NPER = (W * W + NT - 1) / NT;
+        T vv[NPER];
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) {
+            const int idx = tid + q * NT;
+            const int i = idx % W, j = idx / W;
+            vv[q] = (idx < W * W && i < w && j < w && i >= j) ? D[i + (int64_t)j * h] : (T)0;
         }
-        a[i + j * LD] = v;
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) {
+            const int idx = tid + q * NT;
+            if (idx >= W * W) continue;
+            const int i = idx % W, j = idx / W;
+            a[i + j * LD] = (i < w && j < w) ? (double)vv[q] : (i == j ? 1.0 : 0.0);
+        }
     }
     __syncthreads();
 
