@@ -442,8 +442,9 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
 // so the column chain is kept short:
 //  * the factorization runs in LDL^T form in FP64 -- per column one Newton
 //    reciprocal of the pivot, the multipliers, and the in-block updates,
-//    with no square root on the chain; warp 0 owns each 8-column block panel
-//    in registers (two rows per lane), all warps apply the trailing updates;
+//    with no square root on the chain; warps 0 and 1 own each 8-column
+//    block panel in registers (rows 0-31 and 32-63 of the block; each warp
+//    runs the pivot chain itself), the other warps apply the trailing updates;
 //  * L = l diag(sqrt(d)) is formed afterwards, all columns in parallel;
 //  * L^{-1} = diag(1/sqrt(d)) l^{-1}: the unit-lower l is inverted by blocks
 //    (8 x 8 diagonal blocks by single lanes, then pairs of blocks merged with
@@ -497,23 +498,33 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
     // multipliers into a and the unscaled block columns into lA (two buffers,
     // one per block parity, so that the next panel can overlap the trailing
     // update of the previous one).
-    auto panel = [&](int kb) {
+    // Block panel kb (8 columns), rows in registers, by one warp per row set:
+    //   role 0 (warp 0): rows kb .. kb+31, the pivots and their side effects;
+    //   role 1 (warp 1, when rows kb+32.. exist): rows kb+32 .. kb+63.
+    // Warp 1 recomputes the 8 x 8 diagonal part from its own copy of rows
+    // kb .. kb+7 (lane l holds row kb + (l & 7)) with the same operations in
+    // the same order as warp 0, so its pivots and multipliers are bit-equal
+    // and the two warps never wait for each other.  Multipliers go to a, the
+    // unscaled block columns to lA (two buffers, one per block parity, so
+    // that the next panel can overlap the trailing update of the previous).
+    auto panel = [&](int kb, int role) {
         double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
-        const int r0 = kb + lane, r1 = kb + lane + 32;
-        const bool two = kb + 32 < W;   // warp-uniform: second row set present
-        double p0[kDB], p1[kDB];
+        const int rq = role == 0 ? kb + lane : kb + (lane & 7);   // rows of the pivot chain
+        const int r1 = kb + 32 + lane;                            // role 1: its own rows
+        double q[kDB], p1[kDB];
 #pragma unroll
         for (int c = 0; c < kDB; ++c) {
-            p0[c] = r0 < W ? a[r0 + (kb + c) * LD] : 0.0;
-            p1[c] = (two && r1 < W) ? a[r1 + (kb + c) * LD] : 0.0;
+            q[c] = rq < W ? a[rq + (kb + c) * LD] : 0.0;
+            p1[c] = (role == 1 && r1 < W) ? a[r1 + (kb + c) * LD] : 0.0;
         }
 #pragma unroll
         for (int c = 0; c < kDB; ++c) {
             const int k = kb + c;
-            double d = shfl_d(p0[c], c);                 // A(k, k) from lane c
+            double d = shfl_d(q[c], c);                  // A(k, k) from lane c
+            const bool report = role == 0 && lane == 0 && k < w;
             if constexpr (!ldlt) {                        // Cholesky: positive pivots
                 if (!(d > 0.0)) {
-                    if (lane == 0 && k < w) {
+                    if (report) {
                         if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
                         else atomicMin((long long *)err_col, (long long)(col0 + k));
                     }
@@ -521,33 +532,36 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
                 }
             } else {                                      // LDL^T: static pivoting
                 if (!(fabs(d) >= replace_tau) || (replace_tau <= 0.0 && d == 0.0)) {
-                    if (lane == 0 && k < w) {
+                    if (report) {
                         if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
                         else atomicMin((long long *)err_col, (long long)(col0 + k));
                     }
                     d = replace_tau > 0.0 ? (d < 0.0 ? -replace_tau : replace_tau) : 1.0;
                 }
-                if (lane == 0 && k < w && d < 0.0) atomicAdd(nneg, 1ull);
+                if (report && d < 0.0) atomicAdd(nneg, 1ull);
             }
-            const double r = rcp_newton(d);
-            const double u0 = r0 > k ? p0[c] : 0.0;
+            const double r = 1.0 / d;   // measured faster here than the Newton form
+            const double u0 = rq > k ? q[c] : 0.0;
             const double l0 = u0 * r;
 #pragma unroll
             for (int c2 = c + 1; c2 < kDB; ++c2) {
                 const double ac = shfl_d(u0, c2);                   // A(kb + c2, k)
-                if (r0 >= kb + c2) p0[c2] = fma(-l0, ac, p0[c2]);
-                if (two) p1[c2] = fma(-(p1[c] * r), ac, p1[c2]);
+                if (rq >= kb + c2) q[c2] = fma(-l0, ac, q[c2]);
+                if (role == 1) p1[c2] = fma(-(p1[c] * r), ac, p1[c2]);
             }
-            if (r0 < W) lAb[r0 + c * W] = u0;
-            if (two && r1 < W) lAb[r1 + c * W] = p1[c];
-            p0[c] = r0 > k ? l0 : (r0 == k ? 1.0 : 0.0);
-            if (two) p1[c] = p1[c] * r;
-            if (lane == c) dv[k] = d;
+            if (role == 0) {
+                if (rq < W) lAb[rq + c * W] = u0;
+                q[c] = rq > k ? l0 : (rq == k ? 1.0 : 0.0);
+                if (lane == c) dv[k] = d;
+            } else {
+                if (r1 < W) lAb[r1 + c * W] = p1[c];
+                p1[c] = p1[c] * r;
+            }
         }
 #pragma unroll
         for (int c = 0; c < kDB; ++c) {
-            if (r0 < W) a[r0 + (kb + c) * LD] = p0[c];
-            if (two && r1 < W) a[r1 + (kb + c) * LD] = p1[c];
+            if (role == 0 && rq < W) a[rq + (kb + c) * LD] = q[c];
+            if (role == 1 && r1 < W) a[r1 + (kb + c) * LD] = p1[c];
         }
     };
     // Rank-kDB update by block kb of the lower part of columns [j0, j1),
@@ -578,7 +592,8 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
         }
     };
 
-    if (warp == 0) panel(0);
+    if (warp == 0) panel(0, 0);
+    else if (warp == 1 && 32 < W) panel(0, 1);
     __syncthreads();
     for (int kb = 0; kb < W; kb += kDB) {
         const int nb = kb + kDB;                 // next block
@@ -586,9 +601,12 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
             // columns of the next block first, by every thread
             update(kb, nb, nb + kDB, tid, NT);
             __syncthreads();
-            // warp 0 factors the next block while the others finish this block's update
-            if (warp == 0) panel(nb);
-            else update(kb, nb + kDB, W, tid - 32, NT - 32);
+            // warps 0 (and 1) factor the next block while the others finish
+            // this block's update
+            const bool two = nb + 32 < W;
+            if (warp == 0) panel(nb, 0);
+            else if (warp == 1 && two) panel(nb, 1);
+            else update(kb, nb + kDB, W, tid - (two ? 64 : 32), NT - (two ? 64 : 32));
             __syncthreads();
         }
     }
