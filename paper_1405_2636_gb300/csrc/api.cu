@@ -48,13 +48,15 @@ struct spx_handle_s {
     int64_t dinv_elems = 0;           // sum of w^2 over panels
     std::vector<int64_t> chunk_ptr;   // per level, into d_chunks
     RowChunk *d_chunks = nullptr;
-    std::vector<int64_t> tile_ptr;    // per level, into d_tiles (LLT, or LU's L side)
+    // Each per-level tile list holds the 64 x 64 tiles first, then the 256 x 16
+    // tiles of tasks facing at most 16 rows; *_nar[l] is where the latter start.
+    std::vector<int64_t> tile_ptr, tile_nar;    // per level, into d_tiles (LLT, or LU's L side)
     UpdTile *d_tiles = nullptr;
-    std::vector<int64_t> tileu_ptr;   // per level, LU's U^T side
+    std::vector<int64_t> tileu_ptr, tileu_nar;  // per level, LU's U^T side
     UpdTile *d_tilesu = nullptr;
     // tensor-core updates (Cholesky, TF32/BF16): tasks with a source at least
     // kTcMinWidth wide go to the tcgen05 kernel, the rest to the SIMT kernel
-    std::vector<int64_t> tcsmall_ptr; // per level, SIMT tiles of the narrow tasks
+    std::vector<int64_t> tcsmall_ptr, tcsmall_nar; // per level, SIMT tiles of the narrow tasks
     UpdTile *d_tcsmall = nullptr;
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
@@ -268,26 +270,42 @@ spx_status ensure_device(spx_handle h)
     std::vector<UpdTile> tiles, tilesu;
     h->chunk_ptr.assign(P.nlevels + 1, 0);
     h->tile_ptr.assign(P.nlevels + 1, 0);
+    h->tile_nar.assign(P.nlevels, 0);
     h->tileu_ptr.assign(P.nlevels + 1, 0);
-    const int T = spx::kUpdTile;
+    h->tileu_nar.assign(P.nlevels, 0);
+    // Tiles of one task over source rows [mlo, hk) x columns [r0, r1): 64 x 64
+    // tiles, or 256 x 16 tiles when the task faces at most 16 rows (r1 - r0 <= 16,
+    // where a 64-wide tile would leave three quarters of its columns idle).
+    // Lower-triangular targets skip the tiles lying wholly above the diagonal.
+    auto add_tiles = [](std::vector<UpdTile> &wide, std::vector<UpdTile> &nar, int32_t t,
+                        const spx::Task &tk, int32_t mlo, int32_t hk, bool lower) {
+        const int32_t N = tk.r1 - tk.r0;
+        const int TN = N <= spx::kUpdNarrowN ? spx::kUpdNarrowN : spx::kUpdTile;
+        const int TM = 4096 / TN;
+        std::vector<UpdTile> &out = TN == spx::kUpdTile ? wide : nar;
+        for (int32_t m0 = mlo; m0 < hk; m0 += TM)
+            for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += TN) {
+                if (lower && m0 + TM <= n0) continue;
+                out.push_back(UpdTile{t, m0, n0, 0});
+            }
+    };
     for (int32_t l = 0; l < P.nlevels; ++l) {
         for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q) {
             int32_t k = P.level_panels[q];
             for (int32_t r0 = P.pw[k]; r0 < P.ph[k]; r0 += spx::kTrsmRows)
                 chunks.push_back(RowChunk{k, r0});
         }
+        std::vector<UpdTile> nar, naru;
         for (int32_t t = P.level_task_ptr[l]; t < P.level_task_ptr[l + 1]; ++t) {
             const spx::Task &tk = P.tasks[t];
             const int32_t hk = P.ph[tk.src];
-            for (int32_t m0 = tk.r0; m0 < hk; m0 += T)
-                for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += T) {
-                    if (P.method != SPX_LU && m0 + T <= n0) continue;
-                    tiles.push_back(UpdTile{t, m0, n0, 0});
-                }
-            if (P.method == SPX_LU)
-                for (int32_t m0 = tk.r1; m0 < hk; m0 += T)
-                    for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += T) tilesu.push_back(UpdTile{t, m0, n0, 0});
+            add_tiles(tiles, nar, t, tk, tk.r0, hk, P.method != SPX_LU);
+            if (P.method == SPX_LU) add_tiles(tilesu, naru, t, tk, tk.r1, hk, false);
         }
+        h->tile_nar[l] = (int64_t)tiles.size();
+        tiles.insert(tiles.end(), nar.begin(), nar.end());
+        h->tileu_nar[l] = (int64_t)tilesu.size();
+        tilesu.insert(tilesu.end(), naru.begin(), naru.end());
         h->chunk_ptr[l + 1] = (int64_t)chunks.size();
         h->tile_ptr[l + 1] = (int64_t)tiles.size();
         h->tileu_ptr[l + 1] = (int64_t)tilesu.size();
@@ -299,8 +317,10 @@ spx_status ensure_device(spx_handle h)
         std::vector<UpdTile> small;
         std::vector<spx::TcTile> tct;
         h->tcsmall_ptr.assign(P.nlevels + 1, 0);
+        h->tcsmall_nar.assign(P.nlevels, 0);
         h->tctile_ptr.assign(P.nlevels + 1, 0);
         for (int32_t l = 0; l < P.nlevels; ++l) {
+            std::vector<UpdTile> nar;
             for (int32_t t = P.level_task_ptr[l]; t < P.level_task_ptr[l + 1]; ++t) {
                 const spx::Task &tk = P.tasks[t];
                 const int32_t hk = P.ph[tk.src];
@@ -315,13 +335,11 @@ spx_status ensure_device(spx_handle h)
                             tct.push_back(spx::TcTile{t, m0, n0, 0});
                         }
                 } else {
-                    for (int32_t m0 = tk.r0; m0 < hk; m0 += T)
-                        for (int32_t n0 = tk.r0; n0 < tk.r1; n0 += T) {
-                            if (m0 + T <= n0) continue;
-                            small.push_back(UpdTile{t, m0, n0, 0});
-                        }
+                    add_tiles(small, nar, t, tk, tk.r0, hk, true);
                 }
             }
+            h->tcsmall_nar[l] = (int64_t)small.size();
+            small.insert(small.end(), nar.begin(), nar.end());
             h->tcsmall_ptr[l + 1] = (int64_t)small.size();
             h->tctile_ptr[l + 1] = (int64_t)tct.size();
         }
@@ -419,7 +437,9 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
         const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
         const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
         const UpdTile *tl = h->d_tiles + h->tile_ptr[l];
-        const int ntl = (int)(h->tile_ptr[l + 1] - h->tile_ptr[l]);
+        const int ntl = (int)(h->tile_nar[l] - h->tile_ptr[l]);
+        const UpdTile *tln = h->d_tiles + h->tile_nar[l];
+        const int ntln = (int)(h->tile_ptr[l + 1] - h->tile_nar[l]);
         const int wmax = h->lvl_wmax[l];
         for (int c = 0; c < kNumClasses; ++c) {
             const int32_t a = h->cls_ptr[(size_t)l * kNumClasses + c];
@@ -447,31 +467,39 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
             mk.mark(SPX_K_TRSM);
             const T *Bop = ldlt ? W : L;   // LDL^T: C -= L (D L^T)
             if (!tc) {
-                spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, Bop, L, 1, 0, s);
-                cnt += ntl > 0;
+                spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, Bop, L, 1, 0, s, 0);
+                spx::launch_update<T>(h->dp, h->d_tasks, tln, ntln, L, Bop, L, 1, 0, s, 1);
+                cnt += (ntl > 0) + (ntln > 0);
                 mk.mark(SPX_K_UPDATE);
             } else {
                 const UpdTile *ts = h->d_tcsmall + h->tcsmall_ptr[l];
-                const int nts = (int)(h->tcsmall_ptr[l + 1] - h->tcsmall_ptr[l]);
+                const int nts = (int)(h->tcsmall_nar[l] - h->tcsmall_ptr[l]);
+                const UpdTile *tsn = h->d_tcsmall + h->tcsmall_nar[l];
+                const int ntsn = (int)(h->tcsmall_ptr[l + 1] - h->tcsmall_nar[l]);
                 const spx::TcTile *tt = h->d_tctiles + h->tctile_ptr[l];
                 const int ntt = (int)(h->tctile_ptr[l + 1] - h->tctile_ptr[l]);
-                spx::launch_update<T>(h->dp, h->d_tasks, ts, nts, L, Bop, L, 1, 0, s);
+                spx::launch_update<T>(h->dp, h->d_tasks, ts, nts, L, Bop, L, 1, 0, s, 0);
+                spx::launch_update<T>(h->dp, h->d_tasks, tsn, ntsn, L, Bop, L, 1, 0, s, 1);
                 mk.mark(SPX_K_UPDATE);
                 spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, tt, ntt,
                                       (float *)L, 1, h->d_tcerr, s);
                 mk.mark(SPX_K_UPDATE_TC);
-                cnt += (nts > 0) + (ntt > 0);
+                cnt += (nts > 0) + (ntsn > 0) + (ntt > 0);
             }
         } else {
             const UpdTile *tu = h->d_tilesu + h->tileu_ptr[l];
-            const int ntu = (int)(h->tileu_ptr[l + 1] - h->tileu_ptr[l]);
+            const int ntu = (int)(h->tileu_nar[l] - h->tileu_ptr[l]);
+            const UpdTile *tun = h->d_tilesu + h->tileu_nar[l];
+            const int ntun = (int)(h->tileu_ptr[l + 1] - h->tileu_nar[l]);
             spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LU_L, nullptr, nullptr, 0, 0, s);
             spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, U, spx::TRSM_LU_U, nullptr, nullptr, 0, 0, s);
             cnt += 2 * (nch > 0);
             mk.mark(SPX_K_TRSM);
-            spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, U, L, 0, 0, s);
-            spx::launch_update<T>(h->dp, h->d_tasks, tu, ntu, U, L, U, 0, 1, s);
-            cnt += (ntl > 0) + (ntu > 0);
+            spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, U, L, 0, 0, s, 0);
+            spx::launch_update<T>(h->dp, h->d_tasks, tln, ntln, L, U, L, 0, 0, s, 1);
+            spx::launch_update<T>(h->dp, h->d_tasks, tu, ntu, U, L, U, 0, 1, s, 0);
+            spx::launch_update<T>(h->dp, h->d_tasks, tun, ntun, U, L, U, 0, 1, s, 1);
+            cnt += (ntl > 0) + (ntln > 0) + (ntu > 0) + (ntun > 0);
             mk.mark(SPX_K_UPDATE);
         }
     }
@@ -1029,11 +1057,14 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
                                            h->cls_ptr[(size_t)l * kNumClasses + c]);
             K.launches[SPX_K_TRSM] += (int64_t)nfac * (h->chunk_ptr[l + 1] > h->chunk_ptr[l]);
             if (tcm) {
-                K.launches[SPX_K_UPDATE] += (h->tcsmall_ptr[l + 1] > h->tcsmall_ptr[l]);
+                K.launches[SPX_K_UPDATE] += (h->tcsmall_nar[l] > h->tcsmall_ptr[l]) +
+                                            (h->tcsmall_ptr[l + 1] > h->tcsmall_nar[l]);
                 K.launches[SPX_K_UPDATE_TC] += (h->tctile_ptr[l + 1] > h->tctile_ptr[l]);
             } else {
-                K.launches[SPX_K_UPDATE] += (h->tile_ptr[l + 1] > h->tile_ptr[l]) +
-                                            (h->tileu_ptr[l + 1] > h->tileu_ptr[l]);
+                K.launches[SPX_K_UPDATE] += (h->tile_nar[l] > h->tile_ptr[l]) +
+                                            (h->tile_ptr[l + 1] > h->tile_nar[l]) +
+                                            (h->tileu_nar[l] > h->tileu_ptr[l]) +
+                                            (h->tileu_ptr[l + 1] > h->tileu_nar[l]);
             }
         }
     }

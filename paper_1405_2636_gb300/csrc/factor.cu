@@ -1004,15 +1004,19 @@ __device__ __forceinline__ void atomic_sub<double>(double *addr, double v) { ato
 template <>
 __device__ __forceinline__ void atomic_sub<float>(float *addr, float v) { atomicAdd(addr, -v); }
 
-template <typename T>
+template <typename T, int TN>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(DevPlan p, const DevTask *__restrict__ tasks,
                                                      const UpdTile *__restrict__ tiles,
                                                      const T *__restrict__ Aop,
                                                      const T *__restrict__ Bop, T *__restrict__ C,
                                                      int lower, int from_r1)
 {
-    __shared__ T As[16][kUpdTile + 1];
-    __shared__ T Bs[16][kUpdTile + 1];
+    // TM x TN output tile (64 x 64, or 256 x 16 for tasks facing few rows),
+    // 4 x 4 outputs per thread, K-chunks of 16 staged in shared memory
+    constexpr int TM = 4096 / TN;
+    constexpr int RX = TM / 4, CX = TN / 4;      // thread grid: RX rows x 256/RX column groups
+    __shared__ T As[16][TM + 1];
+    __shared__ T Bs[16][TN + 1];
     const UpdTile tl = tiles[blockIdx.x];
     const DevTask tk = tasks[tl.task];
     const int src = tk.src, tgt = tk.tgt;
@@ -1021,30 +1025,44 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(Dev
     const T *A = Aop + sbase;
     const T *B = Bop + sbase;
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int tx = tid % RX, ty = tid / RX;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-    const int lr = tid & 63, lk = tid >> 6;   // loader: 64 rows x 4 k per pass
     for (int k0 = 0; k0 < K; k0 += 16) {
+        if constexpr (TN == TM) {
+            // loader: TM rows x 4 k per pass, A and B side by side
+            const int lr = tid % TM, lk = tid / TM;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int kk = lk + 4 * q;
-            const int kg = k0 + kk;
-            const int ra = tl.m0 + lr, rb = tl.n0 + lr;
-            As[kk][lr] = (kg < K && ra < h) ? A[ra + (int64_t)kg * h] : (T)0;
-            Bs[kk][lr] = (kg < K && rb < tk.r1) ? B[rb + (int64_t)kg * h] : (T)0;
+            for (int q = 0; q < 4; ++q) {
+                const int kk = lk + 4 * q;
+                const int kg = k0 + kk;
+                const int ra = tl.m0 + lr, rb = tl.n0 + lr;
+                As[kk][lr] = (kg < K && ra < h) ? A[ra + (int64_t)kg * h] : (T)0;
+                Bs[kk][lr] = (kg < K && rb < tk.r1) ? B[rb + (int64_t)kg * h] : (T)0;
+            }
+        } else {
+            // loader: 256 rows x 1 k per pass for A, one 16 x 16 block for B
+            static_assert(TM == 256 && TN == 16, "narrow tile is 256 x 16");
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                const int kg = k0 + kk, ra = tl.m0 + tid;
+                As[kk][tid] = (kg < K && ra < h) ? A[ra + (int64_t)kg * h] : (T)0;
+            }
+            const int r = tid & 15, kk = tid >> 4;
+            const int kg = k0 + kk, rb = tl.n0 + r;
+            Bs[kk][r] = (kg < K && rb < tk.r1) ? B[rb + (int64_t)kg * h] : (T)0;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             T av[4], bv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + RX * a];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + CX * b];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1062,18 +1080,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(Dev
     bool cok[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const int j = tl.n0 + ty + 16 * b;
+        const int j = tl.n0 + ty + CX * b;
         cok[b] = j < tk.r1;
         coff[b] = cok[b] ? (int64_t)(srow[j] - fcolT) * hT : 0;
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int i = tl.m0 + tx + 16 * a;
+        const int i = tl.m0 + tx + RX * a;
         if (i >= h || i < rlo) continue;
         const int64_t roff = rmap[i];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int j = tl.n0 + ty + 16 * b;
+            const int j = tl.n0 + ty + CX * b;
             if (!cok[b] || (lower && i < j)) continue;
             atomic_sub<T>(Ct + roff + coff[b], acc[a][b]);
         }
@@ -1082,10 +1100,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(Dev
 
 template <typename T>
 void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles, int count,
-                   const T *Aop, const T *Bop, T *C, int lower, int from_r1, cudaStream_t s)
+                   const T *Aop, const T *Bop, T *C, int lower, int from_r1, cudaStream_t s, int narrow)
 {
     if (count <= 0) return;
-    update_kernel<T><<<count, 256, 0, s>>>(p, tasks, tiles, Aop, Bop, C, lower, from_r1);
+    if (narrow) update_kernel<T, 16><<<count, 256, 0, s>>>(p, tasks, tiles, Aop, Bop, C, lower, from_r1);
+    else update_kernel<T, 64><<<count, 256, 0, s>>>(p, tasks, tiles, Aop, Bop, C, lower, from_r1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1161,7 +1180,7 @@ template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, c
 template void launch_ldlt_diag<double>(const DevPlan &, const int32_t *, int, int, double *, double *, const double *, int64_t *, unsigned long long *, unsigned long long *, cudaStream_t);
 template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, void *, void *, int, int, cudaStream_t, float *);
 template void launch_ldlt_diag<float>(const DevPlan &, const int32_t *, int, int, float *, float *, const double *, int64_t *, unsigned long long *, unsigned long long *, cudaStream_t);
-template void launch_update<double>(const DevPlan &, const DevTask *, const UpdTile *, int, const double *, const double *, double *, int, int, cudaStream_t);
-template void launch_update<float>(const DevPlan &, const DevTask *, const UpdTile *, int, const float *, const float *, float *, int, int, cudaStream_t);
+template void launch_update<double>(const DevPlan &, const DevTask *, const UpdTile *, int, const double *, const double *, double *, int, int, cudaStream_t, int);
+template void launch_update<float>(const DevPlan &, const DevTask *, const UpdTile *, int, const float *, const float *, float *, int, int, cudaStream_t, int);
 
 }  // namespace spx

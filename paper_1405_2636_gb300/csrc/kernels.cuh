@@ -25,8 +25,9 @@ struct DevTask {
     int64_t relmap_off;
 };
 
-// A 64 x 64 tile of one update task: rows [m0, m0+64) x columns [n0, n0+64)
-// in the source panel's local row numbering.
+// A tile of one update task: rows [m0, m0+64) x columns [n0, n0+64) in the
+// source panel's local row numbering, or (narrow tiles, for tasks facing at
+// most 16 rows) rows [m0, m0+256) x columns [n0, n0+16).
 struct UpdTile {
     int32_t task, m0, n0, pad;
 };
@@ -44,6 +45,7 @@ struct RowChunk {
 
 constexpr int kMaxWidth = 160;      // widest panel the diagonal-block kernels keep in shared memory
 constexpr int kUpdTile = 64;
+constexpr int kUpdNarrowN = 16;   // tasks facing at most this many rows take 256 x 16 tiles
 constexpr int kTrsmRows = 64;
 
 // TRSM variants on the off-diagonal rows X of a panel (diagonal block D):
@@ -144,7 +146,7 @@ void launch_update_tc(const void *tmap, const void *tmap_lo, int kind, const Dev
 
 template <typename T>
 void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles, int count,
-                   const T *Aop, const T *Bop, T *C, int lower, int from_r1, cudaStream_t s);
+                   const T *Aop, const T *Bop, T *C, int lower, int from_r1, cudaStream_t s, int narrow = 0);
 
 // The standalone update of the paper's kernel study (double).
 void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A, int64_t lda,
