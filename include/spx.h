@@ -148,7 +148,10 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
 /* Solve A X = B for nrhs columns.  B and X are host or device arrays
  * (`on_device`), column-major with leading dimensions ldb, ldx >= n; X may
  * equal B.  `refine` NULL: no refinement for FP64 factors, the defaults for
- * lower-precision factors.  `info` may be NULL. */
+ * lower-precision factors.  `info` may be NULL.  Each forward or backward
+ * sweep is one launch walking a device-side work queue whose waits are
+ * bounded; SPX_ERR_TIMEOUT if one ran out (here or in an earlier
+ * spx_solve_noalloc on the handle). */
 spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
                      int64_t ldx, int on_device, const spx_refine *refine, spx_solve_info *info,
                      void *cuda_stream);
@@ -188,7 +191,11 @@ spx_status spx_get_panels(spx_handle h, int64_t *first_col, int32_t *width, int3
  *   The sweep vectors live in one file-scope device buffer of 16 MiB that
  *   every GPU loading the library holds until the process exits; the call
  *   needs 4 * n * nrhs elements of the factor's type (8 bytes for an FP64
- *   factor, 4 otherwise) and returns SPX_ERR_ARG when that exceeds 16 MiB.
+ *   factor, 4 otherwise) plus 4 * npanels + 2 32-bit sweep counters, and
+ *   returns SPX_ERR_ARG when that exceeds 16 MiB.
+ *   The sweeps wait on device-side counters with a bounded wait; a wait
+ *   that runs out (which only a stalled device causes) leaves X undefined
+ *   and makes the handle's next spx_solve return SPX_ERR_TIMEOUT.
  *   All calls share that buffer and it keeps the previous call's contents:
  *   calls whose GPU work overlaps (other streams, other handles, other
  *   threads) race and must be ordered by the caller.

@@ -57,6 +57,12 @@ struct spx_handle_s {
     // tensor-core updates (Cholesky, TF32/BF16): tasks with a source at least
     // kTcMinWidth wide go to the tcgen05 kernel, the rest to the SIMT kernel
     std::vector<int64_t> tcsmall_ptr, tcsmall_nar; // per level, SIMT tiles of the narrow tasks
+    // sweep work queues: item orders, chunk -> owning panels, per-panel wait
+    // counts; d_qstate holds the per-sweep counters (zeroed each sweep)
+    int32_t *d_qitems_f = nullptr, *d_qitems_b = nullptr, *d_qtptr = nullptr, *d_qtgt = nullptr;
+    int32_t *d_qneed_f = nullptr, *d_qneed_b = nullptr, *d_qstate = nullptr, *d_qerr = nullptr;
+    int32_t *d_qmerge = nullptr;
+    int32_t q_nitems = 0, q_mat = 0, q_matb = 0, q_vec = 0;
     UpdTile *d_tcsmall = nullptr;
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
@@ -313,6 +319,91 @@ spx_status ensure_device(spx_handle h)
     if ((st = upload(h, &h->d_chunks, chunks)) || (st = upload(h, &h->d_tiles, tiles)) ||
         (st = upload(h, &h->d_tilesu, tilesu)))
         return st;
+    {
+        // Sweep queues.  Forward: per level its panel items, then its chunks;
+        // backward: levels from the root down, chunks before panel items.
+        // A chunk's rows are columns of ancestor panels; each distinct owner
+        // is one count for the forward wait and one flag for the backward.
+        // With panels at most 64 wide, a panel item also takes its first
+        // chunk (the rows right below the diagonal block, usually the
+        // parent's columns), which halves the items on a chain of panels.
+        const int32_t np = P.npanels;
+        const int32_t nchunk = (int32_t)chunks.size();
+        int32_t wmax = 1;
+        for (int32_t q = 0; q < np; ++q) wmax = std::max(wmax, P.pw[q]);
+        const bool merge = wmax <= 64;
+        std::vector<int32_t> itf, itb, tptr(1, 0), tgt, needf(np, 0), needb(np, 0), pmerge(np, -1);
+        std::vector<char> merged(nchunk, 0);
+        itf.reserve((size_t)np + nchunk);
+        itb.reserve((size_t)np + nchunk);
+        for (int32_t c = 0; c < nchunk; ++c) {
+            if (merge && chunks[c].r0 == P.pw[chunks[c].panel]) {
+                pmerge[chunks[c].panel] = c;
+                merged[c] = 1;
+            }
+        }
+        for (int32_t c = 0; c < nchunk; ++c) {
+            const RowChunk &ch = chunks[c];
+            const int32_t *r = P.rows.data() + P.prow[ch.panel];
+            const int32_t r1 = std::min(ch.r0 + spx::kTrsmRows, P.ph[ch.panel]);
+            int32_t last = -1;
+            for (int32_t i = ch.r0; i < r1; ++i) {
+                const int32_t q = P.col2panel[r[i]];
+                if (q != last) {   // rows ascend, so owners come in runs
+                    tgt.push_back(q);
+                    ++needf[q];
+                    last = q;
+                }
+            }
+            tptr.push_back((int32_t)tgt.size());
+            if (!merged[c]) ++needb[ch.panel];
+        }
+        for (int32_t l = 0; l < P.nlevels; ++l) {
+            for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q) itf.push_back(-(P.level_panels[q] + 1));
+            for (int64_t c = h->chunk_ptr[l]; c < h->chunk_ptr[l + 1]; ++c)
+                if (!merged[c]) itf.push_back((int32_t)c);
+        }
+        for (int32_t l = P.nlevels - 1; l >= 0; --l) {
+            for (int64_t c = h->chunk_ptr[l]; c < h->chunk_ptr[l + 1]; ++c)
+                if (!merged[c]) itb.push_back((int32_t)c);
+            for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q) itb.push_back(-(P.level_panels[q] + 1));
+        }
+        // Every wait must name an item earlier in its queue (else the walk
+        // could stall); checked here, before any kernel sees the queues.
+        {
+            std::vector<int64_t> posf(np, -1), posb(np, -1), cposf(nchunk, -1), cposb(nchunk, -1);
+            for (size_t i = 0; i < itf.size(); ++i)
+                (itf[i] < 0 ? posf[-itf[i] - 1] : cposf[itf[i]]) = (int64_t)i;
+            for (size_t i = 0; i < itb.size(); ++i)
+                (itb[i] < 0 ? posb[-itb[i] - 1] : cposb[itb[i]]) = (int64_t)i;
+            int64_t nmerged = 0;
+            for (int32_t c = 0; c < nchunk; ++c) nmerged += merged[c];
+            bool ok = itf.size() == itb.size() && (int64_t)itf.size() == (int64_t)np + nchunk - nmerged;
+            for (int32_t q = 0; q < np && ok; ++q) ok = posf[q] >= 0 && posb[q] >= 0;
+            for (int32_t c = 0; c < nchunk && ok; ++c) {
+                const int32_t pc = chunks[c].panel;
+                // a chunk taken along by its panel item runs at that item's place
+                const int64_t cf = merged[c] ? posf[pc] : cposf[c];
+                const int64_t cb = merged[c] ? posb[pc] : cposb[c];
+                ok = merged[c] ? (cposf[c] < 0 && cposb[c] < 0 && pmerge[pc] == c)
+                               : (cf > posf[pc] && cb < posb[pc]);
+                for (int32_t t = tptr[c]; t < tptr[c + 1] && ok; ++t)
+                    ok = tgt[t] != pc && posf[tgt[t]] > cf && posb[tgt[t]] < cb;
+            }
+            if (!ok) return fail(h, SPX_ERR_STATE, "internal: sweep queue order violates a dependency");
+        }
+        h->q_nitems = (int32_t)itf.size();
+        h->q_mat = wmax * std::max(wmax + 1, 65);
+        h->q_matb = merge ? 65 * wmax : 0;
+        h->q_vec = 16 * std::max(wmax, 64);
+        if ((st = upload(h, &h->d_qitems_f, itf)) || (st = upload(h, &h->d_qitems_b, itb)) ||
+            (st = upload(h, &h->d_qtptr, tptr)) || (st = upload(h, &h->d_qtgt, tgt)) ||
+            (st = upload(h, &h->d_qneed_f, needf)) || (st = upload(h, &h->d_qneed_b, needb)) ||
+            (st = upload(h, &h->d_qmerge, pmerge)) ||
+            (st = dalloc(h, &h->d_qstate, (size_t)4 * np + 2)) || (st = dalloc(h, &h->d_qerr, 1)))
+            return st;
+        CU(cudaMemset(h->d_qerr, 0, sizeof(int32_t)));
+    }
     if (P.method != SPX_LU) {
         std::vector<UpdTile> small;
         std::vector<spx::TcTile> tct;
@@ -506,38 +597,53 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
 }
 
 // One forward + backward sweep in the factor's arithmetic: d_D = A^{-1} d_R.
+// Forward and backward substitution, Y (permuted right-hand sides) to Xs,
+// as one queue launch per direction (sweep.cu); Z and Tacc are work
+// vectors, `state` the 4 npanels + 2 per-sweep counters.  Returns the
+// kernels launched.
+template <typename T>
+int enqueue_queue_sweeps(spx_handle h, int nrhs, T *Y, T *Z, T *Tacc, T *Xs, int32_t *state, cudaStream_t s)
+{
+    const spx::Plan &P = h->plan;
+    const T *L = (const T *)h->d_L, *U = (const T *)h->d_U, *Dinv = (const T *)h->d_Dinv;
+    const bool lu = P.method == SPX_LU;
+    const int32_t np = P.npanels;
+    cudaMemsetAsync(Tacc, 0, sizeof(T) * (size_t)P.n * nrhs, s);
+    cudaMemsetAsync(state, 0, sizeof(int32_t) * ((size_t)4 * np + 2), s);
+    spx::SweepQueue q{};
+    q.nitems = h->q_nitems;
+    q.tptr = h->d_qtptr;
+    q.tgt = h->d_qtgt;
+    q.err = h->d_qerr;
+    q.merge = h->d_qmerge;
+    q.mat_elems = h->q_mat;
+    q.matb_elems = h->q_matb;
+    q.vec_elems = h->q_vec;
+    q.items = h->d_qitems_f;
+    q.need = h->d_qneed_f;
+    q.cnt = state;
+    q.flag = state + np;
+    q.head = state + 4 * np;
+    spx::launch_fwd_queue<T>(h->dp, q, h->d_chunks, Dinv, P.method != SPX_LLT ? 1 : 0, L, Y, Z, nrhs, s);
+    q.items = h->d_qitems_b;
+    q.need = h->d_qneed_b;
+    q.cnt = state + 2 * np;
+    q.flag = state + 3 * np;
+    q.head = state + 4 * np + 1;
+    spx::launch_bwd_queue<T>(h->dp, q, h->d_chunks, Dinv, lu ? 1 : (P.method == SPX_LDLT ? 2 : 0), lu ? U : L, Z,
+                             Tacc, Xs, nrhs, s);
+    return 2 * (q.nitems > 0);
+}
+
 template <typename T>
 void enqueue_sweep(spx_handle h, int nrhs)
 {
     const spx::Plan &P = h->plan;
     cudaStream_t s = h->hs;
-    const T *L = (const T *)h->d_L, *U = (const T *)h->d_U, *Dinv = (const T *)h->d_Dinv;
     T *Y = (T *)h->d_Y, *Z = (T *)h->d_Z, *Tacc = (T *)h->d_T, *Xs = (T *)h->d_Xs;
-    const bool lu = P.method == SPX_LU;
     int64_t k = 0;
     spx::launch_permute_in<T>(P.n, nrhs, h->d_R, P.n, h->d_perm, Y, s);
-    cudaMemsetAsync(Tacc, 0, sizeof(T) * (size_t)P.n * nrhs, s);
-    for (int32_t l = 0; l < P.nlevels; ++l) {
-        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
-        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
-        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
-        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
-        const int wmax = h->lvl_wmax[l];
-        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, P.method != SPX_LLT ? 1 : 0, Y, Z, nrhs, s);
-        spx::launch_fwd_off<T>(h->dp, ch, nch, wmax, L, Z, Y, nrhs, s);
-        k += (np > 0) + (nch > 0);
-    }
-    for (int32_t l = P.nlevels - 1; l >= 0; --l) {
-        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
-        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
-        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
-        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
-        const int wmax = h->lvl_wmax[l];
-        spx::launch_bwd_off<T>(h->dp, ch, nch, wmax, lu ? U : L, Xs, Tacc, nrhs, s);
-        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : (P.method == SPX_LDLT ? 2 : 0), Z, Tacc,
-                                Xs, nrhs, s);
-        k += (np > 0) + (nch > 0);
-    }
+    k += enqueue_queue_sweeps<T>(h, nrhs, Y, Z, Tacc, Xs, h->d_qstate, s);
     spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, h->d_D, P.n, s);
     h->sweep_launches = k + 2;
 }
@@ -705,30 +811,10 @@ void enqueue_sweep_noalloc(spx_handle h, int nrhs, const double *B, int64_t ldb,
 {
     const spx::Plan &P = h->plan;
     const size_t len = (size_t)P.n * nrhs;
-    const T *L = (const T *)h->d_L, *U = (const T *)h->d_U, *Dinv = (const T *)h->d_Dinv;
     T *Y = scratch, *Z = scratch + len, *Tacc = scratch + 2 * len, *Xs = scratch + 3 * len;
-    const bool lu = P.method == SPX_LU;
+    int32_t *state = reinterpret_cast<int32_t *>(scratch + 4 * len);
     spx::launch_permute_in<T>(P.n, nrhs, B, ldb, h->d_perm, Y, s);
-    cudaMemsetAsync(Tacc, 0, sizeof(T) * len, s);
-    for (int32_t l = 0; l < P.nlevels; ++l) {
-        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
-        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
-        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
-        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
-        const int wmax = h->lvl_wmax[l];
-        spx::launch_fwd_diag<T>(h->dp, panels, np, wmax, Dinv, P.method != SPX_LLT ? 1 : 0, Y, Z, nrhs, s);
-        spx::launch_fwd_off<T>(h->dp, ch, nch, wmax, L, Z, Y, nrhs, s);
-    }
-    for (int32_t l = P.nlevels - 1; l >= 0; --l) {
-        const int32_t *panels = h->d_level_panels + P.level_ptr[l];
-        const int np = P.level_ptr[l + 1] - P.level_ptr[l];
-        const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
-        const int nch = (int)(h->chunk_ptr[l + 1] - h->chunk_ptr[l]);
-        const int wmax = h->lvl_wmax[l];
-        spx::launch_bwd_off<T>(h->dp, ch, nch, wmax, lu ? U : L, Xs, Tacc, nrhs, s);
-        spx::launch_bwd_diag<T>(h->dp, panels, np, wmax, Dinv, lu ? 1 : (P.method == SPX_LDLT ? 2 : 0), Z, Tacc,
-                                Xs, nrhs, s);
-    }
+    enqueue_queue_sweeps<T>(h, nrhs, Y, Z, Tacc, Xs, state, s);
     spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, X, ldx, s);
 }
 
@@ -1117,6 +1203,13 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
         h->sgraph_prec = h->precision;
     }
     h->cnt = 0;
+    int32_t qerr = 0;   // a timed-out sweep wait, here or in an earlier spx_solve_noalloc
+    CU(cudaMemcpyAsync(&qerr, h->d_qerr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
+    if (qerr) {
+        CU(cudaMemset(h->d_qerr, 0, sizeof(int32_t)));
+        return fail(h, SPX_ERR_TIMEOUT, "a sweep of an earlier spx_solve_noalloc gave up waiting on its work queue");
+    }
     CU(cudaEventRecord(h->ev_t0, h->hs));
     CU(cudaMemcpyAsync(h->d_R, h->d_B, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, h->hs));
     CU(cudaGraphLaunch(h->sgraph, h->hs));
@@ -1148,7 +1241,12 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
     CU(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), h->d_X, n * sizeof(double),
                          n * sizeof(double), nrhs,
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&qerr, h->d_qerr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaStreamSynchronize(h->hs));
+    if (qerr) {
+        CU(cudaMemset(h->d_qerr, 0, sizeof(int32_t)));
+        return fail(h, SPX_ERR_TIMEOUT, "a triangular sweep gave up waiting on its work queue");
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
     h->info.solve_ms = ms;
@@ -1269,10 +1367,11 @@ spx_status spx_solve_noalloc(spx_handle h, int32_t nrhs, const double *B, int64_
     if (ldb < P.n || ldx < P.n) return fail(h, SPX_ERR_ARG, "leading dimension below n");
     if (nrhs == 0) return SPX_OK;
     const size_t esz = h->precision == SPX_FP64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)4 * (size_t)P.n * (size_t)nrhs * esz;
+    const size_t need = (size_t)4 * (size_t)P.n * (size_t)nrhs * esz +
+                        sizeof(int32_t) * ((size_t)4 * P.npanels + 2);
     if (need > kStaticScratchBytes)
         return fail(h, SPX_ERR_ARG,
-                    "4 * n * nrhs sweep elements (" + std::to_string(need) +
+                    "4 * n * nrhs sweep elements and the sweep counters (" + std::to_string(need) +
                         " bytes) exceed the 16 MiB static scratch of spx_solve_noalloc");
     int dev = -1;
     CU(cudaGetDevice(&dev));

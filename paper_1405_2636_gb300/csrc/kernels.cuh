@@ -57,50 +57,15 @@ enum TrsmMode : int {
     TRSM_LDLT = 4        // W = X l^{-T} (unit l) to Wout, X <- W D^{-1}   (LDL^T)
 };
 
-// One shared-memory carveout (the largest) for the solve-sweep kernels, so
-// that their alternating launches with different shared-memory sizes never
-// make an SM switch its L1 / shared-memory split between them (measured:
-// 3% faster sweeps; the factorization kernels are faster without it).
+// The largest shared-memory carveout, for the solve-sweep kernels (their
+// occupancy is set by shared memory; the factorization kernels are faster
+// with the default split).
 template <typename F>
 inline bool set_max_carveout(F *kernel)
 {
     cudaFuncSetAttribute(reinterpret_cast<const void *>(kernel), cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     return true;
-}
-
-// Programmatic dependent launch.  A kernel launched with launch_pdl may start
-// while the previous kernel of its stream is still running: it does the work
-// that does not depend on that kernel (loading the factor, which is fixed
-// during a solve), then pdl_wait() returns once every earlier grid of the
-// stream has completed and its memory is visible.  pdl_trigger() lets the
-// next kernel be scheduled as soon as all CTAs of this one have started.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// early = false launches in plain stream order.  The sweeps use early
-// launches for single-precision factors only: measured on the 64^3 solve,
-// FP32 sweeps 44.6 -> 33.9 ms, while FP64 sweeps (whose CTAs are bound by
-// the FP64 pipe, not by latency) slowed from 30 to 41 ms.
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(bool early, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, Args... args)
-{
-    if (!early) {
-        kernel<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 // ---- factorization -------------------------------------------------------
@@ -158,24 +123,33 @@ void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A,
 // n x nrhs.  Forward: Z_p = D_p^{-1} Y_p, then Y(rows below) -= L_off Z_p.
 // Backward: T_p += L_off^T X(rows below) (split over row chunks), then
 // X_p = D_p^{-T} (Z_p - T_p)  (LU: U_p^{-1} (Z_p - T_p) with the U^T panel).
+// Each direction is one launch over a work queue (sweep.cu).
 template <typename T>
 void launch_permute_in(int64_t n, int nrhs, const double *B, int64_t ldb, const int64_t *perm,
                        T *Y, cudaStream_t s);
 template <typename T>
 void launch_permute_out(int64_t n, int nrhs, const T *Y, const int64_t *perm, double *X,
                         int64_t ldx, cudaStream_t s);
+// Device-resident work queue of one sweep direction (sweep.cu).  items[]:
+// >= 0 a row chunk (index into the chunk list), < 0 panel -(item + 1), in
+// an order where every item's inputs come from earlier items.  cnt, flag
+// and head are zeroed before each sweep; err is set when a wait runs out.
+struct SweepQueue {
+    const int32_t *items;
+    int32_t nitems;
+    const int32_t *tptr, *tgt;   // per chunk: the distinct panels owning its rows
+    const int32_t *need;         // per panel: counts its panel item waits for
+    const int32_t *merge;        // per panel: its first chunk when the panel item takes it along, else -1
+    int32_t *cnt, *flag, *head;
+    int32_t *err;
+    int32_t mat_elems, matb_elems, vec_elems;   // shared-memory staging, elements of T (matb_elems 0: no chunks taken along)
+};
 template <typename T>
-void launch_fwd_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const T *Dinv,
-                     int unit, const T *Y, T *Z, int nrhs, cudaStream_t s);
+void launch_fwd_queue(const DevPlan &p, const SweepQueue &q, const RowChunk *chunks, const T *Dinv,
+                      int unit, const T *L, T *Y, T *Z, int nrhs, cudaStream_t s);
 template <typename T>
-void launch_fwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *L,
-                    const T *Z, T *Y, int nrhs, cudaStream_t s);
-template <typename T>
-void launch_bwd_off(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Lop,
-                    const T *X, T *Tacc, int nrhs, cudaStream_t s);
-template <typename T>
-void launch_bwd_diag(const DevPlan &p, const int32_t *panels, int count, int wmax, const T *Dinv,
-                     int lu, const T *Z, const T *Tacc, T *X, int nrhs, cudaStream_t s);
+void launch_bwd_queue(const DevPlan &p, const SweepQueue &q, const RowChunk *chunks, const T *Dinv,
+                      int lu, const T *Lop, const T *Z, T *Tacc, T *X, int nrhs, cudaStream_t s);
 
 // ---- FGMRES vector kernels (FP64, n x nrhs column blocks, ld n) ----------
 void launch_spmv_cols(int64_t n, int nrhs, const int64_t *rp, const int32_t *ci, const int64_t *src,

@@ -1,0 +1,401 @@
+// sweep.cu -- forward and backward substitution on the panel factor, each
+// direction one launch over a device-resident queue of work items.
+//
+// The items are the per-panel steps of the triangular solves in elimination
+// order (Sec. III orders the factorization tasks the same way): a panel item
+// applies the inverted diagonal block, a chunk item moves 64 off-diagonal
+// rows of a panel between the panel and its ancestors.  CTAs take items from
+// one atomic counter in queue order; an item waits on per-panel counters for
+// the items it depends on, all of which sit earlier in the queue, so the
+// earliest unfinished item always has its inputs and the walk cannot stall.
+// Every wait is bounded: past the limit the kernel sets *err and its CTAs
+// return, which the host reports as a failed solve.
+//
+// Forward (L y = b):
+//   panel p  waits until every chunk writing into rows of p has finished,
+//            then Z_p = Linv_p Y_p and flag[p] = 1;
+//   chunk    waits for flag[p] of its panel, Y[rows] -= L_chunk Z_p, then
+//            counts itself on each panel owning one of its rows.
+// Backward (L^T x = y):
+//   chunk    waits for flag[q] of each panel q owning one of its rows, then
+//            Tacc_p += L_chunk^T X[rows] and counts itself on its panel;
+//   panel p  waits for all its chunks, X_p = M (Z_p - Tacc_p), flag[p] = 1.
+// Right-hand sides are column-major n x nrhs in the permuted numbering.
+#include "kernels.cuh"
+
+namespace spx {
+
+namespace {
+
+constexpr int kQRhs = 16;                   // right-hand sides per pass
+constexpr int kQThreads = 256;
+constexpr unsigned kSpinLimit = 1u << 22;   // polls of ~256 ns: about a second
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Polled by one thread.  False, with *err set, after the polling limit, or
+// as soon as another CTA has reported a timeout.
+__device__ bool wait_geq(const int32_t *p, int target, int32_t *err)
+{
+    if (ld_acquire(p) >= target) return true;
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        __nanosleep(it < 256 ? 32 : 256);
+        if (ld_acquire(p) >= target) return true;
+        if ((it & 1023) == 1023 && ld_acquire(err) != 0) return false;
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+// Data written by other CTAs of the same launch is read through L2.
+template <typename T>
+__device__ __forceinline__ T ld_l2(const T *p)
+{
+    return __ldcg(p);
+}
+
+// Whole CTA: true once every polled counter reached its target.  Thread t
+// polls cnt[ids[t]] (ids == nullptr: thread 0 polls cnt[0]) for t < m.
+__device__ __forceinline__ bool cta_wait(const int32_t *cnt, const int32_t *ids, int m, int target,
+                                         int32_t *err)
+{
+    int ok = 1;
+    if ((int)threadIdx.x < m) ok = wait_geq(cnt + (ids ? ids[threadIdx.x] : 0), target, err);
+    return __syncthreads_and(ok) != 0;
+}
+
+// Whole CTA, after its writes: they become visible before flag[0] = 1 and
+// before each cnt[ids[t]] (t < m; ids == nullptr: cnt[0]) is incremented
+// (barrier, then one gpu-scope fence by the signalling thread).
+__device__ __forceinline__ void cta_release(int32_t *flag, int32_t *cnt, const int32_t *ids, int m)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (flag) atomicExch(flag, 1);
+        for (int t = 0; t < m; ++t) atomicAdd(cnt + (ids ? ids[t] : 0), 1);
+    }
+}
+
+// Rows [r0, r0 + 64) of a panel's off-diagonal block to dst[k * ld + r]
+// (rows past the panel as zeros).
+template <typename T>
+__device__ __forceinline__ void stage_chunk(T *dst, int ld, const T *Pn, int h, int w, int r0, int nr)
+{
+    for (int e = threadIdx.x; e < w * 64; e += kQThreads) {
+        const int r = e & 63, k = e >> 6;
+        dst[k * ld + r] = r < nr ? Pn[r0 + r + (int64_t)k * h] : (T)0;
+    }
+}
+
+// Y[rows[r]] -= sum_k Lc(r, k) Zs(k, c): Lc staged [k * 64 + r], Zs[c * w + k].
+template <typename T>
+__device__ __forceinline__ void fwd_chunk_pass(const T *Lc, const T *Zs, int w, int nr, int nc,
+                                               const int32_t *crows, T *Y, int64_t n, int c0)
+{
+    const int r = threadIdx.x & 63, g = threadIdx.x >> 6;   // 64 rows x 4 column groups
+    if (r >= nr) return;
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+    for (int k = 0; k < w; ++k) {
+        const T l = Lc[k * 64 + r];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = g + 4 * u;
+            if (c < nc) acc[u] += l * Zs[c * w + k];
+        }
+    }
+    const int64_t gi = crows[r];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = g + 4 * u;
+        if (c < nc) atomicAdd(Y + gi + (int64_t)(c0 + c) * n, -acc[u]);
+    }
+}
+
+// Xs[c * 64 + r] = X[rows[r]] (one pass), then returns for (k, c) the sum
+// over r of Lc(r, k) Xs(r, c) with Lc staged [k * 65 + r].
+template <typename T>
+__device__ __forceinline__ void stage_rows(T *Xs, const T *X, const int32_t *crows, int nr, int nc,
+                                           int64_t n, int c0)
+{
+    for (int e = threadIdx.x; e < 64 * nc; e += kQThreads) {
+        const int r = e & 63, c = e >> 6;
+        Xs[c * 64 + r] = r < nr ? ld_l2(X + crows[r] + (int64_t)(c0 + c) * n) : (T)0;
+    }
+}
+template <typename T>
+__device__ __forceinline__ T chunk_dot(const T *Lc, const T *Xs, int k, int c)
+{
+    T a0 = (T)0, a1 = (T)0;
+#pragma unroll 8
+    for (int r = 0; r < 64; r += 2) {
+        a0 += Lc[k * 65 + r] * Xs[c * 64 + r];
+        a1 += Lc[k * 65 + r + 1] * Xs[c * 64 + r + 1];
+    }
+    return a0 + a1;
+}
+
+}  // namespace
+
+// Shared memory: A (q.mat_elems: a diagonal block, or a chunk), B
+// (q.matb_elems: the chunk a panel item takes along), a vector of
+// q.vec_elems and, when panel items take chunks along, a second one.
+template <typename T>
+__global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, SweepQueue q,
+                                                              const RowChunk *__restrict__ chunks,
+                                                              const T *__restrict__ Dinv, int unit,
+                                                              const T *__restrict__ L, T *Y, T *Z, int nrhs)
+{
+    extern __shared__ unsigned char smraw[];
+    T *matA = reinterpret_cast<T *>(smraw);
+    T *matB = matA + q.mat_elems;
+    T *vec = matB + q.matb_elems;
+    T *vec2 = vec + q.vec_elems;
+    __shared__ int s_next;
+    const int tid = threadIdx.x;
+    const int64_t n = p.n;
+    if (tid == 0) s_next = atomicAdd(q.head, 1);
+    __syncthreads();
+    for (;;) {
+        const int idx = s_next;
+        __syncthreads();
+        if (idx >= q.nitems) return;
+        const int item = q.items[idx];
+        if (tid == 0) s_next = atomicAdd(q.head, 1);   // the next item, fetched early
+        if (item < 0) {
+            // panel: Z_p = Linv_p Y_p (LU / LDL^T: unit Linv), then its
+            // first chunk when it takes one along
+            const int pid = -item - 1;
+            const int w = p.pw[pid], h = p.ph[pid];
+            const int64_t f = p.pfcol[pid];
+            const T *Mi = Dinv + p.pinv[pid];
+            const int mc = q.merge[pid];
+            for (int e = tid; e < w * w; e += kQThreads) matA[e] = Mi[e];   // column-major, ld w
+            int nr = 0;
+            if (mc >= 0) {
+                nr = min(64, h - w);
+                stage_chunk(matB, 64, L + p.pval[pid], h, w, w, nr);
+            }
+            if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err)) return;
+            for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
+                const int nc = min(kQRhs, nrhs - c0);
+                for (int e = tid; e < w * nc; e += kQThreads) {
+                    const int k = e % w, c = e / w;
+                    vec[c * w + k] = ld_l2(Y + f + k + (int64_t)(c0 + c) * n);
+                }
+                __syncthreads();
+                for (int e = tid; e < w * nc; e += kQThreads) {
+                    const int i = e % w, c = e / w;
+                    const T *yc = vec + c * w;
+                    T a0 = unit ? yc[i] : (T)0, a1 = (T)0;
+                    const int kl = unit ? i : i + 1;
+                    int k = 0;
+                    for (; k + 1 < kl; k += 2) {
+                        a0 += matA[i + k * w] * yc[k];
+                        a1 += matA[i + (k + 1) * w] * yc[k + 1];
+                    }
+                    if (k < kl) a0 += matA[i + k * w] * yc[k];
+                    const T z = a0 + a1;
+                    Z[f + i + (int64_t)(c0 + c) * n] = z;
+                    if (mc >= 0) vec2[c * w + i] = z;
+                }
+                __syncthreads();
+                if (mc >= 0) fwd_chunk_pass(matB, vec2, w, nr, nc, p.rows + p.prow[pid] + w, Y, n, c0);
+                __syncthreads();
+            }
+            const int t0 = mc >= 0 ? q.tptr[mc] : 0, t1 = mc >= 0 ? q.tptr[mc + 1] : 0;
+            cta_release(q.flag + pid, q.cnt, q.tgt + t0, t1 - t0);
+        } else {
+            // chunk: Y[rows] -= L(rows, :) Z_p
+            const RowChunk ch = chunks[item];
+            const int pid = ch.panel;
+            const int w = p.pw[pid], h = p.ph[pid];
+            const int64_t f = p.pfcol[pid];
+            const int nr = min(64, h - ch.r0);
+            stage_chunk(matA, 64, L + p.pval[pid], h, w, ch.r0, nr);
+            if (!cta_wait(q.flag + pid, nullptr, 1, 1, q.err)) return;
+            for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
+                const int nc = min(kQRhs, nrhs - c0);
+                for (int e = tid; e < w * nc; e += kQThreads) {
+                    const int k = e % w, c = e / w;
+                    vec[c * w + k] = ld_l2(Z + f + k + (int64_t)(c0 + c) * n);
+                }
+                __syncthreads();
+                fwd_chunk_pass(matA, vec, w, nr, nc, p.rows + p.prow[pid] + ch.r0, Y, n, c0);
+                __syncthreads();
+            }
+            const int t0 = q.tptr[item], t1 = q.tptr[item + 1];
+            cta_release(nullptr, q.cnt, q.tgt + t0, t1 - t0);
+        }
+    }
+}
+
+// lu: 0 Cholesky (M = Linv^T), 1 LU (M = U^{-1}), 2 LDL^T
+// (X_p = l^{-T} (D^{-1} Z_p - Tacc_p), 1/d on the diagonal of Dinv).
+template <typename T>
+__global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, SweepQueue q,
+                                                              const RowChunk *__restrict__ chunks,
+                                                              const T *__restrict__ Dinv, int lu,
+                                                              const T *__restrict__ Lop,
+                                                              const T *__restrict__ Z, T *Tacc, T *X,
+                                                              int nrhs)
+{
+    extern __shared__ unsigned char smraw[];
+    T *matA = reinterpret_cast<T *>(smraw);
+    T *matB = matA + q.mat_elems;
+    T *vec = matB + q.matb_elems;
+    T *vec2 = vec + q.vec_elems;
+    __shared__ int s_next;
+    const int tid = threadIdx.x;
+    const int64_t n = p.n;
+    if (tid == 0) s_next = atomicAdd(q.head, 1);
+    __syncthreads();
+    for (;;) {
+        const int idx = s_next;
+        __syncthreads();
+        if (idx >= q.nitems) return;
+        const int item = q.items[idx];
+        if (tid == 0) s_next = atomicAdd(q.head, 1);
+        if (item < 0) {
+            // panel: X_p = M (Z_p - Tacc_p - Lc^T X[rows of its first chunk])
+            const int pid = -item - 1;
+            const int w = p.pw[pid], h = p.ph[pid], ld = w + 1;
+            const int64_t f = p.pfcol[pid];
+            const T *Mi = Dinv + p.pinv[pid];
+            const int mc = q.merge[pid];
+            // matA[i + k ld] = M(i, k), k >= i
+            for (int e = tid; e < w * w; e += kQThreads) {
+                int i, k;
+                T v;
+                if (lu == 1) {
+                    i = e % w;
+                    k = e / w;
+                    v = Mi[i + k * w];
+                } else {
+                    k = e % w;
+                    i = e / w;
+                    v = (lu == 2 && k == i) ? (T)1 : Mi[k + i * w];
+                }
+                matA[i + k * ld] = k >= i ? v : (T)0;
+            }
+            int nr = 0;
+            const int32_t *crows = p.rows + p.prow[pid] + w;
+            if (mc >= 0) {
+                nr = min(64, h - w);
+                stage_chunk(matB, 65, Lop + p.pval[pid], h, w, w, nr);
+                const int t0 = q.tptr[mc], t1 = q.tptr[mc + 1];
+                if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err)) return;
+            }
+            if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err)) return;
+            for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
+                const int nc = min(kQRhs, nrhs - c0);
+                if (mc >= 0) {
+                    stage_rows(vec2, X, crows, nr, nc, n, c0);
+                    __syncthreads();
+                }
+                for (int e = tid; e < w * nc; e += kQThreads) {
+                    const int k = e % w, c = e / w;
+                    const int64_t gk = f + k + (int64_t)(c0 + c) * n;
+                    T v = (lu == 2 ? Z[gk] * Mi[k + k * w] : Z[gk]) - ld_l2(Tacc + gk);
+                    if (mc >= 0) v -= chunk_dot(matB, vec2, k, c);
+                    vec[c * w + k] = v;
+                }
+                __syncthreads();
+                for (int e = tid; e < w * nc; e += kQThreads) {
+                    const int i = e % w, c = e / w;
+                    const T *yc = vec + c * w;
+                    T a0 = (T)0, a1 = (T)0;
+                    int k = i;
+                    for (; k + 1 < w; k += 2) {
+                        a0 += matA[i + k * ld] * yc[k];
+                        a1 += matA[i + (k + 1) * ld] * yc[k + 1];
+                    }
+                    if (k < w) a0 += matA[i + k * ld] * yc[k];
+                    X[f + i + (int64_t)(c0 + c) * n] = a0 + a1;
+                }
+                __syncthreads();
+            }
+            cta_release(q.flag + pid, nullptr, nullptr, 0);
+        } else {
+            // chunk: Tacc_p += Lop(rows, :)^T X[rows]
+            const RowChunk ch = chunks[item];
+            const int pid = ch.panel;
+            const int w = p.pw[pid], h = p.ph[pid];
+            const int64_t f = p.pfcol[pid];
+            const int nr = min(64, h - ch.r0);
+            stage_chunk(matA, 65, Lop + p.pval[pid], h, w, ch.r0, nr);
+            const int t0 = q.tptr[item], t1 = q.tptr[item + 1];
+            if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err)) return;
+            for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
+                const int nc = min(kQRhs, nrhs - c0);
+                stage_rows(vec, X, p.rows + p.prow[pid] + ch.r0, nr, nc, n, c0);
+                __syncthreads();
+                for (int e = tid; e < w * nc; e += kQThreads) {
+                    const int k = e % w, c = e / w;
+                    atomicAdd(Tacc + f + k + (int64_t)(c0 + c) * n, chunk_dot(matA, vec, k, c));
+                }
+                __syncthreads();
+            }
+            cta_release(nullptr, q.cnt + pid, nullptr, 1);
+        }
+    }
+}
+
+namespace {
+
+template <typename K>
+unsigned queue_grid(K kernel, size_t smem, int nitems)
+{
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_max_carveout(kernel);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kQThreads, smem);
+    const long long g = (long long)std::max(occ, 1) * std::max(sms, 1);
+    return (unsigned)std::max(1LL, std::min<long long>(g, nitems));
+}
+
+template <typename T>
+size_t queue_smem(const SweepQueue &q)
+{
+    return sizeof(T) * ((size_t)q.mat_elems + (size_t)q.matb_elems + (q.matb_elems ? 2 : 1) * (size_t)q.vec_elems);
+}
+
+}  // namespace
+
+template <typename T>
+void launch_fwd_queue(const DevPlan &p, const SweepQueue &q, const RowChunk *chunks, const T *Dinv,
+                      int unit, const T *L, T *Y, T *Z, int nrhs, cudaStream_t s)
+{
+    if (q.nitems <= 0) return;
+    const size_t smem = queue_smem<T>(q);
+    const unsigned grid = queue_grid(fwd_queue_kernel<T>, smem, q.nitems);
+    fwd_queue_kernel<T><<<grid, kQThreads, smem, s>>>(p, q, chunks, Dinv, unit, L, Y, Z, nrhs);
+}
+
+template <typename T>
+void launch_bwd_queue(const DevPlan &p, const SweepQueue &q, const RowChunk *chunks, const T *Dinv,
+                      int lu, const T *Lop, const T *Z, T *Tacc, T *X, int nrhs, cudaStream_t s)
+{
+    if (q.nitems <= 0) return;
+    const size_t smem = queue_smem<T>(q);
+    const unsigned grid = queue_grid(bwd_queue_kernel<T>, smem, q.nitems);
+    bwd_queue_kernel<T><<<grid, kQThreads, smem, s>>>(p, q, chunks, Dinv, lu, Lop, Z, Tacc, X, nrhs);
+}
+
+template void launch_fwd_queue<double>(const DevPlan &, const SweepQueue &, const RowChunk *, const double *, int,
+                                       const double *, double *, double *, int, cudaStream_t);
+template void launch_fwd_queue<float>(const DevPlan &, const SweepQueue &, const RowChunk *, const float *, int,
+                                      const float *, float *, float *, int, cudaStream_t);
+template void launch_bwd_queue<double>(const DevPlan &, const SweepQueue &, const RowChunk *, const double *, int,
+                                       const double *, const double *, double *, double *, int, cudaStream_t);
+template void launch_bwd_queue<float>(const DevPlan &, const SweepQueue &, const RowChunk *, const float *, int,
+                                      const float *, const float *, float *, float *, int, cudaStream_t);
+
+}  // namespace spx
