@@ -93,7 +93,8 @@ __device__ __forceinline__ void stage_chunk(T *dst, int ld, const T *Pn, int h, 
     }
 }
 
-// Y[rows[r]] -= sum_k Lc(r, k) Zs(k, c): Lc staged [k * 64 + r], Zs[c * w + k].
+// Y[rows[r]] -= sum_k Lc(r, k) Zs(k, c): Lc staged [k * 64 + r], Zs[c * w + k]
+// (kQRhs columns, zero past nc).  Thread: row r, columns g, g + 4, ...
 template <typename T>
 __device__ __forceinline__ void fwd_chunk_pass(const T *Lc, const T *Zs, int w, int nr, int nc,
                                                const int32_t *crows, T *Y, int64_t n, int c0)
@@ -101,13 +102,11 @@ __device__ __forceinline__ void fwd_chunk_pass(const T *Lc, const T *Zs, int w, 
     const int r = threadIdx.x & 63, g = threadIdx.x >> 6;   // 64 rows x 4 column groups
     if (r >= nr) return;
     T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll 4
     for (int k = 0; k < w; ++k) {
         const T l = Lc[k * 64 + r];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int c = g + 4 * u;
-            if (c < nc) acc[u] += l * Zs[c * w + k];
-        }
+        for (int u = 0; u < 4; ++u) acc[u] += l * Zs[(g + 4 * u) * w + k];
     }
     const int64_t gi = crows[r];
 #pragma unroll
@@ -117,27 +116,35 @@ __device__ __forceinline__ void fwd_chunk_pass(const T *Lc, const T *Zs, int w, 
     }
 }
 
-// Xs[c * 64 + r] = X[rows[r]] (one pass), then returns for (k, c) the sum
-// over r of Lc(r, k) Xs(r, c) with Lc staged [k * 65 + r].
+// Xs[c * 64 + r] = X[rows[r]] for one pass (kQRhs columns, zero past nc).
 template <typename T>
 __device__ __forceinline__ void stage_rows(T *Xs, const T *X, const int32_t *crows, int nr, int nc,
                                            int64_t n, int c0)
 {
-    for (int e = threadIdx.x; e < 64 * nc; e += kQThreads) {
+    for (int e = threadIdx.x; e < 64 * kQRhs; e += kQThreads) {
         const int r = e & 63, c = e >> 6;
-        Xs[c * 64 + r] = r < nr ? ld_l2(X + crows[r] + (int64_t)(c0 + c) * n) : (T)0;
+        Xs[c * 64 + r] = (r < nr && c < nc) ? ld_l2(X + crows[r] + (int64_t)(c0 + c) * n) : (T)0;
     }
 }
+// acc[u] += sum over r of Lc(r, k) Xs(r, g + 4u), Lc staged [k * 65 + r].
 template <typename T>
-__device__ __forceinline__ T chunk_dot(const T *Lc, const T *Xs, int k, int c)
+__device__ __forceinline__ void chunk_dot4(const T *Lc, const T *Xs, int k, int g, T acc[4])
 {
-    T a0 = (T)0, a1 = (T)0;
-#pragma unroll 8
-    for (int r = 0; r < 64; r += 2) {
-        a0 += Lc[k * 65 + r] * Xs[c * 64 + r];
-        a1 += Lc[k * 65 + r + 1] * Xs[c * 64 + r + 1];
+#pragma unroll 4
+    for (int r = 0; r < 64; ++r) {
+        const T l = Lc[k * 65 + r];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += l * Xs[(g + 4 * u) * 64 + r];
     }
-    return a0 + a1;
+}
+// Right-hand-side block of one pass: Vs[c * w + k] = V[f + k, c0 + c], zero past nc.
+template <typename T>
+__device__ __forceinline__ void stage_vec(T *Vs, const T *V, int64_t f, int w, int nc, int64_t n, int c0)
+{
+    for (int e = threadIdx.x; e < w * kQRhs; e += kQThreads) {
+        const int k = e % w, c = e / w;
+        Vs[c * w + k] = c < nc ? ld_l2(V + f + k + (int64_t)(c0 + c) * n) : (T)0;
+    }
 }
 
 }  // namespace
@@ -184,25 +191,26 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
             if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
-                for (int e = tid; e < w * nc; e += kQThreads) {
-                    const int k = e % w, c = e / w;
-                    vec[c * w + k] = ld_l2(Y + f + k + (int64_t)(c0 + c) * n);
-                }
+                stage_vec(vec, Y, f, w, nc, n, c0);
                 __syncthreads();
-                for (int e = tid; e < w * nc; e += kQThreads) {
-                    const int i = e % w, c = e / w;
-                    const T *yc = vec + c * w;
-                    T a0 = unit ? yc[i] : (T)0, a1 = (T)0;
+                // thread: row i, columns g, g + 4, g + 8, g + 12
+                for (int i = tid & 63, g = tid >> 6; i < w; i += 64) {
+                    T acc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[u] = unit ? vec[(g + 4 * u) * w + i] : (T)0;
                     const int kl = unit ? i : i + 1;
-                    int k = 0;
-                    for (; k + 1 < kl; k += 2) {
-                        a0 += matA[i + k * w] * yc[k];
-                        a1 += matA[i + (k + 1) * w] * yc[k + 1];
+#pragma unroll 4
+                    for (int k = 0; k < kl; ++k) {
+                        const T a = matA[i + k * w];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) acc[u] += a * vec[(g + 4 * u) * w + k];
                     }
-                    if (k < kl) a0 += matA[i + k * w] * yc[k];
-                    const T z = a0 + a1;
-                    Z[f + i + (int64_t)(c0 + c) * n] = z;
-                    if (mc >= 0) vec2[c * w + i] = z;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = g + 4 * u;
+                        if (c < nc) Z[f + i + (int64_t)(c0 + c) * n] = acc[u];
+                        if (mc >= 0) vec2[c * w + i] = acc[u];
+                    }
                 }
                 __syncthreads();
                 if (mc >= 0) fwd_chunk_pass(matB, vec2, w, nr, nc, p.rows + p.prow[pid] + w, Y, n, c0);
@@ -221,10 +229,7 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
             if (!cta_wait(q.flag + pid, nullptr, 1, 1, q.err)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
-                for (int e = tid; e < w * nc; e += kQThreads) {
-                    const int k = e % w, c = e / w;
-                    vec[c * w + k] = ld_l2(Z + f + k + (int64_t)(c0 + c) * n);
-                }
+                stage_vec(vec, Z, f, w, nc, n, c0);
                 __syncthreads();
                 fwd_chunk_pass(matA, vec, w, nr, nc, p.rows + p.prow[pid] + ch.r0, Y, n, c0);
                 __syncthreads();
@@ -298,25 +303,32 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
                     stage_rows(vec2, X, crows, nr, nc, n, c0);
                     __syncthreads();
                 }
-                for (int e = tid; e < w * nc; e += kQThreads) {
-                    const int k = e % w, c = e / w;
-                    const int64_t gk = f + k + (int64_t)(c0 + c) * n;
-                    T v = (lu == 2 ? Z[gk] * Mi[k + k * w] : Z[gk]) - ld_l2(Tacc + gk);
-                    if (mc >= 0) v -= chunk_dot(matB, vec2, k, c);
-                    vec[c * w + k] = v;
+                // vec = Z_p - Tacc_p - Lc^T X[rows] (LDL^T: D^{-1} Z_p - ...)
+                for (int k = tid & 63, g = tid >> 6; k < w; k += 64) {
+                    T part[4] = {(T)0, (T)0, (T)0, (T)0};
+                    if (mc >= 0) chunk_dot4(matB, vec2, k, g, part);
+                    const T dk = lu == 2 ? Mi[k + k * w] : (T)1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = g + 4 * u;
+                        const int64_t gk = f + k + (int64_t)(c0 + c) * n;
+                        vec[c * w + k] = c < nc ? (lu == 2 ? Z[gk] * dk : Z[gk]) - ld_l2(Tacc + gk) - part[u] : (T)0;
+                    }
                 }
                 __syncthreads();
-                for (int e = tid; e < w * nc; e += kQThreads) {
-                    const int i = e % w, c = e / w;
-                    const T *yc = vec + c * w;
-                    T a0 = (T)0, a1 = (T)0;
-                    int k = i;
-                    for (; k + 1 < w; k += 2) {
-                        a0 += matA[i + k * ld] * yc[k];
-                        a1 += matA[i + (k + 1) * ld] * yc[k + 1];
+                for (int i = tid & 63, g = tid >> 6; i < w; i += 64) {
+                    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll 4
+                    for (int k = i; k < w; ++k) {
+                        const T a = matA[i + k * ld];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) acc[u] += a * vec[(g + 4 * u) * w + k];
                     }
-                    if (k < w) a0 += matA[i + k * ld] * yc[k];
-                    X[f + i + (int64_t)(c0 + c) * n] = a0 + a1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = g + 4 * u;
+                        if (c < nc) X[f + i + (int64_t)(c0 + c) * n] = acc[u];
+                    }
                 }
                 __syncthreads();
             }
@@ -335,9 +347,14 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_rows(vec, X, p.rows + p.prow[pid] + ch.r0, nr, nc, n, c0);
                 __syncthreads();
-                for (int e = tid; e < w * nc; e += kQThreads) {
-                    const int k = e % w, c = e / w;
-                    atomicAdd(Tacc + f + k + (int64_t)(c0 + c) * n, chunk_dot(matA, vec, k, c));
+                for (int k = tid & 63, g = tid >> 6; k < w; k += 64) {
+                    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+                    chunk_dot4(matA, vec, k, g, acc);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = g + 4 * u;
+                        if (c < nc) atomicAdd(Tacc + f + k + (int64_t)(c0 + c) * n, acc[u]);
+                    }
                 }
                 __syncthreads();
             }
