@@ -393,8 +393,10 @@ spx_status ensure_device(spx_handle h)
             if (!ok) return fail(h, SPX_ERR_STATE, "internal: sweep queue order violates a dependency");
         }
         h->q_nitems = (int32_t)itf.size();
-        h->q_mat = wmax * std::max(wmax + 1, 65);
-        h->q_matb = merge ? 65 * wmax : 0;
+        // staging sizes in elements, multiples of 4 so that the vectors
+        // after the matrices stay aligned for 4-element vector accesses
+        h->q_mat = (wmax * std::max(wmax + 1, 65) + 3) & ~3;
+        h->q_matb = merge ? (65 * wmax + 3) & ~3 : 0;
         h->q_vec = 16 * std::max(wmax, 64);
         if ((st = upload(h, &h->d_qitems_f, itf)) || (st = upload(h, &h->d_qitems_b, itb)) ||
             (st = upload(h, &h->d_qtptr, tptr)) || (st = upload(h, &h->d_qtgt, tgt)) ||

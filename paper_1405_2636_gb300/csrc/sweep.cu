@@ -71,12 +71,13 @@ __device__ __forceinline__ bool cta_wait(const int32_t *cnt, const int32_t *ids,
 
 // Whole CTA, after its writes: they become visible before flag[0] = 1 and
 // before each cnt[ids[t]] (t < m; ids == nullptr: cnt[0]) is incremented
-// (barrier, then one gpu-scope fence by the signalling thread).
+// (barrier, then one gpu-scope acquire-release fence by the signalling
+// thread, which covers the writes the barrier ordered before it).
 __device__ __forceinline__ void cta_release(int32_t *flag, int32_t *cnt, const int32_t *ids, int m)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (flag) atomicExch(flag, 1);
         for (int t = 0; t < m; ++t) atomicAdd(cnt + (ids ? ids[t] : 0), 1);
     }
@@ -93,57 +94,94 @@ __device__ __forceinline__ void stage_chunk(T *dst, int ld, const T *Pn, int h, 
     }
 }
 
-// Y[rows[r]] -= sum_k Lc(r, k) Zs(k, c): Lc staged [k * 64 + r], Zs[c * w + k]
-// (kQRhs columns, zero past nc).  Thread: row r, columns g, g + 4, ...
-template <typename T>
-__device__ __forceinline__ void fwd_chunk_pass(const T *Lc, const T *Zs, int w, int nr, int nc,
-                                               const int32_t *crows, T *Y, int64_t n, int c0)
+// Right-hand-side blocks in shared memory hold kQRhs columns per row, the
+// four column quads of row k in the order q ^ ((k >> 1) & 3): a thread
+// reads its quad of one row with one vector load (the same address across
+// a warp), and the column-wise staging stores spread over eight banks.
+__device__ __forceinline__ int vslot(int k, int c)
 {
-    const int r = threadIdx.x & 63, g = threadIdx.x >> 6;   // 64 rows x 4 column groups
-    if (r >= nr) return;
-    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-        const T l = Lc[k * 64 + r];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] += l * Zs[(g + 4 * u) * w + k];
+    return k * kQRhs + ((((c >> 2) ^ (k >> 1)) & 3) << 2) + (c & 3);
+}
+template <typename T>
+__device__ __forceinline__ void ld_quad(const T *Vs, int k, int g, T (&v)[4])
+{
+    const T *p = Vs + vslot(k, 4 * g);
+    if constexpr (sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else {
+        const double2 x = *reinterpret_cast<const double2 *>(p);
+        const double2 y = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
     }
-    const int64_t gi = crows[r];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int c = g + 4 * u;
-        if (c < nc) atomicAdd(Y + gi + (int64_t)(c0 + c) * n, -acc[u]);
+}
+template <typename T>
+__device__ __forceinline__ void st_quad(T *Vs, int k, int g, const T (&v)[4])
+{
+    T *p = Vs + vslot(k, 4 * g);
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
     }
 }
 
-// Xs[c * 64 + r] = X[rows[r]] for one pass (kQRhs columns, zero past nc).
-template <typename T>
-__device__ __forceinline__ void stage_rows(T *Xs, const T *X, const int32_t *crows, int nr, int nc,
-                                           int64_t n, int c0)
-{
-    for (int e = threadIdx.x; e < 64 * kQRhs; e += kQThreads) {
-        const int r = e & 63, c = e >> 6;
-        Xs[c * 64 + r] = (r < nr && c < nc) ? ld_l2(X + crows[r] + (int64_t)(c0 + c) * n) : (T)0;
-    }
-}
-// acc[u] += sum over r of Lc(r, k) Xs(r, g + 4u), Lc staged [k * 65 + r].
-template <typename T>
-__device__ __forceinline__ void chunk_dot4(const T *Lc, const T *Xs, int k, int g, T acc[4])
-{
-#pragma unroll 4
-    for (int r = 0; r < 64; ++r) {
-        const T l = Lc[k * 65 + r];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] += l * Xs[(g + 4 * u) * 64 + r];
-    }
-}
-// Right-hand-side block of one pass: Vs[c * w + k] = V[f + k, c0 + c], zero past nc.
+// Vs(k, c) = V[f + k, c0 + c] for k < w (zero past nc), read through L2.
 template <typename T>
 __device__ __forceinline__ void stage_vec(T *Vs, const T *V, int64_t f, int w, int nc, int64_t n, int c0)
 {
     for (int e = threadIdx.x; e < w * kQRhs; e += kQThreads) {
         const int k = e % w, c = e / w;
-        Vs[c * w + k] = c < nc ? ld_l2(V + f + k + (int64_t)(c0 + c) * n) : (T)0;
+        Vs[vslot(k, c)] = c < nc ? ld_l2(V + f + k + (int64_t)(c0 + c) * n) : (T)0;
+    }
+}
+
+// Xs(r, c) = X[row_r, c0 + c] (r < 64, zero past nr or nc); the thread's
+// rows are all r = tid & 63, whose index `row` it loaded beforehand.
+template <typename T>
+__device__ __forceinline__ void stage_rows(T *Xs, const T *X, int64_t row, int nr, int nc, int64_t n, int c0)
+{
+    const int r = threadIdx.x & 63;
+    for (int c = threadIdx.x >> 6; c < kQRhs; c += kQThreads / 64)
+        Xs[vslot(r, c)] = (r < nr && c < nc) ? ld_l2(X + row + (int64_t)(c0 + c) * n) : (T)0;
+}
+
+// Y[row_r, c0 + 4g + u] -= sum_k Lc(r, k) Zs(k, 4g + u) for thread (r, g) =
+// (tid & 63, tid >> 6); Lc staged [k * 64 + r].
+template <typename T>
+__device__ __forceinline__ void fwd_chunk_pass(const T *Lc, const T *Zs, int w, int nr, int nc, int64_t row,
+                                               T *Y, int64_t n, int c0)
+{
+    const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
+    if (r >= nr) return;
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+        const T l = Lc[k * 64 + r];
+        T z[4];
+        ld_quad(Zs, k, g, z);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += l * z[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = 4 * g + u;
+        if (c < nc) atomicAdd(Y + row + (int64_t)(c0 + c) * n, -acc[u]);
+    }
+}
+
+// acc[u] += sum over r of Lc(r, k) Xs(r, 4g + u), Lc staged [k * 65 + r].
+template <typename T>
+__device__ __forceinline__ void chunk_dot4(const T *Lc, const T *Xs, int k, int g, T (&acc)[4])
+{
+#pragma unroll 4
+    for (int r = 0; r < 64; ++r) {
+        const T l = Lc[k * 65 + r];
+        T x[4];
+        ld_quad(Xs, r, g, x);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += l * x[u];
     }
 }
 
@@ -152,19 +190,20 @@ __device__ __forceinline__ void stage_vec(T *Vs, const T *V, int64_t f, int w, i
 // Shared memory: A (q.mat_elems: a diagonal block, or a chunk), B
 // (q.matb_elems: the chunk a panel item takes along), a vector of
 // q.vec_elems and, when panel items take chunks along, a second one.
+// Threads work as (row, column quad) = (tid & 63, tid >> 6).
 template <typename T>
 __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, SweepQueue q,
                                                               const RowChunk *__restrict__ chunks,
                                                               const T *__restrict__ Dinv, int unit,
                                                               const T *__restrict__ L, T *Y, T *Z, int nrhs)
 {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     T *matA = reinterpret_cast<T *>(smraw);
     T *matB = matA + q.mat_elems;
     T *vec = matB + q.matb_elems;
     T *vec2 = vec + q.vec_elems;
     __shared__ int s_next;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, rt = tid & 63, g = tid >> 6;
     const int64_t n = p.n;
     if (tid == 0) s_next = atomicAdd(q.head, 1);
     __syncthreads();
@@ -184,37 +223,42 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
             const int mc = q.merge[pid];
             for (int e = tid; e < w * w; e += kQThreads) matA[e] = Mi[e];   // column-major, ld w
             int nr = 0;
+            int64_t row = 0;
             if (mc >= 0) {
                 nr = min(64, h - w);
                 stage_chunk(matB, 64, L + p.pval[pid], h, w, w, nr);
+                if (rt < nr) row = p.rows[p.prow[pid] + w + rt];
             }
             if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_vec(vec, Y, f, w, nc, n, c0);
                 __syncthreads();
-                // thread: row i, columns g, g + 4, g + 8, g + 12
-                for (int i = tid & 63, g = tid >> 6; i < w; i += 64) {
+                for (int i = rt; i < w; i += 64) {
                     T acc[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) acc[u] = unit ? vec[(g + 4 * u) * w + i] : (T)0;
+                    if (unit) ld_quad(vec, i, g, acc);
+                    else acc[0] = acc[1] = acc[2] = acc[3] = (T)0;
                     const int kl = unit ? i : i + 1;
 #pragma unroll 4
                     for (int k = 0; k < kl; ++k) {
                         const T a = matA[i + k * w];
+                        T y[4];
+                        ld_quad(vec, k, g, y);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) acc[u] += a * vec[(g + 4 * u) * w + k];
+                        for (int u = 0; u < 4; ++u) acc[u] += a * y[u];
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int c = g + 4 * u;
+                        const int c = 4 * g + u;
                         if (c < nc) Z[f + i + (int64_t)(c0 + c) * n] = acc[u];
-                        if (mc >= 0) vec2[c * w + i] = acc[u];
                     }
+                    if (mc >= 0) st_quad(vec2, i, g, acc);
                 }
                 __syncthreads();
-                if (mc >= 0) fwd_chunk_pass(matB, vec2, w, nr, nc, p.rows + p.prow[pid] + w, Y, n, c0);
-                __syncthreads();
+                if (mc >= 0) {
+                    fwd_chunk_pass(matB, vec2, w, nr, nc, row, Y, n, c0);
+                    __syncthreads();
+                }
             }
             const int t0 = mc >= 0 ? q.tptr[mc] : 0, t1 = mc >= 0 ? q.tptr[mc + 1] : 0;
             cta_release(q.flag + pid, q.cnt, q.tgt + t0, t1 - t0);
@@ -226,12 +270,13 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
             const int64_t f = p.pfcol[pid];
             const int nr = min(64, h - ch.r0);
             stage_chunk(matA, 64, L + p.pval[pid], h, w, ch.r0, nr);
+            const int64_t row = rt < nr ? p.rows[p.prow[pid] + ch.r0 + rt] : 0;
             if (!cta_wait(q.flag + pid, nullptr, 1, 1, q.err)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_vec(vec, Z, f, w, nc, n, c0);
                 __syncthreads();
-                fwd_chunk_pass(matA, vec, w, nr, nc, p.rows + p.prow[pid] + ch.r0, Y, n, c0);
+                fwd_chunk_pass(matA, vec, w, nr, nc, row, Y, n, c0);
                 __syncthreads();
             }
             const int t0 = q.tptr[item], t1 = q.tptr[item + 1];
@@ -250,13 +295,13 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
                                                               const T *__restrict__ Z, T *Tacc, T *X,
                                                               int nrhs)
 {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     T *matA = reinterpret_cast<T *>(smraw);
     T *matB = matA + q.mat_elems;
     T *vec = matB + q.matb_elems;
     T *vec2 = vec + q.vec_elems;
     __shared__ int s_next;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, rt = tid & 63, g = tid >> 6;
     const int64_t n = p.n;
     if (tid == 0) s_next = atomicAdd(q.head, 1);
     __syncthreads();
@@ -288,49 +333,76 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
                 }
                 matA[i + k * ld] = k >= i ? v : (T)0;
             }
-            int nr = 0;
-            const int32_t *crows = p.rows + p.prow[pid] + w;
+            int nr = 0, t0 = 0, m = 0;
+            int64_t row = 0;
             if (mc >= 0) {
                 nr = min(64, h - w);
                 stage_chunk(matB, 65, Lop + p.pval[pid], h, w, w, nr);
-                const int t0 = q.tptr[mc], t1 = q.tptr[mc + 1];
-                if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err)) return;
+                if (rt < nr) row = p.rows[p.prow[pid] + w + rt];
+                t0 = q.tptr[mc];
+                m = q.tptr[mc + 1] - t0;
             }
-            if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err)) return;
+            // the first pass's Z_p (LDL^T: D^{-1} Z_p) is fixed: staged
+            // before the wait, Tacc_p subtracted after it by the same threads
+            const int nc0 = min(kQRhs, nrhs);
+            for (int e = tid; e < w * kQRhs; e += kQThreads) {
+                const int k = e % w, c = e / w;
+                const int64_t gk = f + k + (int64_t)c * n;
+                vec[vslot(k, c)] = c < nc0 ? (lu == 2 ? Z[gk] * Mi[k + k * w] : Z[gk]) : (T)0;
+            }
+            // one wait: threads < m on the panels owning the chunk's rows,
+            // thread m on the panel's own chunks
+            {
+                int ok = 1;
+                if (tid < m) ok = wait_geq(q.flag + q.tgt[t0 + tid], 1, q.err);
+                else if (tid == m) ok = wait_geq(q.cnt + pid, q.need[pid], q.err);
+                if (!__syncthreads_and(ok)) return;
+            }
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
-                if (mc >= 0) {
-                    stage_rows(vec2, X, crows, nr, nc, n, c0);
+                if (c0 > 0) {
                     __syncthreads();
-                }
-                // vec = Z_p - Tacc_p - Lc^T X[rows] (LDL^T: D^{-1} Z_p - ...)
-                for (int k = tid & 63, g = tid >> 6; k < w; k += 64) {
-                    T part[4] = {(T)0, (T)0, (T)0, (T)0};
-                    if (mc >= 0) chunk_dot4(matB, vec2, k, g, part);
-                    const T dk = lu == 2 ? Mi[k + k * w] : (T)1;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int c = g + 4 * u;
+                    for (int e = tid; e < w * kQRhs; e += kQThreads) {
+                        const int k = e % w, c = e / w;
                         const int64_t gk = f + k + (int64_t)(c0 + c) * n;
-                        vec[c * w + k] = c < nc ? (lu == 2 ? Z[gk] * dk : Z[gk]) - ld_l2(Tacc + gk) - part[u] : (T)0;
+                        vec[vslot(k, c)] = c < nc ? (lu == 2 ? Z[gk] * Mi[k + k * w] : Z[gk]) : (T)0;
                     }
                 }
+                // vec -= Tacc_p, loaded with the chunk's rows of X
+                if (mc >= 0) stage_rows(vec2, X, row, nr, nc, n, c0);
+                for (int e = tid; e < w * kQRhs; e += kQThreads) {
+                    const int k = e % w, c = e / w;
+                    if (c < nc) vec[vslot(k, c)] -= ld_l2(Tacc + f + k + (int64_t)(c0 + c) * n);
+                }
                 __syncthreads();
-                for (int i = tid & 63, g = tid >> 6; i < w; i += 64) {
+                if (mc >= 0) {   // vec -= Lc^T X[rows]
+                    for (int k = rt; k < w; k += 64) {
+                        T part[4] = {(T)0, (T)0, (T)0, (T)0};
+                        chunk_dot4(matB, vec2, k, g, part);
+                        T v[4];
+                        ld_quad(vec, k, g, v);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v[u] -= part[u];
+                        st_quad(vec, k, g, v);
+                    }
+                    __syncthreads();
+                }
+                for (int i = rt; i < w; i += 64) {
                     T acc[4] = {(T)0, (T)0, (T)0, (T)0};
 #pragma unroll 4
                     for (int k = i; k < w; ++k) {
                         const T a = matA[i + k * ld];
+                        T v[4];
+                        ld_quad(vec, k, g, v);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) acc[u] += a * vec[(g + 4 * u) * w + k];
+                        for (int u = 0; u < 4; ++u) acc[u] += a * v[u];
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int c = g + 4 * u;
+                        const int c = 4 * g + u;
                         if (c < nc) X[f + i + (int64_t)(c0 + c) * n] = acc[u];
                     }
                 }
-                __syncthreads();
             }
             cta_release(q.flag + pid, nullptr, nullptr, 0);
         } else {
@@ -341,18 +413,19 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
             const int64_t f = p.pfcol[pid];
             const int nr = min(64, h - ch.r0);
             stage_chunk(matA, 65, Lop + p.pval[pid], h, w, ch.r0, nr);
+            const int64_t row = rt < nr ? p.rows[p.prow[pid] + ch.r0 + rt] : 0;
             const int t0 = q.tptr[item], t1 = q.tptr[item + 1];
             if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
-                stage_rows(vec, X, p.rows + p.prow[pid] + ch.r0, nr, nc, n, c0);
+                stage_rows(vec, X, row, nr, nc, n, c0);
                 __syncthreads();
-                for (int k = tid & 63, g = tid >> 6; k < w; k += 64) {
+                for (int k = rt; k < w; k += 64) {
                     T acc[4] = {(T)0, (T)0, (T)0, (T)0};
                     chunk_dot4(matA, vec, k, g, acc);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int c = g + 4 * u;
+                        const int c = 4 * g + u;
                         if (c < nc) atomicAdd(Tacc + f + k + (int64_t)(c0 + c) * n, acc[u]);
                     }
                 }
