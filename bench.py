@@ -528,6 +528,7 @@ def main():
             sinfo_h = {"backward_error": float("nan")}
         results[mode] = {
             "ms_per_step": ms,
+            "step_ms": [round(t, 3) for t in times],
             "factor_ms": info["factor_ms"],
             "solve_ms": info["solve_ms"],
             "factor_gflops": flops / (info["factor_ms"] / 1e3) / 1e9,
