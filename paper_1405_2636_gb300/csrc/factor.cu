@@ -824,8 +824,11 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
 //   LU_L: B = U^{-1}           (B(k,j) = Uinv(k,j))
 //   LU_U: B = L^{-T}, unit L   (B(k,j) = Linv(j,k), 1 on the diagonal)
 //   RIGHT_LINV: B = L^{-1}     (B(k,j) = Linv(k,j); the selected inversion's L_RJ L_JJ^{-1})
-// The CTA copies its rows to shared memory first, so writing them back in
-// place is safe; 64 x 64 output tiles, 4 x 4 per thread, K-chunks of 16.
+// The CTA copies its rows and the whole B operand of a 64-column tile to
+// shared memory first (every load of a batch issued before its stores), so
+// writing the rows back in place is safe and the K loop runs without
+// barriers; 64 x 64 output tiles, 4 x 4 per thread, written back through
+// shared memory in whole segments.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float round_tf32(float x)
 {
@@ -841,57 +844,73 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                                                         void *opc_lo, int kpad, int op_kind,
                                                         T *__restrict__ Wout)
 {
+    constexpr int NB = 16;                     // loads in flight per thread while staging
     extern __shared__ unsigned char smraw[];
-    T *Xs = reinterpret_cast<T *>(smraw);      // Xs[k * 64 + r], k < wpad
-    __shared__ T Bs[16][kUpdTile + 1];
     const RowChunk ch = chunks[blockIdx.x];
     const int pid = ch.panel;
     const int w = p.pw[pid], h = p.ph[pid];
     const int wpad = (w + 15) & ~15;
+    T *Xs = reinterpret_cast<T *>(smraw);      // Xs[k * 64 + r], k < wpad
+    T *Bf = Xs + wpad * kTrsmRows;             // Bf[k * 65 + j], k < max(wpad, 64); then the output tile
     const T *Mi = Dinv + p.pinv[pid];
     T *Xg = X + p.pval[pid] + ch.r0;
     const int nr = min(kTrsmRows, h - ch.r0);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    for (int e = tid; e < wpad * kTrsmRows; e += 256) {
-        const int r = e & 63, k = e >> 6;
-        Xs[e] = (r < nr && k < w) ? Xg[r + (int64_t)k * h] : (T)0;
+    // B(k, j) of the product X B (see the table above)
+    auto bval = [&](int k, int j) -> T {
+        if (k >= w || j >= w) return (T)0;
+        if (mode == TRSM_RIGHT_LINV) return k >= j ? Mi[k + j * w] : (T)0;
+        if (mode == TRSM_LU_L) return k <= j ? Mi[k + j * w] : (T)0;
+        if (j > k) return Mi[j + k * w];
+        if (j == k) return (mode == TRSM_LU_U || mode == TRSM_LDLT) ? (T)1 : Mi[j + k * w];
+        return (T)0;
+    };
+    // the chunk's rows, every load of a batch issued before its stores
+    for (int base = tid; base < wpad * kTrsmRows; base += 256 * NB) {
+        T v[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + 256 * q, r = e & 63, k = e >> 6;
+            v[q] = (e < wpad * kTrsmRows && r < nr && k < w) ? Xg[r + (int64_t)k * h] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + 256 * q;
+            if (e < wpad * kTrsmRows) Xs[e] = v[q];
+        }
     }
-    __syncthreads();
     for (int c0 = 0; c0 < w; c0 += kUpdTile) {
+        if (c0 > 0) __syncthreads();           // the previous tile is out of Bf
+        for (int base = tid; base < wpad * kUpdTile; base += 256 * NB) {
+            T v[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int e = base + 256 * q;
+                v[q] = e < wpad * kUpdTile ? bval(e >> 6, c0 + (e & 63)) : (T)0;
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int e = base + 256 * q;
+                if (e < wpad * kUpdTile) Bf[(e >> 6) * (kUpdTile + 1) + (e & 63)] = v[q];
+            }
+        }
+        __syncthreads();
         T acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-        for (int k0 = 0; k0 < wpad; k0 += 16) {
+#pragma unroll 4
+        for (int k = 0; k < wpad; ++k) {
+            T av[4], bv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = tid + 256 * q;
-                const int kk = e >> 6, jj = e & 63;
-                const int k = k0 + kk, j = c0 + jj;
-                T v = (T)0;
-                if (k < w && j < w) {
-                    if (mode == TRSM_RIGHT_LINV) v = (k >= j) ? Mi[k + j * w] : (T)0;
-                    else if (mode == TRSM_LU_L) v = (k <= j) ? Mi[k + j * w] : (T)0;
-                    else if (j > k) v = Mi[j + k * w];
-                    else if (j == k) v = (mode == TRSM_LU_U || mode == TRSM_LDLT) ? (T)1 : Mi[j + k * w];
-                }
-                Bs[kk][jj] = v;
-            }
-            __syncthreads();
+            for (int a = 0; a < 4; ++a) av[a] = Xs[k * 64 + tx + 16 * a];
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                T av[4], bv[4];
+            for (int b = 0; b < 4; ++b) bv[b] = Bf[k * (kUpdTile + 1) + ty + 16 * b];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) av[a] = Xs[(k0 + kk) * 64 + tx + 16 * a];
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-            }
-            __syncthreads();
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
         }
         if (mode == TRSM_LDLT) {
             // acc = X l^{-T} is the D L^T buffer row (Sec. V-B: the update then
@@ -922,45 +941,46 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
             }
             continue;
         }
+        // the 64 x 64 result tile through shared memory, so that both the
+        // column-major panel and the row-major operand copy are written in
+        // whole segments
+        __syncthreads();                       // every read of Bf is done
+        T *Ot = Bf;                            // Ot[r * 65 + jj]
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int r = tx + 16 * a;
-            if (r >= nr) continue;
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int j = c0 + ty + 16 * b;
-                if (j < w) Xg[r + (int64_t)j * h] = acc[a][b];
-            }
+            for (int b = 0; b < 4; ++b) Ot[(tx + 16 * a) * (kUpdTile + 1) + ty + 16 * b] = acc[a][b];
+        __syncthreads();
+        const int nc = min(kUpdTile, w - c0);
+        for (int e = tid; e < nc * kTrsmRows; e += 256) {
+            const int r = e & 63, jj = e >> 6;
+            if (r < nr) Xg[r + (int64_t)(c0 + jj) * h] = Ot[r * (kUpdTile + 1) + jj];
         }
         if (opc) {
-            // the same rows, K-major, for the tensor-core updates
+            // the same rows, K-major, for the tensor-core updates; columns
+            // w .. c0+63 of the tile are zero and fill the row's padding
             const int64_t orow0 = p.prow[pid] + ch.r0;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int r = tx + 16 * a;
-                if (r >= nr) continue;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int j = c0 + ty + 16 * b;
-                    if (j >= w) continue;
-                    const int64_t o = (orow0 + r) * kpad + j;
-                    const float v = (float)acc[a][b];
-                    if (op_kind == 1) {
-                        reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(v);
-                    } else {
-                        const float hi = round_tf32(v);
-                        reinterpret_cast<float *>(opc)[o] = hi;
-                        if (op_kind == 2) reinterpret_cast<float *>(opc_lo)[o] = round_tf32(v - hi);
-                    }
+            for (int e = tid; e < nr * kUpdTile; e += 256) {
+                const int r = e >> 6, jj = e & 63;
+                const int64_t o = (orow0 + r) * kpad + c0 + jj;
+                const float v = (float)Ot[r * (kUpdTile + 1) + jj];
+                if (op_kind == 1) {
+                    reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(v);
+                } else {
+                    const float hi = round_tf32(v);
+                    reinterpret_cast<float *>(opc)[o] = hi;
+                    if (op_kind == 2) reinterpret_cast<float *>(opc_lo)[o] = round_tf32(v - hi);
                 }
             }
         }
     }
     if (opc) {
+        // the rest of each operand row's padding
         const int64_t orow0 = p.prow[pid] + ch.r0;
-        const int padw = kpad - w;
+        const int j0 = mode == TRSM_LDLT ? w : (w + kUpdTile - 1) / kUpdTile * kUpdTile;
+        const int padw = kpad - j0;
         for (int e = tid; e < nr * padw; e += 256) {
-            const int r = e / padw, j = w + e % padw;
+            const int r = e / padw, j = j0 + e % padw;
             const int64_t o = (orow0 + r) * kpad + j;
             if (op_kind == 1 || op_kind == 4) {
                 reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(0.0f);
@@ -974,6 +994,12 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
 }
 
 template <typename T>
+constexpr size_t trsm_smem_bytes(int wpad)
+{
+    return sizeof(T) * ((size_t)wpad * kTrsmRows + (size_t)(wpad > kUpdTile ? wpad : kUpdTile) * (kUpdTile + 1));
+}
+
+template <typename T>
 void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, const T *Dinv,
                  T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s, T *Wout)
 {
@@ -981,10 +1007,10 @@ void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, 
     static bool once = false;
     if (!once) {
         cudaFuncSetAttribute(trsm_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(T) * kMaxWidth * kTrsmRows));
+                             (int)trsm_smem_bytes<T>((kMaxWidth + 15) & ~15));
         once = true;
     }
-    const size_t smem = sizeof(T) * (size_t)((wmax + 15) & ~15) * kTrsmRows;
+    const size_t smem = trsm_smem_bytes<T>((wmax + 15) & ~15);
     trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, opc_lo, kpad, op_kind, Wout);
 }
 
