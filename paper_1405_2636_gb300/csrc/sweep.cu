@@ -83,14 +83,49 @@ __device__ __forceinline__ void cta_release(int32_t *flag, int32_t *cnt, const i
     }
 }
 
+// The staging loops below issue every load of a batch before its first
+// store, so that a thread's global loads overlap instead of each waiting
+// for the previous one.
+
 // Rows [r0, r0 + 64) of a panel's off-diagonal block to dst[k * ld + r]
 // (rows past the panel as zeros).
 template <typename T>
 __device__ __forceinline__ void stage_chunk(T *dst, int ld, const T *Pn, int h, int w, int r0, int nr)
 {
-    for (int e = threadIdx.x; e < w * 64; e += kQThreads) {
-        const int r = e & 63, k = e >> 6;
-        dst[k * ld + r] = r < nr ? Pn[r0 + r + (int64_t)k * h] : (T)0;
+    constexpr int NB = 8;
+    const int total = w * 64;
+    for (int base = threadIdx.x; base < total; base += kQThreads * NB) {
+        T v[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + q * kQThreads, r = e & 63, k = e >> 6;
+            v[q] = (e < total && r < nr) ? Pn[r0 + r + (int64_t)k * h] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + q * kQThreads;
+            if (e < total) dst[(e >> 6) * ld + (e & 63)] = v[q];
+        }
+    }
+}
+
+// dst[e] = src[e], e < total (a diagonal block's inverse, column-major).
+template <typename T>
+__device__ __forceinline__ void stage_copy(T *dst, const T *src, int total)
+{
+    constexpr int NB = 8;
+    for (int base = threadIdx.x; base < total; base += kQThreads * NB) {
+        T v[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + q * kQThreads;
+            v[q] = e < total ? src[e] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + q * kQThreads;
+            if (e < total) dst[e] = v[q];
+        }
     }
 }
 
@@ -131,9 +166,20 @@ __device__ __forceinline__ void st_quad(T *Vs, int k, int g, const T (&v)[4])
 template <typename T>
 __device__ __forceinline__ void stage_vec(T *Vs, const T *V, int64_t f, int w, int nc, int64_t n, int c0)
 {
-    for (int e = threadIdx.x; e < w * kQRhs; e += kQThreads) {
-        const int k = e % w, c = e / w;
-        Vs[vslot(k, c)] = c < nc ? ld_l2(V + f + k + (int64_t)(c0 + c) * n) : (T)0;
+    constexpr int NB = 4;
+    const int total = w * kQRhs;
+    for (int base = threadIdx.x; base < total; base += kQThreads * NB) {
+        T v[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + q * kQThreads, k = e % w, c = e / w;
+            v[q] = (e < total && c < nc) ? ld_l2(V + f + k + (int64_t)(c0 + c) * n) : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = base + q * kQThreads;
+            if (e < total) Vs[vslot(e % w, e / w)] = v[q];
+        }
     }
 }
 
@@ -142,9 +188,16 @@ __device__ __forceinline__ void stage_vec(T *Vs, const T *V, int64_t f, int w, i
 template <typename T>
 __device__ __forceinline__ void stage_rows(T *Xs, const T *X, int64_t row, int nr, int nc, int64_t n, int c0)
 {
-    const int r = threadIdx.x & 63;
-    for (int c = threadIdx.x >> 6; c < kQRhs; c += kQThreads / 64)
-        Xs[vslot(r, c)] = (r < nr && c < nc) ? ld_l2(X + row + (int64_t)(c0 + c) * n) : (T)0;
+    constexpr int NC = kQRhs / (kQThreads / 64);   // columns per thread
+    const int r = threadIdx.x & 63, cf = threadIdx.x >> 6;
+    T v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const int c = cf + q * (kQThreads / 64);
+        v[q] = (r < nr && c < nc) ? ld_l2(X + row + (int64_t)(c0 + c) * n) : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) Xs[vslot(r, cf + q * (kQThreads / 64))] = v[q];
 }
 
 // Y[row_r, c0 + 4g + u] -= sum_k Lc(r, k) Zs(k, 4g + u) for thread (r, g) =
@@ -221,7 +274,7 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
             const int64_t f = p.pfcol[pid];
             const T *Mi = Dinv + p.pinv[pid];
             const int mc = q.merge[pid];
-            for (int e = tid; e < w * w; e += kQThreads) matA[e] = Mi[e];   // column-major, ld w
+            stage_copy(matA, Mi, w * w);   // column-major, ld w
             int nr = 0;
             int64_t row = 0;
             if (mc >= 0) {
@@ -318,20 +371,25 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
             const int64_t f = p.pfcol[pid];
             const T *Mi = Dinv + p.pinv[pid];
             const int mc = q.merge[pid];
-            // matA[i + k ld] = M(i, k), k >= i
-            for (int e = tid; e < w * w; e += kQThreads) {
-                int i, k;
-                T v;
-                if (lu == 1) {
-                    i = e % w;
-                    k = e / w;
-                    v = Mi[i + k * w];
-                } else {
-                    k = e % w;
-                    i = e / w;
-                    v = (lu == 2 && k == i) ? (T)1 : Mi[k + i * w];
+            // matA[i + k ld] = M(i, k), k >= i; source element e read in order
+            for (int base = tid; base < w * w; base += kQThreads * 8) {
+                T v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int e = base + q * kQThreads;
+                    v[q] = e < w * w ? Mi[e] : (T)0;
                 }
-                matA[i + k * ld] = k >= i ? v : (T)0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int e = base + q * kQThreads;
+                    if (e >= w * w) continue;
+                    // Mi[e] is M(i, k) with (i, k) = (e % w, e / w) (LU: U^{-1}),
+                    // else M(i, k) = Linv(k, i) with (k, i) = (e % w, e / w)
+                    const int a0 = e % w, a1 = e / w;
+                    const int i = lu == 1 ? a0 : a1, k = lu == 1 ? a1 : a0;
+                    const T val = (lu == 2 && k == i) ? (T)1 : v[q];
+                    matA[i + k * ld] = k >= i ? val : (T)0;
+                }
             }
             int nr = 0, t0 = 0, m = 0;
             int64_t row = 0;
@@ -345,10 +403,20 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
             // the first pass's Z_p (LDL^T: D^{-1} Z_p) is fixed: staged
             // before the wait, Tacc_p subtracted after it by the same threads
             const int nc0 = min(kQRhs, nrhs);
-            for (int e = tid; e < w * kQRhs; e += kQThreads) {
-                const int k = e % w, c = e / w;
-                const int64_t gk = f + k + (int64_t)c * n;
-                vec[vslot(k, c)] = c < nc0 ? (lu == 2 ? Z[gk] * Mi[k + k * w] : Z[gk]) : (T)0;
+            for (int base = tid; base < w * kQRhs; base += kQThreads * 4) {
+                T v[4], dg[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = base + q * kQThreads, k = e % w, c = e / w;
+                    const bool ok = e < w * kQRhs && c < nc0;
+                    v[q] = ok ? Z[f + k + (int64_t)c * n] : (T)0;
+                    dg[q] = (ok && lu == 2) ? Mi[k + k * w] : (T)1;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = base + q * kQThreads;
+                    if (e < w * kQRhs) vec[vslot(e % w, e / w)] = lu == 2 ? v[q] * dg[q] : v[q];
+                }
             }
             // one wait: threads < m on the panels owning the chunk's rows,
             // thread m on the panel's own chunks
@@ -370,9 +438,18 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
                 }
                 // vec -= Tacc_p, loaded with the chunk's rows of X
                 if (mc >= 0) stage_rows(vec2, X, row, nr, nc, n, c0);
-                for (int e = tid; e < w * kQRhs; e += kQThreads) {
-                    const int k = e % w, c = e / w;
-                    if (c < nc) vec[vslot(k, c)] -= ld_l2(Tacc + f + k + (int64_t)(c0 + c) * n);
+                for (int base = tid; base < w * kQRhs; base += kQThreads * 4) {
+                    T t[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int e = base + q * kQThreads, k = e % w, c = e / w;
+                        t[q] = (e < w * kQRhs && c < nc) ? ld_l2(Tacc + f + k + (int64_t)(c0 + c) * n) : (T)0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int e = base + q * kQThreads;
+                        if (e < w * kQRhs && e / w < nc) vec[vslot(e % w, e / w)] -= t[q];
+                    }
                 }
                 __syncthreads();
                 if (mc >= 0) {   // vec -= Lc^T X[rows]
