@@ -65,6 +65,15 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *a, double 
     atomicMax(a, (unsigned long long)__double_as_longlong(nan_to_inf(v)));
 }
 
+// |v| as bits, NaN as +inf: for non-negative doubles the order of the bit
+// patterns is the numeric order, so the norms reduce with integer maxima
+// (FP64 comparisons would run on this part's slow FP64 pipe).
+__device__ __forceinline__ unsigned long long abs_bits_inf(double v)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    return u > 0x7FF0000000000000ull ? 0x7FF0000000000000ull : u;
+}
+
 __global__ void __launch_bounds__(256) residual_kernel(int64_t n, int nrhs,
                                                        const int64_t *__restrict__ rp,
                                                        const int32_t *__restrict__ ci,
@@ -77,28 +86,29 @@ __global__ void __launch_bounds__(256) residual_kernel(int64_t n, int nrhs,
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    const int64_t e0 = i < n ? rp[i] : 0, e1 = i < n ? rp[i + 1] : 0;
     for (int c = 0; c < nrhs; ++c) {
-        double r = 0.0, ax = 0.0, ab = 0.0;
+        unsigned long long r = 0, ax = 0, ab = 0;
         if (i < n) {
             double s = 0.0;
-            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) s += vals[src[e]] * X[ci[e] + c * ldx];
+            for (int64_t e = e0; e < e1; ++e) s += vals[src[e]] * X[ci[e] + c * ldx];
             const double b = B[i + c * ldb];
-            r = b - s;
-            R[i + c * n] = r;
-            r = nan_to_inf(fabs(r));
-            ax = nan_to_inf(fabs(X[i + c * ldx]));
-            ab = nan_to_inf(fabs(b));
+            const double rr = b - s;
+            R[i + c * n] = rr;
+            r = abs_bits_inf(rr);
+            ax = abs_bits_inf(X[i + c * ldx]);
+            ab = abs_bits_inf(b);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
-            ax = fmax(ax, __shfl_down_sync(0xffffffffu, ax, o));
-            ab = fmax(ab, __shfl_down_sync(0xffffffffu, ab, o));
+            r = max(r, __shfl_down_sync(0xffffffffu, r, o));
+            ax = max(ax, __shfl_down_sync(0xffffffffu, ax, o));
+            ab = max(ab, __shfl_down_sync(0xffffffffu, ab, o));
         }
         if (lane == 0) {
-            atomic_max_nonneg(norms + 3 * c + 0, r);
-            atomic_max_nonneg(norms + 3 * c + 1, ax);
-            atomic_max_nonneg(norms + 3 * c + 2, ab);
+            atomicMax(norms + 3 * c + 0, r);
+            atomicMax(norms + 3 * c + 1, ax);
+            atomicMax(norms + 3 * c + 2, ab);
         }
     }
 }
