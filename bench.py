@@ -553,7 +553,7 @@ def main():
                  if st["ms"] > 0}
     dominant = max(rooflines, key=lambda c: rooflines[c]["device_ms"])
     roofline = dict(rooflines[dominant])
-    roofline["kernel"] = {"diag": "potrf_kernel (FP64 diagonal blocks)",
+    roofline["kernel"] = {"diag": "potrf_ldl_kernel / potrf_kernel (FP64 diagonal blocks)",
                           "trsm": "trsm_gemm_kernel", "update": "update_kernel (CUDA cores)",
                           "update_tc": "update_tc_kernel (tcgen05)",
                           "assemble": "assemble_kernel"}[dominant]
