@@ -97,11 +97,6 @@ def _args():
     return ap.parse_args()
 
 
-def _dist():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
 
 
 # ---------------------------------------------------------------------------
@@ -197,7 +192,8 @@ def oracle_rate(grid, seconds_budget: float) -> dict:
 
 
 def run_reference(args):
-    world, rank, _ = _dist()
+    from paper_1405_2636_gb300 import replicas
+    _, rank, _ = replicas.env_ranks()
     if rank != 0:
         return
     import oracle
@@ -245,12 +241,19 @@ def run_reference(args):
 BATCH_TOL = 1e-10
 
 
-def run_batched(torch, spx, inputs, steps: int) -> dict:
+def run_batched(torch, spx, inputs, steps: int, group, rank: int) -> dict:
     """4096 independent 2-D convection-diffusion systems (sides 12..80),
     static-pivot LU in FP32 with FP64 refinement to 1e-10, one persistent
-    launch; the autotuner picks the launch configuration first."""
+    launch; the autotuner picks the launch configuration first.  With
+    several ranks each takes a flop-balanced bin of the systems and the
+    statistics are combined once at the end (max time, summed work)."""
+    from paper_1405_2636_gb300 import replicas
     W = inputs.BATCHED_CD_4096
-    mats, sides, rhs = inputs.batched_convection_diffusion(W["count"], W["seed"])
+    mine = None
+    if group.world > 1:
+        work = [replicas.lu_work_estimate(k) for k in inputs.batched_sides(W["count"], W["seed"])]
+        mine = replicas.shard_by_work(work, group.world)[rank]
+    mats, sides, rhs = inputs.batched_convection_diffusion(W["count"], W["seed"], systems=mine)
     arrs = [inputs.csc_arrays(A) for A in mats]
     b = spx.batch_analyze([(cp, ri) for cp, ri, _ in arrs], grids=[(k, k, 1) for k in sides],
                           ordering=spx.SPX_ORDER_GRID)
@@ -262,6 +265,7 @@ def run_batched(torch, spx, inputs, steps: int) -> dict:
     b.tune(vals, bd, precision="fp32", refine=ref)
     tune_s = time.perf_counter() - t0
     out = {}
+    i = b.info()
     for prec in ("fp32", "fp64"):
         b.run(vals, bd, precision=prec, refine=ref)
         ms = []
@@ -270,12 +274,19 @@ def run_batched(torch, spx, inputs, steps: int) -> dict:
             ms.append(b.info()["run_ms"])
         i = b.info()
         si = b.system_info()
-        out[prec] = {"ms": statistics.median(ms), "status": st,
-                     "gflops": i["flops"] / (statistics.median(ms) / 1e3) / 1e9,
-                     "all_converged": bool(np.all(si["converged"] == 1)),
-                     "max_backward_error": float(si["berr"].max()),
-                     "max_refine_iters": int(si["iters"].max()),
-                     "pivot_replacements": int(si["npivot_repl"].sum())}
+        local = {"ms": statistics.median(ms), "flops": i["flops"], "systems": i["nsys"],
+                 "n_total": i["n_total"], "nnz_l_total": i["nnz_l_total"],
+                 "all_converged": float(np.all(si["converged"] == 1)),
+                 "max_backward_error": float(si["berr"].max()) if len(si["berr"]) else 0.0,
+                 "max_refine_iters": float(si["iters"].max()) if len(si["iters"]) else 0.0,
+                 "pivot_replacements": float(si["npivot_repl"].sum())}
+        c = replicas.combine_batch_stats(group, local)
+        out[prec] = {"ms": c["ms"], "status": st, "gflops": c["gflops"],
+                     "all_converged": bool(c["all_converged"] == 1.0),
+                     "max_backward_error": c["max_backward_error"],
+                     "max_refine_iters": int(c["max_refine_iters"]),
+                     "pivot_replacements": int(c["pivot_replacements"])}
+        tot = c
     # end to end through the C ABI with host buffers (copies inside the call)
     Xh = np.empty(b.n_total)
     e2e = []
@@ -283,7 +294,7 @@ def run_batched(torch, spx, inputs, steps: int) -> dict:
         t0 = time.perf_counter()
         b.run(vals_h, rhs, Xh, precision="fp32", refine=ref)
         e2e.append(1e3 * (time.perf_counter() - t0))
-    i = b.info()
+    e2e_ms = group.max(statistics.median(e2e))
     peaks = measured_peaks()
     ms32 = out["fp32"]["ms"]
     e = 4.0
@@ -291,15 +302,18 @@ def run_batched(torch, spx, inputs, steps: int) -> dict:
     # once and read by each of the sweeps (1 + refinement steps, forward and
     # backward), A read by each residual, the solution written
     sweeps = 1 + out["fp32"]["max_refine_iters"]
-    byts = (i["nnz_total"] * 8.0 * (2 + sweeps) + i["factor_elems"] * e * (1 + 2 * sweeps)
-            + i["n_total"] * 8.0 * 3)
-    res = {"workload": W["name"], "systems": i["nsys"], "pattern_classes": i["nclasses"],
-           "n_total": i["n_total"], "n_max": i["n_max"], "nnz_l_total": i["nnz_l_total"],
-           "flops_exact": i["flops"], "target_backward_error": BATCH_TOL,
+    byts = group.sum(i["nnz_total"] * 8.0 * (2 + sweeps) + i["factor_elems"] * e * (1 + 2 * sweeps)
+                     + i["n_total"] * 8.0 * 3)
+    res = {"workload": W["name"], "systems": int(tot["systems"]), "ranks": group.world,
+           "sharding": ("flop-balanced bins of whole systems, one per rank; statistics combined "
+                        "once after the timed runs" if group.world > 1 else "one rank"),
+           "pattern_classes": i["nclasses"], "n_total": int(tot["n_total"]), "n_max": i["n_max"],
+           "nnz_l_total": int(tot["nnz_l_total"]),
+           "flops_exact": tot["flops"], "target_backward_error": BATCH_TOL,
            "metric": "time to factorize and solve every system to backward error 1e-10 (one launch)",
            "fp32_refined": out["fp32"], "fp64": out["fp64"],
            "speedup_fp32_over_fp64": out["fp64"]["ms"] / ms32,
-           "e2e_host_buffers_ms": statistics.median(e2e),
+           "e2e_host_buffers_ms": e2e_ms,
            "config": {"ctas_per_sm": i["ctas_per_sm"], "leaf_width": i["leaf_width"],
                       "rows_per_thread": i["rows_per_thread"], "tuned_ms": i["tuned_ms"],
                       "tune_seconds": tune_s},
@@ -430,11 +444,12 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    world, rank, local = _dist()
     import torch
 
     import __graft_entry__
-    from paper_1405_2636_gb300 import inputs, spx
+    from paper_1405_2636_gb300 import inputs, replicas, spx
+
+    world, rank, local = replicas.env_ranks()
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -459,16 +474,9 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    group = replicas.RankGroup(world, dev)
+    barrier = group.barrier
+    max_over_ranks = group.max
 
     def step(mode):
         h.factorize(vals_d, mode)
@@ -558,20 +566,21 @@ def main():
                           "update_tc": "update_tc_kernel (tcgen05)",
                           "assemble": "assemble_kernel"}[dominant]
 
+    extra = {}
+    if not args.no_extra:   # every rank: the batch is sharded over the ranks
+        extra["batched_lu"] = run_batched(torch, spx, inputs, args.steps, group, rank)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    extra = {}
     if not args.no_extra:
-        extra["batched_lu"] = run_batched(torch, spx, inputs, args.steps)
         extra["differentiation"] = run_differentiation(torch, spx, inputs, args.steps)
         extra["ldlt"] = run_ldlt(torch, spx, inputs, args.steps)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_rate((32, 32, 32), 8.0)
-    value = world * flops / (R["ms_per_step"] / 1e3) / 1e9
-    e2e_value = world * flops / (R["e2e_ms"] / 1e3) / 1e9
+    value = replicas.whole_job_rate(flops, world, R["ms_per_step"]) / 1e9
+    e2e_value = replicas.whole_job_rate(flops, world, R["e2e_ms"]) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": R["ms_per_step"],

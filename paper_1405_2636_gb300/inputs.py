@@ -17,7 +17,7 @@ stream])`` so that matrix values and right-hand sides are independent streams.
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 import scipy.sparse as sp
@@ -297,22 +297,35 @@ DIFFUSION3D_64 = Workload("diffusion3d_64^3", (64, 64, 64), 1, 16, 2)
 ELASTICITY27_40 = Workload("elasticity27_40^3x3", (40, 40, 40), 3, 1, 3)
 
 
-def batched_convection_diffusion(count: int, seed: int, k_lo: int = 12, k_hi: int = 80):
+def batched_sides(count: int, seed: int, k_lo: int = 12, k_hi: int = 80) -> List[int]:
+    """Grid side of each system of the batched workload, k ~ U{k_lo..k_hi}."""
+    return [int(k) for k in rng(seed, STREAM_EXTRA).integers(k_lo, k_hi + 1, size=count)]
+
+
+def batched_convection_diffusion(count: int, seed: int, k_lo: int = 12, k_hi: int = 80,
+                                 systems: Optional[Sequence[int]] = None):
     """The batched workload: ``count`` independent 2-D convection-diffusion
     systems, side k ~ U{k_lo..k_hi} per system (n = k^2), each with its own
     wind angle and mesh Peclet number and one right-hand side ~ U(-1, 1).
 
-    System s draws from seed ``seed * 1_000_003 + s``.  Returns (list of
-    csc matrices, list of sides, concatenated right-hand sides).
+    System s draws from seed ``seed * 1_000_003 + s``, so a subset
+    (``systems``: indices in any order; all by default) holds the same
+    systems as the whole batch.  Returns (list of csc matrices, list of
+    sides, concatenated right-hand sides), in the order of ``systems``.
     """
-    sides = rng(seed, STREAM_EXTRA).integers(k_lo, k_hi + 1, size=count)
-    mats, rhss = [], []
-    for s, k in enumerate(sides):
+    sides = batched_sides(count, seed, k_lo, k_hi)
+    idx = range(count) if systems is None else systems
+    mats, rhss, ks = [], [], []
+    for s in idx:
+        if not 0 <= s < count:
+            raise ValueError(f"system {s} outside 0..{count - 1}")
+        k = sides[s]
         sseed = seed * 1_000_003 + s
-        A, _ = convection_diffusion_2d(int(k), sseed)
+        A, _ = convection_diffusion_2d(k, sseed)
         mats.append(A)
+        ks.append(k)
         rhss.append(rhs(A.shape[0], 1, sseed).ravel())
-    return mats, [int(k) for k in sides], (np.concatenate(rhss) if rhss else np.zeros(0))
+    return mats, ks, (np.concatenate(rhss) if rhss else np.zeros(0))
 
 
 BATCHED_CD_4096 = {"name": "batched_convdiff2d_4096x_k12-80", "count": 4096, "seed": 4}
