@@ -180,9 +180,9 @@ spx_status spx_get_panels(spx_handle h, int64_t *first_col, int32_t *width, int3
 
 /* Allocation-free solve.  (The paper has no counterpart; this entry point
  * exists for callers that cannot allocate device memory when they solve:
- * code that replays a solve inside a captured CUDA graph or a real-time
- * loop, where cudaMalloc would stall the device or is not allowed, and hosts
- * whose device memory belongs to another allocator.)  It runs one forward
+ * a real-time loop, where a cudaMalloc would synchronize the device and
+ * stall it, and hosts whose device memory belongs to another allocator that
+ * must see every byte.)  It runs one forward
  * and one backward sweep through the factor of the last spx_factorize --
  * spx_solve without refinement -- and allocates nothing: no cudaMalloc,
  * cudaFree, graph or library call that allocates.

@@ -1,9 +1,9 @@
 """spx_solve_noalloc: the solve for callers that cannot allocate device memory.
 
-Some callers cannot allocate when they solve (a solve replayed inside a
-captured CUDA graph or a real-time loop, or a host whose device memory is
-owned by another allocator).  spx_solve_noalloc keeps its sweep vectors in a
-fixed file-scope device buffer instead.  Its output must match spx_solve
+Some callers cannot allocate when they solve (a real-time loop, where a
+cudaMalloc would synchronize and stall the device, or a host whose device
+memory is owned by another allocator).  spx_solve_noalloc keeps its sweep
+vectors in a fixed file-scope device buffer instead.  Its output must match spx_solve
 without refinement -- the same sweep, with the handle's workspace -- within
 the tolerances the other GPU tests use, on two calls in a row (the buffer
 keeps the previous call's contents).  This file is collected last.
