@@ -37,6 +37,12 @@ WORKLOAD = "diffusion3d_64^3_7pt_expN01_16rhs"
 FP64_ALU_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9        # 2 DFMA / clk / SM
 FP32_ALU_PEAK_GFLOPS = 152 * 128 * 2 * 2.07e9 / 1e9      # 128 FFMA / clk / SM
 L2_FLUSH_BYTES = 256 << 20
+# arithmetic of each factorization mode (the solve's residual and correction
+# are FP64 in every mode)
+DTYPES = {"fp64": "f64",
+          "fp32": "3xtf32 updates (f32 accumulate), f64 diagonal blocks and refinement",
+          "tf32": "tf32 updates (f32 accumulate), f64 diagonal blocks and refinement",
+          "bf16": "bf16 updates (f32 accumulate), f64 diagonal blocks and refinement"}
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25                       # nominal dense tensor rates
 
 
@@ -585,7 +591,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": R["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "f32-factor+f64-refinement",
+        "dtype": DTYPES[head],
         "data": "synthetic",
         "config": {"workload": WORKLOAD if grid == GRID else
                    f"diffusion3d_{grid[0]}x{grid[1]}x{grid[2]}_7pt_expN01_16rhs",
