@@ -584,7 +584,7 @@ def main():
         extra["ldlt"] = run_ldlt(torch, spx, inputs, args.steps)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_rate((32, 32, 32), 8.0)
+        cpu = oracle_rate((32, 32, 32), 12.0)   # about 12-15 s of single-core work
     value = replicas.whole_job_rate(flops, world, R["ms_per_step"]) / 1e9
     e2e_value = replicas.whole_job_rate(flops, world, R["e2e_ms"]) / 1e9
     line = {
