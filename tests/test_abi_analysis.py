@@ -185,3 +185,49 @@ def test_update_task_structure_invariants():
     assert info["npanels"] >= info["nsupernodes"] * 0 + 1
     assert info["update_flops"] <= info["flops_stored"]
     assert info["flops_stored"] >= info["flops"]
+
+
+def _edge_patterns():
+    import scipy.sparse as sp
+    n = 40
+    diag = sp.identity(n, format="csc") * 2.0                       # no update at all
+    dense = sp.csc_matrix(np.ones((70, 70)) + 70 * np.eye(70))      # one supernode, split into panels
+    m = 60
+    arrow = sp.lil_matrix((m, m))                                   # dense last row and column
+    for i in range(m):
+        arrow[i, i] = 4.0
+        arrow[i, m - 1] = arrow[m - 1, i] = 1.0
+    arrow[m - 1, m - 1] = 100.0
+    blocks = sp.block_diag([inputs.random_spd_graph(80, 4.0, 1),   # two components
+                            inputs.random_spd_graph(50, 4.0, 2)]).tocsc()
+    unsym = (sp.random(90, 90, density=0.04, random_state=5, format="csc")
+             + sp.identity(90) * 5).tocsc()                          # LU on A + A^T
+    nodiag = inputs.laplacian_2d(6, 6).tolil()                      # a column without its diagonal
+    nodiag[7, 7] = 0
+    nodiag = nodiag.tocsc()
+    nodiag.eliminate_zeros()
+    return [("diagonal", diag, "llt"), ("dense", dense, "llt"), ("dense", dense, "lu"),
+            ("arrow", arrow.tocsc(), "llt"), ("components", blocks, "llt"),
+            ("unsymmetric", unsym, "lu"), ("no-diagonal", nodiag, "lu")]
+
+
+@pytest.mark.parametrize("name,A,method", _edge_patterns(), ids=lambda v: v if isinstance(v, str) else "")
+@pytest.mark.parametrize("ordering", [spx.SPX_ORDER_NATURAL, spx.SPX_ORDER_GRAPH])
+def test_edge_patterns_match_oracle(name, A, method, ordering):
+    """Fill and flop count of the library's analysis equal the oracle's
+    symbolic factorization on the library's final order, for patterns at the
+    edges of the supernode partition."""
+    cp, ri, _ = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, method, ordering=ordering, max_width=16)
+    perm = h.perm()
+    assert sorted(perm.tolist()) == list(range(A.shape[0]))
+    s = _oracle_counts(A, perm)
+    info = h.info()
+    assert info["nnz_l"] == int(s.Lp[-1])
+    assert info["flops"] == pytest.approx(oracle.flops(s.counts, method), rel=0, abs=0.5)
+    assert info["nnz_l"] <= info["nnz_stored"]
+    if name == "diagonal":
+        assert info["nupdates"] == 0 and info["npanels"] == A.shape[0]
+    if name == "dense":
+        assert info["npanels"] == (A.shape[0] + 15) // 16
+    h.free()
