@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
                                                         unsigned long long *nneg)
 {
     constexpr int LD = W + 1;
-    constexpr int NT = 256, NW = NT / 32;
+    constexpr int NT = 256;
     extern __shared__ double sm[];
     double *a = sm;                          // W x LD, FP64 working block
     double *lA = a + W * LD;                 // 2 x (W x kDB) unscaled block columns (ld W)
