@@ -491,6 +491,7 @@ def main():
         return sinfo
 
     results = {}
+    x_fp64 = None   # the FP64 factor's solution (that factor matches the oracle to 1e-12 in the tests)
     launches_total = 0
     clocks = None
     modes = [m for m in args.modes.split(",") if m]
@@ -517,6 +518,10 @@ def main():
         info = h.info()
         # independent host check of the timed step's output (scipy residual)
         Xc = X_d.cpu().numpy()
+        if mode == "fp64":
+            x_fp64 = Xc.copy()
+        diff_fp64 = (float(np.linalg.norm(Xc - x_fp64) / np.linalg.norm(x_fp64))
+                     if x_fp64 is not None else None)
         R_host = B - A @ Xc
         den = (abs(A).sum(axis=1).max() * np.abs(Xc).max(axis=0) + np.abs(B).max(axis=0))
         host_berr = float(np.max(np.abs(R_host).max(axis=0) / den))
@@ -549,6 +554,7 @@ def main():
             "time_to_solve_gflops": flops / (ms / 1e3) / 1e9,
             "backward_error": sinfo["backward_error"],
             "host_backward_error": host_berr,
+            "rel_diff_to_fp64_solution": diff_fp64,
             "refine_iters": sinfo["iters"],
             "converged": bool(sinfo["backward_error"] <= TARGET_BERR and host_berr <= TARGET_BERR),
             "launches_per_step": info["launches_factor"] + info["launches_solve"],
