@@ -313,7 +313,8 @@ def run_batched(torch, spx, inputs, steps: int, group, rank: int) -> dict:
     res = {"workload": W["name"], "systems": int(tot["systems"]), "ranks": group.world,
            "sharding": ("flop-balanced bins of whole systems, one per rank; statistics combined "
                         "once after the timed runs" if group.world > 1 else "one rank"),
-           "pattern_classes": i["nclasses"], "n_total": int(tot["n_total"]), "n_max": i["n_max"],
+           "pattern_classes": int(group.max(i["nclasses"])), "n_total": int(tot["n_total"]),
+           "n_max": int(group.max(i["n_max"])),
            "nnz_l_total": int(tot["nnz_l_total"]),
            "flops_exact": tot["flops"], "target_backward_error": BATCH_TOL,
            "metric": "time to factorize and solve every system to backward error 1e-10 (one launch)",
