@@ -86,6 +86,26 @@ def class_roofline(cls: str, st: dict, mode: str, peaks: dict) -> dict:
     return out
 
 
+def solve_roofline(info: dict, nrhs: int, refine_iters: int, peaks: dict) -> dict:
+    """Roofline of a refined solve: each forward + backward sweep pair reads
+    the stored factor twice; each residual reads A (values, column indices,
+    value map: 8 + 4 + 8 bytes per entry) and X, B, R (n x nrhs FP64).  One
+    sweep pair and one residual per refinement step, plus the first solve
+    and the final check.  HBM-bound: the bytes over the measured solve time."""
+    pairs = 1 + refine_iters
+    residuals = refine_iters + (1 if refine_iters > 0 else 0)
+    byts = (pairs * 2.0 * info["factor_bytes"]
+            + residuals * (20.0 * info["nnz_a"] + 3.0 * 8.0 * info["n"] * nrhs))
+    ms = info["solve_ms"]
+    out = {"kernel": "fwd_queue_kernel + bwd_queue_kernel (+ residual_kernel)", "bound": "hbm",
+           "sweep_pairs": pairs, "algorithmic_bytes": byts, "device_ms": ms, "unit": "GB/s",
+           "peak": peaks["hbm_gbs"], "peak_source": peaks["source"], "traffic": None}
+    if ms > 0:
+        out["achieved"] = byts / (ms / 1e3) / 1e9
+        out["frac"] = out["achieved"] / peaks["hbm_gbs"]
+    return out
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -551,6 +571,7 @@ def main():
             "step_ms": [round(t, 3) for t in times],
             "factor_ms": info["factor_ms"],
             "solve_ms": info["solve_ms"],
+            "factor_bytes": info["factor_bytes"],
             "factor_gflops": flops / (info["factor_ms"] / 1e3) / 1e9,
             "time_to_solve_gflops": flops / (ms / 1e3) / 1e9,
             "backward_error": sinfo["backward_error"],
@@ -572,6 +593,8 @@ def main():
     peaks = measured_peaks()
     rooflines = {c: class_roofline(c, st, head, peaks) for c, st in R["kernel_stats"].items()
                  if st["ms"] > 0}
+    solve_rl = solve_roofline({"factor_bytes": R["factor_bytes"], "nnz_a": int(colptr[-1]), "n": n,
+                               "solve_ms": R["solve_ms"]}, NRHS, R["refine_iters"], peaks)
     dominant = max(rooflines, key=lambda c: rooflines[c]["device_ms"])
     roofline = dict(rooflines[dominant])
     roofline["kernel"] = {"diag": "potrf_ldl_kernel / potrf_kernel (FP64 diagonal blocks)",
@@ -614,6 +637,7 @@ def main():
         "kernel_stats": {m: results[m]["kernel_stats"] for m in modes},
         "roofline": roofline,
         "rooflines": rooflines,
+        "solve_roofline": solve_rl,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GFlop/s",
                 "h2d_bytes_per_step": int(8 * colptr[-1] + 8 * n * NRHS),

@@ -75,3 +75,20 @@ def test_peaks_come_from_the_measured_file_when_present():
     else:
         assert p["source"] == "of fallback"
     assert set(bench.DTYPES) == {"fp64", "fp32", "tf32", "bf16"}
+
+
+def test_solve_roofline_arithmetic_and_info_keys():
+    from paper_1405_2636_gb300 import spx
+    keys = spx.spx_info().as_dict()        # the binding's info dictionary
+    for k in ("factor_bytes", "nnz_a", "n", "solve_ms"):
+        assert k in keys
+    peaks = {"hbm_gbs": 5000.0, "bf16_tflops": 2000.0, "source": "of measured"}
+    info = {"factor_bytes": 7e8, "nnz_a": 1.8e6, "n": 262144, "solve_ms": 20.0}
+    r = bench.solve_roofline(info, 16, 3, peaks)
+    expect = 4 * 2 * 7e8 + 4 * (20 * 1.8e6 + 3 * 8 * 262144 * 16)
+    assert r["sweep_pairs"] == 4 and r["algorithmic_bytes"] == pytest.approx(expect)
+    assert r["achieved"] == pytest.approx(expect / 0.02 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 5000.0) and r["bound"] == "hbm"
+    r0 = bench.solve_roofline(info, 16, 0, peaks)        # FP64: one sweep pair, no residual
+    assert r0["algorithmic_bytes"] == pytest.approx(2 * 7e8)
+    assert "frac" not in bench.solve_roofline(dict(info, solve_ms=0.0), 16, 0, peaks)
