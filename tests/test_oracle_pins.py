@@ -243,3 +243,18 @@ def test_spmv_matches_scipy():
     A = _coldominant_unsym(70, 9)
     x = inputs.rhs(70, 1, 9)[:, 0]
     np.testing.assert_allclose(oracle.spmv(A, x), A @ x, rtol=1e-14, atol=1e-14)
+
+
+def test_lu_solve_matches_dense_solve():
+    """The LU solve on an unsymmetric, column-dominant matrix (no pivot is
+    replaced) equals the dense solve; solving with A^T instead of A, or with
+    L and U swapped, would not."""
+    A = _coldominant_unsym(120, 12)
+    for perm in (np.arange(120), oracle.nd_graph(A)):
+        F = oracle.lu(A, perm)
+        assert F.nrepl == 0
+        B = inputs.rhs(120, 3, 12)
+        X = oracle.solve(F, B)
+        np.testing.assert_allclose(X, np.linalg.solve(A.toarray(), B), rtol=1e-11, atol=1e-13)
+        assert np.abs(A.toarray() - A.toarray().T).max() > 0.1      # the check would see a transpose
+        assert oracle.backward_error(A, X, B) < 1e-15
