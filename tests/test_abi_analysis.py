@@ -231,3 +231,34 @@ def test_edge_patterns_match_oracle(name, A, method, ordering):
     if name == "dense":
         assert info["npanels"] == (A.shape[0] + 15) // 16
     h.free()
+
+
+@pytest.mark.parametrize("method,maker,opts", [
+    ("llt", lambda: inputs.diffusion_3d(10, 9, 8, 7), dict(ordering=1, grid=(10, 9, 8), max_width=8)),
+    ("llt", lambda: inputs.random_spd_graph(700, 5.0, 3), dict(ordering=2, max_width=24)),
+    ("lu", lambda: inputs.convection_diffusion_2d(25, 1)[0], dict(ordering=1, grid=(25, 25, 1), max_width=16)),
+], ids=["grid-llt", "graph-llt", "grid-lu"])
+def test_panel_tree_invariants(method, maker, opts):
+    """The panel structure (Sec. III: supernodes split into panels of at most
+    max_width columns, each a dense trapezoid of its rows) accounts exactly
+    for the stored entries and the stored flop count, and its tree is a
+    level structure: parents later and higher, leaves at level 0."""
+    A = maker()
+    cp, ri, _ = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, method, **opts)
+    P, info = h.panels(), h.info()
+    w, hh = P["width"].astype(np.int64), P["height"].astype(np.int64)
+    par, lev = P["parent"], P["level"]
+    assert w.sum() == A.shape[0] and np.all(w >= 1) and np.all(w <= opts["max_width"])
+    assert P["first_col"][0] == 0 and np.array_equal(np.diff(P["first_col"]), w[:-1])
+    assert np.all(hh >= w) and np.all(hh <= A.shape[0] - P["first_col"])
+    assert info["nnz_stored"] == int(np.sum(w * (hh - w) + w * (w + 1) // 2))
+    c = np.concatenate([hh[p] - np.arange(w[p]) for p in range(len(w))]).astype(np.float64)
+    stored = np.sum(c * c) if method == "llt" else np.sum(2 * (c - 1) ** 2 + (c - 1))
+    assert info["flops_stored"] == pytest.approx(stored, rel=1e-15)
+    for p in range(len(par)):
+        assert par[p] == -1 or (par[p] > p and lev[par[p]] > lev[p])
+    has_child = np.zeros(len(par), bool)
+    has_child[par[par >= 0]] = True
+    assert np.all(lev[~has_child] == 0) and info["nlevels"] == lev.max() + 1
+    h.free()
