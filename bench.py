@@ -464,6 +464,73 @@ def run_ldlt(torch, spx, inputs, steps: int) -> dict:
 
 
 # ---------------------------------------------------------------------------
+# the kernel study of Sec. V-B through the factorization's update kernels
+# ---------------------------------------------------------------------------
+STUDY_WIDTHS = (32, 64, 128, 256)                  # N: source panel width (K of the product)
+STUDY_HEIGHTS = (256, 512, 1024, 2048, 4096, 8192)  # M: source panel rows
+STUDY_CALLS = 100
+
+
+def run_update_study(torch, spx, inputs, peaks: dict) -> dict:
+    """C = C - A B^T with A of M x N, B its first N rows, C a panel twice as
+    tall as A with random blocks of about 200 rows (A's blocks inside C's),
+    each point the average of 100 back-to-back calls (Sec. V-B protocol),
+    through the hot-path update kernels (spx_update_* runs update_tc_kernel
+    or update_kernel on a one-task plan).  flops = 2 M N^2; bytes = A and B
+    read once, the touched C entries read and written once."""
+    stream = torch.cuda.current_stream()
+    modes = (("tf32", "tensor_cores"), ("bf16", "tensor_cores"), ("fp64", "cuda_cores"))
+    out = {}
+    for mode, engine in modes:
+        rows = []
+        for N in STUDY_WIDTHS:
+            for M in STUDY_HEIGHTS:
+                A, C, rowmap, colmap = inputs.gapped_update_case(M, N, N, 1000 * M + N)
+                dt = np.float64 if mode == "fp64" else np.float32
+                plan = spx.UpdatePlan(M, N, N, C.shape[0], C.shape[1], rowmap, colmap, lower=False,
+                                      precision=mode, engine=engine)
+                tA = torch.from_numpy(np.ascontiguousarray(A.T, dtype=dt)).cuda().t()
+                tC = torch.from_numpy(np.ascontiguousarray(C.T, dtype=dt)).cuda().t()
+                plan.stage(tA, stream=stream)
+                for _ in range(3):
+                    plan.run(tC, wait=False, stream=stream)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(STUDY_CALLS):
+                    plan.run(tC, wait=False, stream=stream)
+                e1.record(stream)
+                plan.run(tC, wait=True, stream=stream)     # reports a pipeline timeout, if any
+                ms = e0.elapsed_time(e1) / STUDY_CALLS
+                plan.free()
+                flops = 2.0 * M * N * N
+                eop = {"tf32": 4.0, "bf16": 2.0, "fp64": 8.0}[mode]
+                eacc = 8.0 if mode == "fp64" else 4.0
+                byts = (M + N) * N * eop + 2.0 * M * N * eacc
+                rows.append({"N": N, "M": M, "us_per_call": round(ms * 1e3, 3),
+                             "gflops": flops / (ms / 1e3) / 1e9, "gbs": byts / (ms / 1e3) / 1e9})
+        if mode == "fp64":
+            peak, src = FP64_ALU_PEAK_GFLOPS, "derived FP64 ALU peak"
+        else:
+            peak = peaks["bf16_tflops"] * 1e3 * (1.0 if mode == "bf16" else NOMINAL_TF32_OVER_BF16)
+            src = "measured bf16" + ("" if mode == "bf16" else " x nominal tf32/bf16 ratio (1.1/2.25)")
+        for r in rows:
+            r["frac_compute_peak"] = r["gflops"] / peak
+            r["frac_hbm"] = r["gbs"] / peaks["hbm_gbs"]
+        best = max(rows, key=lambda r: r["gflops"])
+        out[mode] = {"engine": engine,
+                     "kernel": "update_tc_kernel (tcgen05)" if engine == "tensor_cores" else
+                               "update_kernel (CUDA cores)",
+                     "compute_peak_gflops": peak, "peak_source": src, "points": rows,
+                     "best": {k: best[k] for k in ("N", "M", "gflops", "frac_compute_peak")}}
+    return {"protocol": "Sec. V-B: C = C - A B^T, A M x N, B = first N rows of A, C twice as tall "
+                        "with random ~200-row blocks, average of 100 back-to-back calls "
+                        "(C stays in L2 across the calls)",
+            "modes": out}
+
+
+# ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -585,12 +652,24 @@ def main():
             "e2e_backward_error": sinfo_h["backward_error"],
             "clocks": ck,
         }
-        clocks = ck if clocks is None else clocks
 
     ok = [m for m in modes if results[m]["converged"]]
     head = min(ok, key=lambda m: results[m]["ms_per_step"]) if ok else modes[0]
     R = results[head]
+    clocks = R["clocks"]          # sampled during the headline mode's timed steps
     peaks = measured_peaks()
+    # roofline model of the whole factorization: every task at the better of
+    # its two bounds (spx_roofline_model), against the measured factor time
+    tpeak = peaks["bf16_tflops"] * 1e3 * (1.0 if head == "bf16" else NOMINAL_TF32_OVER_BF16)
+    model = h.roofline_model(head, peaks["hbm_gbs"], FP64_ALU_PEAK_GFLOPS, FP32_ALU_PEAK_GFLOPS, tpeak)
+    model_total = sum(model.values())
+    factor_model = {"mode": head, "model_ms_per_class": model, "model_ms": model_total,
+                    "measured_factor_ms": R["factor_ms"],
+                    "frac": model_total / R["factor_ms"] if R["factor_ms"] > 0 else None,
+                    "peaks": {"hbm_gbs": peaks["hbm_gbs"], "fp64_gflops": FP64_ALU_PEAK_GFLOPS,
+                              "fp32_gflops": FP32_ALU_PEAK_GFLOPS, "tensor_gflops": tpeak},
+                    "definition": "sum over tasks of max(flops / compute peak, bytes / HBM bandwidth) "
+                                  "over the measured factorization time"}
     rooflines = {c: class_roofline(c, st, head, peaks) for c, st in R["kernel_stats"].items()
                  if st["ms"] > 0}
     solve_rl = solve_roofline({"factor_bytes": R["factor_bytes"], "nnz_a": int(colptr[-1]), "n": n,
@@ -605,6 +684,8 @@ def main():
     extra = {}
     if not args.no_extra:   # every rank: the batch is sharded over the ranks
         extra["batched_lu"] = run_batched(torch, spx, inputs, args.steps, group, rank)
+    if not args.no_extra and rank == 0:
+        extra["update_kernel_study"] = run_update_study(torch, spx, inputs, peaks)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -635,8 +716,12 @@ def main():
         "modes": {m: {k: v for k, v in results[m].items() if k not in ("kernel_stats",)}
                   for m in modes},
         "kernel_stats": {m: results[m]["kernel_stats"] for m in modes},
+        "fp64_ms_per_step": results["fp64"]["ms_per_step"] if "fp64" in results else None,
+        "speedup_mixed_over_fp64": (results["fp64"]["ms_per_step"] / R["ms_per_step"]
+                                    if "fp64" in results and head != "fp64" else None),
         "roofline": roofline,
         "rooflines": rooflines,
+        "factorization_roofline_model": factor_model,
         "solve_roofline": solve_rl,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GFlop/s",

@@ -127,6 +127,8 @@ typedef struct {
     double solve_ms;        /* device time of the last spx_solve */
     int64_t npivot_neg;     /* LDL^T: negative pivots of the last factorization (the inertia, when
                                no pivot was replaced) */
+    int64_t noalloc_timeout;/* 1 if the last spx_solve_noalloc whose work has completed had a sweep
+                               wait give up (its X is then undefined), else 0 */
 } spx_info;
 
 /* Host-only analysis (Sec. III: ordering, elimination tree, symbolic
@@ -158,6 +160,15 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
 
 /* Statistics of the analysis and of the last factorization/solve. */
 spx_status spx_get_info(spx_handle h, spx_info *info);
+
+/* Bounded device waits of the triangular sweeps (spx_solve,
+ * spx_solve_noalloc): a wait on a work-queue counter gives up after `polls`
+ * polls of about 256 ns and the call returns SPX_ERR_TIMEOUT (spx_solve) or
+ * records it (spx_solve_noalloc, see spx_info.noalloc_timeout); the
+ * solution is then undefined and the handle stays usable.  polls = 0
+ * restores the default, 2^22 (about a second), which only a stalled device
+ * exhausts.  SPX_ERR_ARG for polls outside [0, 2^32). */
+spx_status spx_set_wait_limit(spx_handle h, int64_t polls);
 
 /* Copy the final permutation (new -> old, length n) to host memory. */
 spx_status spx_get_perm(spx_handle h, int64_t *perm);
@@ -191,19 +202,24 @@ spx_status spx_get_panels(spx_handle h, int64_t *first_col, int32_t *width, int3
  *   The sweep vectors live in one file-scope device buffer of 16 MiB that
  *   every GPU loading the library holds until the process exits; the call
  *   needs 4 * n * nrhs elements of the factor's type (8 bytes for an FP64
- *   factor, 4 otherwise) plus 4 * npanels + 2 32-bit sweep counters, and
- *   returns SPX_ERR_ARG when that exceeds 16 MiB.
- *   The sweeps wait on device-side counters with a bounded wait; a wait
- *   that runs out (which only a stalled device causes) leaves X undefined
- *   and makes the handle's next spx_solve return SPX_ERR_TIMEOUT.
+ *   factor, 4 otherwise) plus 4 * npanels + 3 32-bit words (the sweep
+ *   counters and the error word), and returns SPX_ERR_ARG when that exceeds
+ *   16 MiB.
+ *   The sweeps wait on device-side counters with a bounded wait
+ *   (spx_set_wait_limit); the call's own error word, kept in the same
+ *   buffer and zeroed at the start of each call, is copied to host memory
+ *   the handle owns at the end of the call's work: once the caller has
+ *   synchronized cuda_stream, spx_get_info's noalloc_timeout is 1 if a wait
+ *   ran out (X is then undefined; only a stalled device or a tiny wait
+ *   limit causes it) and 0 otherwise.
  *   All calls share that buffer and it keeps the previous call's contents:
  *   calls whose GPU work overlaps (other streams, other handles, other
  *   threads) race and must be ordered by the caller.
  *   The work is enqueued on cuda_stream and the call returns without
  *   waiting for it.  The current device must be the one the handle
- *   factorized on.  The first call on a device looks up the buffer's device
- *   address (cudaGetSymbolAddress); make that first call before any stream
- *   capture. */
+ *   factorized on.  spx_factorize looks up the buffer's device address
+ *   (cudaGetSymbolAddress, once per device), which also loads the module
+ *   that holds the buffer, so this call only reads the cached address. */
 spx_status spx_solve_noalloc(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
                              int64_t ldx, void *cuda_stream);
 
@@ -272,25 +288,82 @@ typedef struct {
 spx_status spx_set_profiling(spx_handle h, int on);
 spx_status spx_get_kernel_stats(spx_handle h, spx_kernel_stats *out);
 
+/* Roofline model of the factorization's work on the analysed structure:
+ * for every task of each kernel class (a panel's diagonal block, a panel's
+ * TRSM, an update task, the assembly), the time it takes at the better of
+ * its two bounds, max(flops / compute peak, bytes / bandwidth), with the
+ * algorithmic flops and bytes spx_get_kernel_stats uses, summed per class
+ * into model_ms[SPX_K_CLASSES] (milliseconds).  Update tasks go to the engine
+ * spx_factorize would use in `precision`.  peaks[4]: HBM GB/s, FP64 GFLOP/s
+ * (the diagonal blocks always), FP32 CUDA-core GFLOP/s, tensor-core GFLOP/s
+ * of the mode's operand type.  Sum over the classes / measured factorization
+ * time = the fraction of the roofline model the factorization reaches. */
+spx_status spx_roofline_model(spx_handle h, spx_precision precision, const double *peaks,
+                              double *model_ms);
+
 /* Release a handle and everything it owns.  NULL-safe. */
 void spx_free(spx_handle h);
 
-/* The supernodal update on its own, as the paper's kernel study runs it
- * (Sec. V-B: C = C - A B^T where B is the first K rows of A, and C is a
- * taller panel with a gapped block structure; each row block of A lies
- * inside one row block of C, and blocks of A do not overlap).
- *   A     : device, column-major m x k (lda >= m), the source panel rows.
- *   nb_rows: the first nb_rows rows of A form B (the facing columns).
- *   C     : device, column-major ldc x nc target panel.
- *   rowmap: device int32[m]: target row of each source row (C row index).
- *   colmap: device int32[nb_rows]: target column of each of B's rows.
- *   lower : 1 = only entries with source row index >= source column index
- *           (the diagonal-block region) are updated, as in Cholesky.
- * Entries are subtracted with atomic adds, so several calls may target the
- * same C concurrently.  precision: SPX_FP64 (A, C double) only. */
-spx_status spx_update(int64_t m, int64_t nb_rows, int64_t k, const double *A, int64_t lda,
-                      double *C, int64_t ldc, const int32_t *rowmap, const int32_t *colmap,
-                      int lower, void *cuda_stream);
+/* ---- The supernodal update on its own (the kernel study of Sec. V-B) ------
+ *
+ * C = C - A B^T, where A (m x k) holds the rows of a source panel, B is its
+ * first nb_rows rows (the rows facing the target's columns, as in the
+ * Cholesky update) and C is a target panel (ldc x nc, column-major) whose
+ * rows are cut into blocks.  Row i of A lands on row rowmap[i] of C and row
+ * j of B on column colmap[j]; each block of A lies inside one block of C, so
+ * the product is subtracted directly at those positions with no temporary
+ * buffer (Sec. V-B).  A plan describes this single (source, target) task
+ * exactly as the analysis describes one of the factorization's tasks;
+ * spx_update_stage stores A the way the factorization stores a panel
+ * (column-major, plus for the tensor cores the rounded K-major operand copy
+ * the panel TRSM writes); spx_update_run launches the factorization's own
+ * update kernels over the task's tiles -- update_kernel on the CUDA cores or
+ * update_tc_kernel on the tcgen05 tensor cores -- with the factorization's
+ * tile rules.  Entries are subtracted with atomic adds.
+ *
+ *   precision : SPX_FP64: A, W and C are double.  Otherwise they are float
+ *               (the mixed factor's storage) and the products use the mode's
+ *               arithmetic: SPX_FP32 = FP32 on the CUDA cores or split TF32
+ *               (hi*hi + hi*lo + lo*hi) on the tensor cores; SPX_TF32 / SPX_BF16
+ *               = TF32 / BF16 operands; FP32 accumulation throughout.
+ *   engine    : 0 = the factorization's choice (tensor cores for the single-
+ *               precision modes when k >= 32, except LDL^T in SPX_FP32; CUDA
+ *               cores otherwise); 1 = CUDA cores; 2 = tensor cores (SPX_ERR_ARG
+ *               for SPX_FP64 and for LDL^T in SPX_FP32).
+ *   ldlt      : 1 = the LDL^T update C = C - L (D L^T)^T (Sec. V-B): A holds
+ *               rows of L and W (spx_update_stage) the same rows of D L^T; B is
+ *               the first nb_rows rows of W.
+ *   lower     : 1 = only entries with source row index i >= facing row index j
+ *               (the diagonal-block region of a Cholesky target).
+ *   rowmap    : host int32[m], entries in [0, ldc); colmap: host int32[nb_rows],
+ *               entries in [0, nc); both copied.  SPX_ERR_ARG otherwise.
+ * The plan owns its device copies; the caller owns A, W and C. */
+typedef struct spx_update_s *spx_update_plan;
+
+spx_status spx_update_create(int64_t m, int64_t nb_rows, int64_t k, int64_t ldc, int64_t nc,
+                             const int32_t *rowmap, const int32_t *colmap, int lower,
+                             spx_precision precision, int engine, int ldlt, spx_update_plan *out);
+
+/* Stage the source panel: A (and W for LDL^T) are device arrays, column-
+ * major m x k with leading dimension lda >= m, of the plan's element type.
+ * Returns after the staging has completed on cuda_stream. */
+spx_status spx_update_stage(spx_update_plan u, const void *A, const void *W, int64_t lda,
+                            void *cuda_stream);
+
+/* C -= A B^T on the device array C (ldc x nc, the plan's element type).
+ * wait = 0: enqueue on cuda_stream and return (repeated calls accumulate);
+ * wait = 1: also wait for completion and report SPX_ERR_TIMEOUT if a bounded
+ * wait of the tensor-core pipeline expired. */
+spx_status spx_update_run(spx_update_plan u, void *C, int wait, void *cuda_stream);
+
+/* Engine in use (1 CUDA cores, 2 tensor cores) and output tiles per run. */
+spx_status spx_update_get_info(spx_update_plan u, int32_t *engine, int64_t *tiles);
+
+/* Message for the last failing call on u (or on plan creation when u is NULL). */
+const char *spx_update_last_error(spx_update_plan u);
+
+/* Release a plan.  NULL-safe. */
+void spx_update_free(spx_update_plan u);
 
 /* ---- Batched static-pivot LU of many small independent systems ----------
  *

@@ -19,7 +19,9 @@ dense inverse by brute force, the closed-form inverse of the 1-D Laplacian
 and trace(A Z) = n; for LDL^T the reconstruction P A P^T = L D L^T by brute
 force, Sylvester's law of inertia against dense eigenvalues, the Cholesky
 factor as L sqrt(D) on SPD matrices, the closed-form LDL^T of the 1-D
-Laplacian and a hand-computed static-pivot replacement.
+Laplacian and a hand-computed static-pivot replacement; for the panel
+update (Sec. V-B) a hand-computed gapped case and the Schur-complement
+identity M22 - L21 L21^T = L22 L22^T of a dense Cholesky factor.
 """
 from __future__ import annotations
 
@@ -361,6 +363,25 @@ def logdet_gradient(A, F: Factor) -> np.ndarray:
     out = np.empty(A.nnz)
     # tocoo of a canonical CSC keeps the CSC order
     out[:] = vals
+    return out
+
+
+def panel_update(A: np.ndarray, B: np.ndarray, C: np.ndarray, rowmap: np.ndarray,
+                 colmap: np.ndarray, lower: bool) -> np.ndarray:
+    """The supernodal update of Sec. V-B: C - A B^T subtracted at the target
+    positions the block structure gives (row i of A to row rowmap[i] of C,
+    row j of B to column colmap[j]); with ``lower`` only the entries with
+    source row i >= facing row j (the diagonal-block region of a Cholesky
+    target).  FP64: the product W = A B^T, then the scatter.  Returns a new C.
+    Pinned (tests/test_oracle_update.py) by a hand-computed case and by the
+    Schur-complement identity of a dense Cholesky factor."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    out = np.array(C, dtype=np.float64, copy=True)
+    W = A @ B.T
+    for j in range(B.shape[0]):
+        i0 = j if lower else 0
+        out[rowmap[i0:], colmap[j]] -= W[i0:, j]
     return out
 
 

@@ -22,9 +22,10 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", CSRC, "-I", INCLUDE]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 
-CU_SOURCES = ["api.cu", "factor.cu", "solve.cu", "update_tc.cu", "batch_api.cu", "batch_lu.cu", "selinv.cu", "sweep.cu"]
+CU_SOURCES = ["api.cu", "factor.cu", "solve.cu", "update_tc.cu", "batch_api.cu", "batch_lu.cu", "selinv.cu",
+              "sweep.cu", "study.cu"]
 CXX_SOURCES = ["analyze.cpp"]
-HEADERS = ["kernels.cuh", "spx_plan.h", "batch_kernel.cuh"]
+HEADERS = ["kernels.cuh", "spx_plan.h", "batch_kernel.cuh", "operand.cuh"]
 
 
 def _sources():

@@ -63,6 +63,8 @@ struct spx_handle_s {
     int32_t *d_qneed_f = nullptr, *d_qneed_b = nullptr, *d_qstate = nullptr, *d_qerr = nullptr;
     int32_t *d_qmerge = nullptr;
     int32_t q_nitems = 0, q_mat = 0, q_matb = 0, q_vec = 0;
+    uint32_t spin_limit = spx::kDefaultSpinLimit;   // polls before a sweep wait gives up
+    int32_t *h_noalloc_err = nullptr;   // pinned: the error word of the last completed spx_solve_noalloc
     UpdTile *d_tcsmall = nullptr;
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
@@ -222,6 +224,8 @@ spx_status ensure_device(spx_handle h)
     CU(cudaEventCreateWithFlags(&h->ev_fence, cudaEventDisableTiming));
     CU(cudaEventCreate(&h->ev_t0));
     CU(cudaEventCreate(&h->ev_t1));
+    CU(cudaHostAlloc((void **)&h->h_noalloc_err, sizeof(int32_t), cudaHostAllocDefault));
+    *h->h_noalloc_err = 0;
 
     const spx::Plan &P = h->plan;
     spx_status st;
@@ -604,7 +608,8 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
 // vectors, `state` the 4 npanels + 2 per-sweep counters.  Returns the
 // kernels launched.
 template <typename T>
-int enqueue_queue_sweeps(spx_handle h, int nrhs, T *Y, T *Z, T *Tacc, T *Xs, int32_t *state, cudaStream_t s)
+int enqueue_queue_sweeps(spx_handle h, int nrhs, T *Y, T *Z, T *Tacc, T *Xs, int32_t *state, int32_t *err,
+                         cudaStream_t s)
 {
     const spx::Plan &P = h->plan;
     const T *L = (const T *)h->d_L, *U = (const T *)h->d_U, *Dinv = (const T *)h->d_Dinv;
@@ -616,7 +621,8 @@ int enqueue_queue_sweeps(spx_handle h, int nrhs, T *Y, T *Z, T *Tacc, T *Xs, int
     q.nitems = h->q_nitems;
     q.tptr = h->d_qtptr;
     q.tgt = h->d_qtgt;
-    q.err = h->d_qerr;
+    q.err = err;
+    q.spin_limit = h->spin_limit;
     q.merge = h->d_qmerge;
     q.mat_elems = h->q_mat;
     q.matb_elems = h->q_matb;
@@ -645,7 +651,7 @@ void enqueue_sweep(spx_handle h, int nrhs)
     T *Y = (T *)h->d_Y, *Z = (T *)h->d_Z, *Tacc = (T *)h->d_T, *Xs = (T *)h->d_Xs;
     int64_t k = 0;
     spx::launch_permute_in<T>(P.n, nrhs, h->d_R, P.n, h->d_perm, Y, s);
-    k += enqueue_queue_sweeps<T>(h, nrhs, Y, Z, Tacc, Xs, h->d_qstate, s);
+    k += enqueue_queue_sweeps<T>(h, nrhs, Y, Z, Tacc, Xs, h->d_qstate, h->d_qerr, s);
     spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, h->d_D, P.n, s);
     h->sweep_launches = k + 2;
 }
@@ -781,7 +787,9 @@ spx_status residual(spx_handle h, int nrhs, double *berr)
 // ---------------------------------------------------------------------------
 // Allocation-free solve: the sweep vectors live in this file-scope buffer.
 // Host code must not hand the symbol itself to a kernel (in host code it is a
-// host-side stand-in); its device address is looked up once per device.
+// host-side stand-in); its device address is looked up once per device, by
+// spx_factorize, so that the module holding the buffer is loaded there and
+// spx_solve_noalloc only reads the cached address.
 // ---------------------------------------------------------------------------
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 static __device__ __align__(256) unsigned char spx_static_scratch[kStaticScratchBytes];
@@ -806,7 +814,11 @@ spx_status static_scratch_address(spx_handle h, int device, void **out)
 }
 
 // One forward + backward sweep from B (original numbering) to X with the
-// sweep vectors Y, Z, Tacc, Xs carved out of `scratch`; launches only.
+// sweep vectors Y, Z, Tacc, Xs carved out of `scratch`, followed by the
+// 4 npanels + 2 sweep counters and the call's own error word (zeroed first,
+// so that a timeout of an earlier call does not carry over); the error word
+// is then copied to the handle's pinned host word.  Launches and
+// stream-ordered copies only.
 template <typename T>
 void enqueue_sweep_noalloc(spx_handle h, int nrhs, const double *B, int64_t ldb, double *X,
                            int64_t ldx, T *scratch, cudaStream_t s)
@@ -815,9 +827,12 @@ void enqueue_sweep_noalloc(spx_handle h, int nrhs, const double *B, int64_t ldb,
     const size_t len = (size_t)P.n * nrhs;
     T *Y = scratch, *Z = scratch + len, *Tacc = scratch + 2 * len, *Xs = scratch + 3 * len;
     int32_t *state = reinterpret_cast<int32_t *>(scratch + 4 * len);
+    int32_t *err = state + 4 * (size_t)P.npanels + 2;
+    cudaMemsetAsync(err, 0, sizeof(int32_t), s);
     spx::launch_permute_in<T>(P.n, nrhs, B, ldb, h->d_perm, Y, s);
-    enqueue_queue_sweeps<T>(h, nrhs, Y, Z, Tacc, Xs, state, s);
+    enqueue_queue_sweeps<T>(h, nrhs, Y, Z, Tacc, Xs, state, err, s);
     spx::launch_permute_out<T>(P.n, nrhs, Xs, h->d_perm, X, ldx, s);
+    cudaMemcpyAsync(h->h_noalloc_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1040,6 +1055,12 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     if (precision < SPX_FP64 || precision > SPX_BF16) return fail(h, SPX_ERR_ARG, "unknown precision");
     spx_status st = ensure_device(h);
     if (st != SPX_OK) return st;
+    {
+        // look up the allocation-free solve's static buffer now, so that the
+        // module holding it is loaded before any spx_solve_noalloc call
+        void *scratch = nullptr;
+        if ((st = static_scratch_address(h, h->device, &scratch)) != SPX_OK) return st;
+    }
     const spx::Plan &P = h->plan;
     const bool fp64 = precision == SPX_FP64;
     const size_t elems = (size_t)P.pval[P.npanels];
@@ -1205,13 +1226,7 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
         h->sgraph_prec = h->precision;
     }
     h->cnt = 0;
-    int32_t qerr = 0;   // a timed-out sweep wait, here or in an earlier spx_solve_noalloc
-    CU(cudaMemcpyAsync(&qerr, h->d_qerr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs));
-    CU(cudaStreamSynchronize(h->hs));
-    if (qerr) {
-        CU(cudaMemset(h->d_qerr, 0, sizeof(int32_t)));
-        return fail(h, SPX_ERR_TIMEOUT, "a sweep of an earlier spx_solve_noalloc gave up waiting on its work queue");
-    }
+    int32_t qerr = 0;
     CU(cudaEventRecord(h->ev_t0, h->hs));
     CU(cudaMemcpyAsync(h->d_R, h->d_B, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, h->hs));
     CU(cudaGraphLaunch(h->sgraph, h->hs));
@@ -1262,7 +1277,70 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
 spx_status spx_get_info(spx_handle h, spx_info *info)
 {
     if (!h || !info) return fail(h, SPX_ERR_ARG, "NULL argument");
+    h->info.noalloc_timeout = h->h_noalloc_err ? *(volatile int32_t *)h->h_noalloc_err : 0;
     *info = h->info;
+    return SPX_OK;
+}
+
+spx_status spx_roofline_model(spx_handle h, spx_precision precision, const double *peaks, double *model_ms)
+{
+    if (!h || !peaks || !model_ms) return fail(h, SPX_ERR_ARG, "NULL argument");
+    if (precision < SPX_FP64 || precision > SPX_BF16) return fail(h, SPX_ERR_ARG, "unknown precision");
+    for (int i = 0; i < 4; ++i)
+        if (!(peaks[i] > 0.0)) return fail(h, SPX_ERR_ARG, "peaks must be positive");
+    const spx::Plan &P = h->plan;
+    const bool fp64 = precision == SPX_FP64;
+    const bool lu = P.method == SPX_LU;
+    const double e = fp64 ? 8.0 : 4.0;
+    const double bw = peaks[0] * 1e9, f64 = peaks[1] * 1e9, f32 = peaks[2] * 1e9, tc = peaks[3] * 1e9;
+    const double simt = fp64 ? f64 : f32;
+    const bool tcm = uses_tensor_cores(P.method, precision);
+    const double eop = precision == SPX_BF16 ? 2.0 : (precision == SPX_FP32 ? 8.0 : 4.0);
+    auto t = [&](double flops, double bytes, double peak) { return std::max(flops / peak, bytes / bw); };
+    double ms[SPX_K_CLASSES] = {0, 0, 0, 0, 0};
+    const double nfac = lu ? 2.0 : 1.0;
+    ms[SPX_K_ASSEMBLE] = ((double)P.nnz_a * (16.0 + e * nfac) + (double)P.pval[P.npanels] * e * nfac) / bw;
+    for (int32_t q = 0; q < P.npanels; ++q) {
+        const double w = P.pw[q], off = (double)P.ph[q] - P.pw[q];
+        double df = 0.0;
+        for (int32_t j = 0; j < P.pw[q]; ++j) {
+            const double c = w - j;
+            df += lu ? 2.0 * (c - 1.0) * (c - 1.0) + (c - 1.0) : c * c;
+        }
+        ms[SPX_K_DIAG] += t(df, 2.0 * w * w * e, f64);
+        ms[SPX_K_TRSM] += t(nfac * off * w * w, nfac * (2.0 * off * w + w * w) * e, simt);
+    }
+    for (const spx::Task &tk : P.tasks) {
+        const double M = (double)P.ph[tk.src] - tk.r0, N = (double)tk.r1 - tk.r0, K = P.pw[tk.src];
+        double flops, elems_op, elems_acc;
+        if (!lu) {
+            flops = 2.0 * (M - N) * N * K + N * (N + 1.0) * K;
+            elems_op = (M + N) * K;
+            elems_acc = 2.0 * ((M - N) * N + N * (N + 1.0) / 2.0);
+        } else {
+            flops = 2.0 * M * N * K + 2.0 * (M - N) * N * K;
+            elems_op = (M + N) * K + M * K;
+            elems_acc = 2.0 * (M * N + (M - N) * N);
+        }
+        if (tcm && P.pw[tk.src] >= kTcMinWidth)
+            ms[SPX_K_UPDATE_TC] += t(flops, elems_op * eop + elems_acc * 4.0, tc);
+        else
+            ms[SPX_K_UPDATE] += t(flops, (elems_op + elems_acc) * e, simt);
+    }
+    for (int c = 0; c < SPX_K_CLASSES; ++c) model_ms[c] = ms[c] * 1e3;
+    return SPX_OK;
+}
+
+spx_status spx_set_wait_limit(spx_handle h, int64_t polls)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (polls < 0 || polls > (int64_t)UINT32_MAX) return fail(h, SPX_ERR_ARG, "polls outside [0, 2^32)");
+    h->spin_limit = polls == 0 ? spx::kDefaultSpinLimit : (uint32_t)polls;
+    if (h->sgraph) {   // the captured sweeps carry the old limit
+        cudaGraphExecDestroy(h->sgraph);
+        h->sgraph = nullptr;
+        h->sgraph_nrhs = -1;
+    }
     return SPX_OK;
 }
 
@@ -1370,10 +1448,10 @@ spx_status spx_solve_noalloc(spx_handle h, int32_t nrhs, const double *B, int64_
     if (nrhs == 0) return SPX_OK;
     const size_t esz = h->precision == SPX_FP64 ? sizeof(double) : sizeof(float);
     const size_t need = (size_t)4 * (size_t)P.n * (size_t)nrhs * esz +
-                        sizeof(int32_t) * ((size_t)4 * P.npanels + 2);
+                        sizeof(int32_t) * ((size_t)4 * P.npanels + 3);
     if (need > kStaticScratchBytes)
         return fail(h, SPX_ERR_ARG,
-                    "4 * n * nrhs sweep elements and the sweep counters (" + std::to_string(need) +
+                    "4 * n * nrhs sweep elements, the sweep counters and the error word (" + std::to_string(need) +
                         " bytes) exceed the 16 MiB static scratch of spx_solve_noalloc");
     int dev = -1;
     CU(cudaGetDevice(&dev));
@@ -1606,24 +1684,8 @@ void spx_free(spx_handle h)
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
     if (h->hs) cudaStreamDestroy(h->hs);
+    if (h->h_noalloc_err) cudaFreeHost(h->h_noalloc_err);
     delete h;
-}
-
-spx_status spx_update(int64_t m, int64_t nb_rows, int64_t k, const double *A, int64_t lda,
-                      double *C, int64_t ldc, const int32_t *rowmap, const int32_t *colmap,
-                      int lower, void *cuda_stream)
-{
-    spx_handle h = nullptr;
-    if (m < 0 || nb_rows < 0 || k < 0 || nb_rows > m) return fail(h, SPX_ERR_ARG, "bad sizes");
-    if (m > INT32_MAX || k > INT32_MAX) return fail(h, SPX_ERR_ARG, "sizes above 2^31");
-    if (m == 0 || nb_rows == 0) return SPX_OK;
-    if (!A || !C || !rowmap || !colmap) return fail(h, SPX_ERR_ARG, "NULL pointer");
-    if (lda < m) return fail(h, SPX_ERR_ARG, "lda below m");
-    spx::launch_update_standalone(m, nb_rows, k, A, lda, C, ldc, rowmap, colmap, lower,
-                                  (cudaStream_t)cuda_stream);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(h, SPX_ERR_CUDA, cudaGetErrorString(e));
-    return SPX_OK;
 }
 
 }  // extern "C"

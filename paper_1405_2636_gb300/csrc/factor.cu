@@ -10,6 +10,7 @@
 // off-diagonal rows below.  T is the storage type (double, or float for the
 // mixed-precision factor); the diagonal blocks are always factored in double.
 #include "kernels.cuh"
+#include "operand.cuh"
 
 #include <cuda_bf16.h>
 #include <cstdio>
@@ -830,13 +831,6 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
 // barriers; 64 x 64 output tiles, 4 x 4 per thread, written back through
 // shared memory in whole segments.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float round_tf32(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                         const T *__restrict__ Dinv,
@@ -927,16 +921,9 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                     Wg[r + (int64_t)j * h] = acc[a][b];
                     const T l = acc[a][b] * dinv;
                     Xg[r + (int64_t)j * h] = l;
-                    if (opc) {   // A operand: L; B operand: D L^T
-                        const int64_t o = (p.prow[pid] + ch.r0 + r) * kpad + j;
-                        if (op_kind == 4) {
-                            reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16((float)l);
-                            reinterpret_cast<__nv_bfloat16 *>(opc_lo)[o] = __float2bfloat16((float)acc[a][b]);
-                        } else {
-                            reinterpret_cast<float *>(opc)[o] = round_tf32((float)l);
-                            reinterpret_cast<float *>(opc_lo)[o] = round_tf32((float)acc[a][b]);
-                        }
-                    }
+                    if (opc)   // A operand: L; B operand: D L^T
+                        put_operand(opc, opc_lo, (p.prow[pid] + ch.r0 + r) * kpad + j, op_kind, (float)l,
+                                    (float)acc[a][b]);
                 }
             }
             continue;
@@ -962,15 +949,8 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
             const int64_t orow0 = p.prow[pid] + ch.r0;
             for (int e = tid; e < nr * kUpdTile; e += 256) {
                 const int r = e >> 6, jj = e & 63;
-                const int64_t o = (orow0 + r) * kpad + c0 + jj;
-                const float v = (float)Ot[r * (kUpdTile + 1) + jj];
-                if (op_kind == 1) {
-                    reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(v);
-                } else {
-                    const float hi = round_tf32(v);
-                    reinterpret_cast<float *>(opc)[o] = hi;
-                    if (op_kind == 2) reinterpret_cast<float *>(opc_lo)[o] = round_tf32(v - hi);
-                }
+                put_operand(opc, opc_lo, (orow0 + r) * kpad + c0 + jj, op_kind,
+                            (float)Ot[r * (kUpdTile + 1) + jj], 0.0f);
             }
         }
     }
@@ -981,14 +961,7 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
         const int padw = kpad - j0;
         for (int e = tid; e < nr * padw; e += 256) {
             const int r = e / padw, j = j0 + e % padw;
-            const int64_t o = (orow0 + r) * kpad + j;
-            if (op_kind == 1 || op_kind == 4) {
-                reinterpret_cast<__nv_bfloat16 *>(opc)[o] = __float2bfloat16(0.0f);
-                if (op_kind == 4) reinterpret_cast<__nv_bfloat16 *>(opc_lo)[o] = __float2bfloat16(0.0f);
-            } else {
-                reinterpret_cast<float *>(opc)[o] = 0.0f;
-                if (op_kind == 2 || op_kind == 3) reinterpret_cast<float *>(opc_lo)[o] = 0.0f;
-            }
+            put_operand(opc, opc_lo, (orow0 + r) * kpad + j, op_kind, 0.0f, 0.0f);
         }
     }
 }
@@ -1131,68 +1104,6 @@ void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles,
     if (count <= 0) return;
     if (narrow) update_kernel<T, 16><<<count, 256, 0, s>>>(p, tasks, tiles, Aop, Bop, C, lower, from_r1);
     else update_kernel<T, 64><<<count, 256, 0, s>>>(p, tasks, tiles, Aop, Bop, C, lower, from_r1);
-}
-
-// ---------------------------------------------------------------------------
-// The same update as a standalone call (the paper's kernel study, Sec. V-B:
-// C = C - A B^T with B the first rows of A and C a taller gapped panel).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) update_standalone_kernel(
-    int m, int nb, int k, const double *__restrict__ A, int64_t lda, double *__restrict__ C,
-    int64_t ldc, const int32_t *__restrict__ rowmap, const int32_t *__restrict__ colmap, int lower)
-{
-    __shared__ double As[16][kUpdTile + 1];
-    __shared__ double Bs[16][kUpdTile + 1];
-    const int m0 = blockIdx.x * kUpdTile, n0 = blockIdx.y * kUpdTile;
-    if (lower && m0 + kUpdTile <= n0) return;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[4][4] = {};
-    const int lr = tid & 63, lk = tid >> 6;
-    for (int k0 = 0; k0 < k; k0 += 16) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int kk = lk + 4 * q, kg = k0 + kk;
-            const int ra = m0 + lr, rb = n0 + lr;
-            As[kk][lr] = (kg < k && ra < m) ? A[ra + (int64_t)kg * lda] : 0.0;
-            Bs[kk][lr] = (kg < k && rb < nb) ? A[rb + (int64_t)kg * lda] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            double av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = m0 + tx + 16 * a;
-        if (i >= m) continue;
-        const int64_t r = rowmap[i];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int j = n0 + ty + 16 * b;
-            if (j >= nb || (lower && i < j)) continue;
-            atomicAdd(C + r + (int64_t)colmap[j] * ldc, -acc[a][b]);
-        }
-    }
-}
-
-void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A, int64_t lda,
-                              double *C, int64_t ldc, const int32_t *rowmap,
-                              const int32_t *colmap, int lower, cudaStream_t s)
-{
-    dim3 grid((unsigned)((m + kUpdTile - 1) / kUpdTile), (unsigned)((nb + kUpdTile - 1) / kUpdTile));
-    if (grid.x == 0 || grid.y == 0) return;
-    update_standalone_kernel<<<grid, 256, 0, s>>>((int)m, (int)nb, (int)k, A, lda, C, ldc, rowmap,
-                                                  colmap, lower);
 }
 
 // explicit instantiations

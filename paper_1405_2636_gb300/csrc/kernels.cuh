@@ -113,10 +113,13 @@ template <typename T>
 void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles, int count,
                    const T *Aop, const T *Bop, T *C, int lower, int from_r1, cudaStream_t s, int narrow = 0);
 
-// The standalone update of the paper's kernel study (double).
-void launch_update_standalone(int64_t m, int64_t nb, int64_t k, const double *A, int64_t lda,
-                              double *C, int64_t ldc, const int32_t *rowmap,
-                              const int32_t *colmap, int lower, cudaStream_t s);
+// Operand copy of a column-major m x k panel A (ld lda; W: the D L^T rows
+// for op_kinds 3 / 4, same layout) into rows [0, m) of opc / opc_lo, kpad
+// elements per row, zero past k (kernel study; the factorization's TRSM
+// writes the same copy, operand.cuh).
+template <typename T>
+void launch_stage_operand(int64_t m, int k, const T *A, const T *W, int64_t lda, void *opc, void *opc_lo,
+                          int kpad, int op_kind, cudaStream_t s);
 
 // ---- solves ----------------------------------------------------------------
 // Vectors in the permuted numbering are of the factor's type T, column-major
@@ -143,7 +146,9 @@ struct SweepQueue {
     int32_t *cnt, *flag, *head;
     int32_t *err;
     int32_t mat_elems, matb_elems, vec_elems;   // shared-memory staging, elements of T (matb_elems 0: no chunks taken along)
+    uint32_t spin_limit;                        // polls of ~256 ns before a wait gives up
 };
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;   // about a second
 template <typename T>
 void launch_fwd_queue(const DevPlan &p, const SweepQueue &q, const RowChunk *chunks, const T *Dinv,
                       int unit, const T *L, T *Y, T *Z, int nrhs, cudaStream_t s);

@@ -29,7 +29,6 @@ namespace {
 
 constexpr int kQRhs = 16;                   // right-hand sides per pass
 constexpr int kQThreads = 256;
-constexpr unsigned kSpinLimit = 1u << 22;   // polls of ~256 ns: about a second
 
 __device__ __forceinline__ int ld_acquire(const int32_t *p)
 {
@@ -38,12 +37,12 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p)
     return v;
 }
 
-// Polled by one thread.  False, with *err set, after the polling limit, or
-// as soon as another CTA has reported a timeout.
-__device__ bool wait_geq(const int32_t *p, int target, int32_t *err)
+// Polled by one thread.  False, with *err set, after `limit` polls (of
+// about 256 ns each), or as soon as another CTA has reported a timeout.
+__device__ bool wait_geq(const int32_t *p, int target, int32_t *err, uint32_t limit)
 {
     if (ld_acquire(p) >= target) return true;
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         __nanosleep(it < 256 ? 32 : 256);
         if (ld_acquire(p) >= target) return true;
         if ((it & 1023) == 1023 && ld_acquire(err) != 0) return false;
@@ -62,10 +61,10 @@ __device__ __forceinline__ T ld_l2(const T *p)
 // Whole CTA: true once every polled counter reached its target.  Thread t
 // polls cnt[ids[t]] (ids == nullptr: thread 0 polls cnt[0]) for t < m.
 __device__ __forceinline__ bool cta_wait(const int32_t *cnt, const int32_t *ids, int m, int target,
-                                         int32_t *err)
+                                         int32_t *err, uint32_t limit)
 {
     int ok = 1;
-    if ((int)threadIdx.x < m) ok = wait_geq(cnt + (ids ? ids[threadIdx.x] : 0), target, err);
+    if ((int)threadIdx.x < m) ok = wait_geq(cnt + (ids ? ids[threadIdx.x] : 0), target, err, limit);
     return __syncthreads_and(ok) != 0;
 }
 
@@ -282,7 +281,7 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
                 stage_chunk(matB, 64, L + p.pval[pid], h, w, w, nr);
                 if (rt < nr) row = p.rows[p.prow[pid] + w + rt];
             }
-            if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err)) return;
+            if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err, q.spin_limit)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_vec(vec, Y, f, w, nc, n, c0);
@@ -324,7 +323,7 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
             const int nr = min(64, h - ch.r0);
             stage_chunk(matA, 64, L + p.pval[pid], h, w, ch.r0, nr);
             const int64_t row = rt < nr ? p.rows[p.prow[pid] + ch.r0 + rt] : 0;
-            if (!cta_wait(q.flag + pid, nullptr, 1, 1, q.err)) return;
+            if (!cta_wait(q.flag + pid, nullptr, 1, 1, q.err, q.spin_limit)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_vec(vec, Z, f, w, nc, n, c0);
@@ -422,8 +421,8 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
             // thread m on the panel's own chunks
             {
                 int ok = 1;
-                if (tid < m) ok = wait_geq(q.flag + q.tgt[t0 + tid], 1, q.err);
-                else if (tid == m) ok = wait_geq(q.cnt + pid, q.need[pid], q.err);
+                if (tid < m) ok = wait_geq(q.flag + q.tgt[t0 + tid], 1, q.err, q.spin_limit);
+                else if (tid == m) ok = wait_geq(q.cnt + pid, q.need[pid], q.err, q.spin_limit);
                 if (!__syncthreads_and(ok)) return;
             }
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
@@ -492,7 +491,7 @@ __global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, Swee
             stage_chunk(matA, 65, Lop + p.pval[pid], h, w, ch.r0, nr);
             const int64_t row = rt < nr ? p.rows[p.prow[pid] + ch.r0 + rt] : 0;
             const int t0 = q.tptr[item], t1 = q.tptr[item + 1];
-            if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err)) return;
+            if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err, q.spin_limit)) return;
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_rows(vec, X, row, nr, nc, n, c0);

@@ -32,8 +32,10 @@ STATUS_NAMES = {0: "SPX_OK", 1: "SPX_ERR_ARG", 2: "SPX_ERR_ALLOC", 3: "SPX_ERR_C
 # Every symbol include/spx.h declares.
 EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_factorize",
             "spx_solve", "spx_get_info", "spx_get_perm", "spx_get_factor", "spx_last_error",
-            "spx_free", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
-            "spx_get_panels", "spx_solve_noalloc",
+            "spx_free", "spx_set_profiling", "spx_get_kernel_stats",
+            "spx_get_panels", "spx_solve_noalloc", "spx_set_wait_limit", "spx_roofline_model",
+            "spx_update_create", "spx_update_stage", "spx_update_run", "spx_update_get_info",
+            "spx_update_last_error", "spx_update_free",
             "spx_batch_analyze", "spx_batch_run", "spx_batch_tune", "spx_batch_set_config",
             "spx_batch_get_info", "spx_batch_system_info", "spx_batch_get_perm",
             "spx_batch_get_factor", "spx_batch_last_error", "spx_batch_free",
@@ -69,7 +71,7 @@ class spx_info(ctypes.Structure):
         (name, ctypes.c_double) for name in ("flops", "flops_stored", "update_flops")] + [
         ("launches_factor", ctypes.c_int64), ("launches_solve", ctypes.c_int64)] + [
         (name, ctypes.c_double) for name in ("analyze_ms", "factor_ms", "solve_ms")] + [
-        ("npivot_neg", ctypes.c_int64)]
+        ("npivot_neg", ctypes.c_int64), ("noalloc_timeout", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -135,7 +137,17 @@ def load():
     lib.spx_solve_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _i64, _vp, _i64, _vp]
     lib.spx_free.argtypes = [_vp]
     lib.spx_free.restype = None
-    lib.spx_update.argtypes = [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]
+    lib.spx_set_wait_limit.argtypes = [_vp, _i64]
+    lib.spx_roofline_model.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    lib.spx_update_create.argtypes = [_i64, _i64, _i64, _i64, _i64, _vp, _vp, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
+    lib.spx_update_stage.argtypes = [_vp, _vp, _vp, _i64, _vp]
+    lib.spx_update_run.argtypes = [_vp, _vp, ctypes.c_int, _vp]
+    lib.spx_update_get_info.argtypes = [_vp, _vp, _vp]
+    lib.spx_update_last_error.argtypes = [_vp]
+    lib.spx_update_last_error.restype = ctypes.c_char_p
+    lib.spx_update_free.argtypes = [_vp]
+    lib.spx_update_free.restype = None
     lib.spx_batch_analyze.argtypes = [ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.POINTER(spx_options),
                                       ctypes.POINTER(_vp)]
     lib.spx_batch_run.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int,
@@ -156,8 +168,11 @@ def load():
     lib.spx_batch_free.argtypes = [_vp]
     lib.spx_batch_free.restype = None
     for name in ("spx_analyze", "spx_factorize", "spx_solve", "spx_get_info", "spx_get_perm",
-                 "spx_get_factor", "spx_update", "spx_set_profiling", "spx_get_kernel_stats",
-                 "spx_get_panels", "spx_solve_noalloc", "spx_batch_analyze", "spx_batch_run",
+                 "spx_get_factor", "spx_set_profiling", "spx_get_kernel_stats",
+                 "spx_get_panels", "spx_solve_noalloc", "spx_set_wait_limit", "spx_roofline_model",
+                 "spx_update_create",
+                 "spx_update_stage", "spx_update_run", "spx_update_get_info",
+                 "spx_batch_analyze", "spx_batch_run",
                  "spx_batch_tune", "spx_batch_set_config", "spx_batch_get_info",
                  "spx_batch_system_info", "spx_batch_get_perm", "spx_batch_get_factor",
                  "spx_logdet", "spx_selected_inverse", "spx_get_selected_inverse",
@@ -285,6 +300,19 @@ class Handle:
         _check(load().spx_get_info(self._h, ctypes.byref(i)), self._h)
         return i.as_dict()
 
+    def roofline_model(self, precision: str, hbm_gbs: float, fp64_gflops: float, fp32_gflops: float,
+                       tensor_gflops: float) -> dict:
+        """Per kernel class, the summed per-task roofline time (ms) of the
+        factorization in ``precision`` (spx_roofline_model)."""
+        peaks = np.array([hbm_gbs, fp64_gflops, fp32_gflops, tensor_gflops], dtype=np.float64)
+        out = np.zeros(len(KERNEL_CLASSES), dtype=np.float64)
+        _check(load().spx_roofline_model(self._h, PRECISIONS[precision], _ptr(peaks), _ptr(out)), self._h)
+        return {c: float(out[i]) for i, c in enumerate(KERNEL_CLASSES)}
+
+    def set_wait_limit(self, polls: int = 0):
+        """Polls (~256 ns each) before a sweep wait gives up; 0 = default."""
+        _check(load().spx_set_wait_limit(self._h, int(polls)), self._h)
+
     def set_profiling(self, on: bool = True):
         _check(load().spx_set_profiling(self._h, 1 if on else 0), self._h)
 
@@ -384,11 +412,73 @@ def analyze(colptr: np.ndarray, rowind: np.ndarray, method: str = "llt", perm=No
     return Handle(raw.value, n, int(colptr[-1]))
 
 
-def update(m, nb_rows, k, A, lda, C, ldc, rowmap, colmap, lower=True, stream=None):
-    """spx_update on CUDA tensors (the supernodal update kernel on its own)."""
-    st = load().spx_update(m, nb_rows, k, _ptr(A), lda, _ptr(C), ldc, _ptr(rowmap), _ptr(colmap),
-                           1 if lower else 0, _stream_ptr(stream))
-    _check(st, None)
+ENGINES = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
+
+
+def _ucheck(status: int, plan=None):
+    if status != SPX_OK:
+        msg = load().spx_update_last_error(plan)
+        raise SpxError(status, msg.decode() if msg else "")
+
+
+class UpdatePlan:
+    """One (source, target) update task run through the factorization's own
+    update kernels (spx_update_*): C -= A B^T, B the first nb_rows rows of A
+    (of W for LDL^T), row i of A to row rowmap[i] of C, row j of B to column
+    colmap[j]."""
+
+    def __init__(self, m, nb_rows, k, ldc, nc, rowmap, colmap, lower=True, precision="fp64",
+                 engine="auto", ldlt=False):
+        rowmap = np.ascontiguousarray(rowmap, dtype=np.int32)
+        colmap = np.ascontiguousarray(colmap, dtype=np.int32)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        eng = ENGINES[engine] if isinstance(engine, str) else int(engine)
+        raw = _vp()
+        _ucheck(load().spx_update_create(m, nb_rows, k, ldc, nc, _ptr(rowmap), _ptr(colmap),
+                                         1 if lower else 0, prec, eng, 1 if ldlt else 0,
+                                         ctypes.byref(raw)), None)
+        self._u = raw.value
+        self.m, self.k = m, k
+
+    def free(self):
+        if self._u:
+            load().spx_update_free(self._u)
+            self._u = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stage(self, A, W=None, lda=None, stream=None):
+        """A (and W): CUDA tensors, column-major m x k (``X.t().contiguous().t()``)."""
+        lda = lda if lda is not None else (A.stride(1) if A.dim() == 2 else self.m)
+        _ucheck(load().spx_update_stage(self._u, _ptr(A), _ptr(W), lda, _stream_ptr(stream)), self._u)
+
+    def run(self, C, wait=True, stream=None):
+        _ucheck(load().spx_update_run(self._u, _ptr(C), 1 if wait else 0, _stream_ptr(stream)), self._u)
+
+    def info(self) -> dict:
+        e = ctypes.c_int32()
+        t = ctypes.c_int64()
+        _ucheck(load().spx_update_get_info(self._u, ctypes.byref(e), ctypes.byref(t)), self._u)
+        return {"engine": {1: "cuda_cores", 2: "tensor_cores"}[e.value], "tiles": t.value}
+
+
+def update(A, C, rowmap, colmap, nb_rows, lower=True, precision="fp64", engine="auto", W=None,
+           stream=None):
+    """C -= A B^T once through the factorization's update kernels (creates,
+    stages, runs and frees an UpdatePlan).  A, W, C: column-major CUDA tensors."""
+    m, k = A.shape
+    ldc, nc = C.shape
+    plan = UpdatePlan(m, nb_rows, k, C.stride(1), nc, rowmap, colmap, lower=lower,
+                      precision=precision, engine=engine, ldlt=W is not None)
+    try:
+        plan.stage(A, W, stream=stream)
+        plan.run(C, wait=True, stream=stream)
+    finally:
+        plan.free()
 
 
 # ---------------------------------------------------------------------------

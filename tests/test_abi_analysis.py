@@ -175,6 +175,44 @@ def test_calls_on_null_or_unfactored_handles_fail_cleanly():
     assert b"factorize" in lib.spx_last_error(h._h)
 
 
+def test_wait_limit_on_an_analysed_handle():
+    """spx_set_wait_limit needs no GPU: it checks its argument and keeps the
+    value for the next sweeps."""
+    A = inputs.laplacian_2d(9, 9)
+    cp, ri, _ = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "llt")
+    for bad in (-1, 2 ** 32):
+        with pytest.raises(spx.SpxError) as e:
+            h.set_wait_limit(bad)
+        assert e.value.status == spx.SPX_ERR_ARG
+    h.set_wait_limit(2 ** 32 - 1)
+    h.set_wait_limit(0)
+    assert spx.load().spx_set_wait_limit(None, 0) == spx.SPX_ERR_ARG
+    h.free()
+
+
+def test_update_plan_rejects_bad_arguments():
+    """The kernel-study plan checks sizes, maps and the engine before it
+    touches the device."""
+    rm = np.arange(10, dtype=np.int32)
+    cm = np.arange(4, dtype=np.int32)
+    bad = [dict(m=10, nb_rows=11, k=8, ldc=10, nc=4),              # nb_rows > m
+           dict(m=10, nb_rows=4, k=0, ldc=10, nc=4),               # k = 0
+           dict(m=10, nb_rows=4, k=8, ldc=9, nc=4),                # rowmap reaches ldc
+           dict(m=10, nb_rows=4, k=8, ldc=10, nc=3)]               # colmap reaches nc
+    for b in bad:
+        with pytest.raises(spx.SpxError) as e:
+            spx.UpdatePlan(b["m"], b["nb_rows"], b["k"], b["ldc"], b["nc"], rm, cm)
+        assert e.value.status == spx.SPX_ERR_ARG
+    for prec, ldlt in (("fp64", False), ("fp32", True)):
+        with pytest.raises(spx.SpxError) as e:   # no tensor-core form of these
+            spx.UpdatePlan(10, 4, 8, 10, 4, rm, cm, precision=prec, engine="tensor_cores", ldlt=ldlt)
+        assert e.value.status == spx.SPX_ERR_ARG
+    lib = spx.load()
+    assert lib.spx_update_run(None, None, 1, None) == spx.SPX_ERR_ARG
+    lib.spx_update_free(None)
+
+
 def test_update_task_structure_invariants():
     """Every source row below a facing block lies in its target (Sec. V-B:
     each block of the source lies inside one block of the facing panel)."""

@@ -93,6 +93,7 @@ def test_ldlt_mixed_precision_and_refinement(torch, prec, bound):
     h.factorize(vals, prec)
     Lx = h.factor_on_pattern(F.sym.Lp, F.sym.Li)
     assert _rel(Lx, F.Lx) <= bound
+    assert np.max(np.abs(Lx - F.Lx)) <= bound * np.max(np.abs(F.Lx))   # entry by entry
     B = inputs.rhs(A.shape[0], 4, 10)
     X, sinfo = h.solve(B, refine=spx.default_refine(tol=1e-12))
     assert sinfo["converged"]

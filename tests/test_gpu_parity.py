@@ -154,6 +154,30 @@ def test_lu_fp64_matches_oracle(torch, name, maker, opts):
     assert oracle.backward_error(A, X, B) <= 1e-13
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("name,maker,opts", LU_CASES[:2], ids=[c[0] for c in LU_CASES[:2]])
+def test_lu_single_precision_factor_and_refinement(torch, name, maker, opts, prec):
+    """The single-system LU with a single-precision factor (the panel
+    updates run on the CUDA cores in FP32 for every single-precision mode of
+    LU): L and U against the FP64 oracle, relative and entry by entry, then
+    FP64 refinement to backward error 1e-12."""
+    A = maker()
+    cp, ri, vals = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "lu", **opts)
+    F = oracle.lu(A, h.perm())
+    h.factorize(vals, prec)
+    Lx, Ut = h.factor_on_pattern(F.sym.Lp, F.sym.Li, lu=True)
+    for got, ref in ((Lx, F.Lx), (Ut, F.Ut)):
+        assert _rel(got, ref) <= 1e-4
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    assert h.info()["npivot_repl"] == 0
+    B = inputs.rhs(A.shape[0], 3, 8)
+    X, info = h.solve(B, refine=spx.default_refine(tol=1e-12))
+    assert info["converged"], info
+    assert oracle.backward_error(A, X, B) <= 1e-12
+    h.free()
+
+
 def test_lu_static_pivot_hand_example(torch):
     """[[0, 1], [1, 1]]: the zero pivot becomes tau = 2^-25 (Sec. III static
     pivoting, threshold sqrt(eps) ||A||_inf); L(1,0) = 2^25, U(1,1) = 1 - 2^25."""
@@ -188,6 +212,9 @@ def test_mixed_precision_factor_and_refinement(torch, prec):
     err = _rel(Lx, F.Lx)
     bound = {"fp32": 1e-4, "tf32": 2e-2, "bf16": 1e-1}[prec]
     assert err <= bound
+    # entry by entry as well: no entry may be off by more than the bound
+    # times the largest entry (a dropped or misplaced update would be)
+    assert np.max(np.abs(Lx - F.Lx)) <= bound * np.max(np.abs(F.Lx))
     B = inputs.rhs(A.shape[0], 4, 3)
     X, info = h.solve(B, refine=spx.default_refine(tol=1e-12))
     assert info["converged"], info
@@ -197,20 +224,15 @@ def test_mixed_precision_factor_and_refinement(torch, prec):
 def test_update_kernel_on_the_papers_synthetic_panels(torch):
     """Sec. V-B kernel study: C = C - A B^T with B the first rows of A, C a
     panel twice as tall as A cut into random blocks of ~200 rows, A's blocks
-    inside C's blocks."""
+    inside C's blocks; FP64 through the factorization's CUDA-core update
+    kernel (spx.update), against the oracle's panel update."""
     for (m, k, nb, lower, seed) in [(300, 64, 100, 0, 1), (1000, 128, 257, 1, 2),
                                     (65, 1, 65, 1, 3), (777, 33, 64, 0, 4), (2048, 160, 511, 1, 5)]:
         A, C, rowmap, colmap = inputs.gapped_update_case(m, k, nb, seed)
-        W = A @ A[:nb].T
-        expect = C.copy()
-        for j in range(nb):
-            rows = np.arange(m) if not lower else np.arange(j, m)
-            expect[rowmap[rows], colmap[j]] -= W[rows, j]
+        expect = oracle.panel_update(A, A[:nb], C, rowmap, colmap, bool(lower))
         tA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
         tC = torch.from_numpy(np.ascontiguousarray(C.T)).cuda().t()
-        spx.update(m, nb, k, tA, m, tC, C.shape[0], torch.from_numpy(rowmap).cuda(),
-                   torch.from_numpy(colmap).cuda(), lower=bool(lower))
-        torch.cuda.synchronize()
+        spx.update(tA, tC, rowmap, colmap, nb, lower=bool(lower))
         got = tC.cpu().numpy()
         assert np.max(np.abs(got - expect)) <= 1e-12 * max(1.0, np.max(np.abs(expect)))
 

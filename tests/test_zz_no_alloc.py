@@ -32,30 +32,77 @@ def _colmajor(torch, M):
     return torch.from_numpy(np.ascontiguousarray(M.T)).cuda().t()
 
 
-def _noalloc(torch, h, Bd, nrhs):
+def _noalloc(torch, h, Bd, nrhs, check_free=False):
     n = h.n
     Xd = torch.full((nrhs, n), float("nan"), dtype=torch.float64, device="cuda").t()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     st = spx.load().spx_solve_noalloc(h._h, nrhs, Bd.data_ptr(), n, Xd.data_ptr(), n, None)
     assert st == spx.SPX_OK, spx.load().spx_last_error(h._h)
     torch.cuda.synchronize()
+    if check_free:   # the call itself took no device memory
+        assert torch.cuda.mem_get_info()[0] == free0
     return Xd.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_noalloc_solve_matches_spx_solve(torch, prec, tol):
+CASES = [  # method, precision, tolerance against spx_solve without refinement
+    ("llt", "fp64", 1e-12), ("llt", "fp32", 1e-5),
+    ("lu", "fp64", 1e-12), ("ldlt", "fp64", 1e-12),
+]
+
+
+def _system(method):
+    if method == "lu":
+        A = inputs.convection_diffusion_2d(47, 21)[0]
+        return A, dict(ordering=spx.SPX_ORDER_GRID, grid=(47, 47, 1), max_width=48)
+    if method == "ldlt":
+        A = inputs.quasi_definite_3d(9, 8, 7, 21)
+        return A, dict(ordering=spx.SPX_ORDER_GRID, grid=(9, 8, 7), dof=2, max_width=48)
     A = inputs.diffusion_3d(14, 13, 12, 21)
+    return A, dict(ordering=spx.SPX_ORDER_GRID, grid=(14, 13, 12), max_width=48)
+
+
+@pytest.mark.parametrize("method,prec,tol", CASES)
+def test_noalloc_solve_matches_spx_solve(torch, method, prec, tol):
+    A, opts = _system(method)
     cp, ri, vals = inputs.csc_arrays(A)
-    h = spx.analyze(cp, ri, "llt", ordering=spx.SPX_ORDER_GRID, grid=(14, 13, 12), max_width=48)
+    h = spx.analyze(cp, ri, method, **opts)
     h.factorize(vals, prec)
     nrhs = 5
     B = inputs.rhs(A.shape[0], nrhs, 21)
     Bd = _colmajor(torch, B)
     X_ref, _ = h.solve(Bd, refine=spx.default_refine(mode=0))
     X_ref = X_ref.cpu().numpy()
-    for _ in range(2):   # the second call starts from the first call's buffer contents
-        X = _noalloc(torch, h, Bd, nrhs)
+    for call in range(2):   # the second call starts from the first call's buffer contents
+        X = _noalloc(torch, h, Bd, nrhs, check_free=call == 1)
         assert np.all(np.isfinite(X))
         assert np.linalg.norm(X - X_ref) / np.linalg.norm(X_ref) <= tol
+        assert h.info()["noalloc_timeout"] == 0
+    h.free()
+
+
+def test_noalloc_timeout_is_reported_and_does_not_carry_over(torch):
+    """A wait of the allocation-free solve that runs out (a one-poll wait
+    limit) is recorded for that call alone: the next call, with the default
+    limit, is correct and reports no timeout, and spx_solve is not blamed."""
+    g = (24, 24, 24)     # a tree with a chain of single-panel levels at the top
+    A = inputs.diffusion_3d(*g, 5)
+    cp, ri, vals = inputs.csc_arrays(A)
+    h = spx.analyze(cp, ri, "llt", ordering=spx.SPX_ORDER_GRID, grid=g, max_width=64)
+    h.factorize(vals, "fp64")
+    B = inputs.rhs(A.shape[0], 3, 5)
+    Bd = _colmajor(torch, B)
+    X_ref, _ = h.solve(Bd, refine=spx.default_refine(mode=0))
+    X_ref = X_ref.cpu().numpy()
+    h.set_wait_limit(1)
+    _noalloc(torch, h, Bd, 3)
+    assert h.info()["noalloc_timeout"] == 1
+    h.set_wait_limit(0)
+    X = _noalloc(torch, h, Bd, 3)
+    assert h.info()["noalloc_timeout"] == 0
+    assert np.linalg.norm(X - X_ref) / np.linalg.norm(X_ref) <= 1e-12
+    X2, info = h.solve(Bd, refine=spx.default_refine(mode=0))
+    assert info["status"] == "SPX_OK"
     h.free()
 
 
