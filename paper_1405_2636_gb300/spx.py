@@ -453,7 +453,8 @@ class UpdatePlan:
 
     def stage(self, A, W=None, lda=None, stream=None):
         """A (and W): CUDA tensors, column-major m x k (``X.t().contiguous().t()``)."""
-        lda = lda if lda is not None else (A.stride(1) if A.dim() == 2 else self.m)
+        if lda is None:   # a size-1 dimension may carry any stride
+            lda = A.stride(1) if A.dim() == 2 and A.shape[1] > 1 else self.m
         _ucheck(load().spx_update_stage(self._u, _ptr(A), _ptr(W), lda, _stream_ptr(stream)), self._u)
 
     def run(self, C, wait=True, stream=None):
@@ -471,8 +472,9 @@ def update(A, C, rowmap, colmap, nb_rows, lower=True, precision="fp64", engine="
     """C -= A B^T once through the factorization's update kernels (creates,
     stages, runs and frees an UpdatePlan).  A, W, C: column-major CUDA tensors."""
     m, k = A.shape
-    ldc, nc = C.shape
-    plan = UpdatePlan(m, nb_rows, k, C.stride(1), nc, rowmap, colmap, lower=lower,
+    nc = C.shape[1]
+    ldc = C.stride(1) if nc > 1 else C.shape[0]
+    plan = UpdatePlan(m, nb_rows, k, ldc, nc, rowmap, colmap, lower=lower,
                       precision=precision, engine=engine, ldlt=W is not None)
     try:
         plan.stage(A, W, stream=stream)
