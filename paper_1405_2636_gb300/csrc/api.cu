@@ -65,6 +65,8 @@ struct spx_handle_s {
     int32_t q_nitems = 0, q_mat = 0, q_matb = 0, q_vec = 0;
     uint32_t spin_limit = spx::kDefaultSpinLimit;   // polls before a sweep wait gives up
     int32_t *h_noalloc_err = nullptr;   // pinned: the error word of the last completed spx_solve_noalloc
+    void *h_stage[2] = {nullptr, nullptr};  // pinned staging buffers for host-buffer copies
+    cudaEvent_t ev_stage[2] = {nullptr, nullptr};
     UpdTile *d_tcsmall = nullptr;
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
@@ -715,6 +717,95 @@ spx_status ensure_operand_copy(spx_handle h, int kind)
     return SPX_OK;
 }
 
+// Copies between the caller's (pageable) host buffers and the device go
+// through two pinned staging buffers owned by the handle: the host packs or
+// unpacks one buffer while the copy engine moves the other, so pageable
+// memory never takes the driver's slow bounce path.  The device side is
+// contiguous (`cols` columns of `col_bytes`); the host side has pitch
+// `hpitch`.  Ordered on h->hs.
+constexpr size_t kStageBytes = (size_t)8 << 20;
+
+spx_status ensure_stage(spx_handle h)
+{
+    for (int b = 0; b < 2; ++b) {
+        if (!h->h_stage[b]) CU(cudaHostAlloc(&h->h_stage[b], kStageBytes, cudaHostAllocDefault));
+        if (!h->ev_stage[b]) CU(cudaEventCreateWithFlags(&h->ev_stage[b], cudaEventDisableTiming));
+    }
+    return SPX_OK;
+}
+
+// walk the host side of a (cols x col_bytes) block in chunks of at most
+// kStageBytes; fn(host_piece, bytes, offset_in_chunk) for each piece
+template <typename F>
+size_t chunk_pieces(size_t pos, size_t total, size_t col_bytes, size_t hpitch, char *host, F fn)
+{
+    const size_t len = std::min(kStageBytes, total - pos);
+    size_t done = 0;
+    while (done < len) {
+        const size_t col = (pos + done) / col_bytes, off = (pos + done) % col_bytes;
+        const size_t piece = std::min(len - done, col_bytes - off);
+        fn(host + col * hpitch + off, piece, done);
+        done += piece;
+    }
+    return len;
+}
+
+spx_status staged_h2d(spx_handle h, void *dev, const void *host, size_t hpitch, size_t col_bytes, size_t cols)
+{
+    spx_status st = ensure_stage(h);
+    if (st != SPX_OK) return st;
+    const size_t total = col_bytes * cols;
+    bool busy[2] = {false, false};
+    int b = 0;
+    for (size_t pos = 0; pos < total; b ^= 1) {
+        if (busy[b]) CU(cudaEventSynchronize(h->ev_stage[b]));
+        char *stage = (char *)h->h_stage[b];
+        const size_t len = chunk_pieces(pos, total, col_bytes, hpitch, (char *)host,
+                                        [&](const char *src, size_t bytes, size_t at) {
+                                            std::memcpy(stage + at, src, bytes);
+                                        });
+        CU(cudaMemcpyAsync((char *)dev + pos, stage, len, cudaMemcpyHostToDevice, h->hs));
+        CU(cudaEventRecord(h->ev_stage[b], h->hs));
+        busy[b] = true;
+        pos += len;
+    }
+    return SPX_OK;
+}
+
+spx_status staged_d2h(spx_handle h, void *host, size_t hpitch, const void *dev, size_t col_bytes, size_t cols)
+{
+    spx_status st = ensure_stage(h);
+    if (st != SPX_OK) return st;
+    const size_t total = col_bytes * cols;
+    size_t pend_pos[2] = {0, 0};
+    bool busy[2] = {false, false};
+    auto drain = [&](int b) -> spx_status {
+        CU(cudaEventSynchronize(h->ev_stage[b]));
+        const char *stage = (const char *)h->h_stage[b];
+        chunk_pieces(pend_pos[b], total, col_bytes, hpitch, (char *)host,
+                     [&](const char *dst, size_t bytes, size_t at) {
+                         std::memcpy(const_cast<char *>(dst), stage + at, bytes);
+                     });
+        busy[b] = false;
+        return SPX_OK;
+    };
+    int b = 0;
+    for (size_t pos = 0; pos < total; b ^= 1) {
+        if (busy[b] && (st = drain(b))) return st;
+        const size_t len = std::min(kStageBytes, total - pos);
+        CU(cudaMemcpyAsync(h->h_stage[b], (const char *)dev + pos, len, cudaMemcpyDeviceToHost, h->hs));
+        CU(cudaEventRecord(h->ev_stage[b], h->hs));
+        busy[b] = true;
+        pend_pos[b] = pos;
+        pos += len;
+        // unpack the other buffer while this chunk is in flight
+        if (busy[b ^ 1] && (st = drain(b ^ 1))) return st;
+    }
+    for (int q = 0; q < 2; ++q)
+        if (busy[q] && (st = drain(q))) return st;
+    return SPX_OK;
+}
+
 void body_sweep(spx_handle h, int nrhs, bool fp64)
 {
     if (fp64) enqueue_sweep<double>(h, nrhs);
@@ -1101,8 +1192,10 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         if ((st = ensure_operand_copy(h, operand_kind(P.method, precision)))) return st;
     }
     fence_from(h, cuda_stream);
-    CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a,
-                       values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->hs));
+    if (values_on_device)
+        CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a, cudaMemcpyDeviceToDevice, h->hs));
+    else if ((st = staged_h2d(h, h->d_vals, values, 0, sizeof(double) * (size_t)P.nnz_a, 1)))
+        return st;
     Marks mk{h, h->profiling};
     if (h->profiling) {
         h->cnt = 0;
@@ -1217,9 +1310,11 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
     if (st != SPX_OK) return st;
     fence_from(h, cuda_stream);
     const size_t n = (size_t)P.n;
-    CU(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, (size_t)ldb * sizeof(double),
-                         n * sizeof(double), nrhs,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->hs));
+    if (on_device)
+        CU(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, (size_t)ldb * sizeof(double), n * sizeof(double),
+                             nrhs, cudaMemcpyDeviceToDevice, h->hs));
+    else if ((st = staged_h2d(h, h->d_B, B, (size_t)ldb * sizeof(double), n * sizeof(double), (size_t)nrhs)))
+        return st;
     if (h->sgraph_nrhs != nrhs || h->sgraph_prec != h->precision || !h->sgraph) {
         if ((st = capture(h, &h->sgraph, body_sweep, nrhs, fp64))) return st;
         h->sgraph_nrhs = nrhs;
@@ -1255,9 +1350,11 @@ spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, d
         si.converged = (rf.mode == 0) ? 1 : (berr <= rf.tol);
     }
     CU(cudaEventRecord(h->ev_t1, h->hs));
-    CU(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), h->d_X, n * sizeof(double),
-                         n * sizeof(double), nrhs,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->hs));
+    if (on_device)
+        CU(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), h->d_X, n * sizeof(double), n * sizeof(double),
+                             nrhs, cudaMemcpyDeviceToDevice, h->hs));
+    else if ((st = staged_d2h(h, X, (size_t)ldx * sizeof(double), h->d_X, n * sizeof(double), (size_t)nrhs)))
+        return st;
     CU(cudaMemcpyAsync(&qerr, h->d_qerr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaStreamSynchronize(h->hs));
     if (qerr) {
@@ -1685,6 +1782,10 @@ void spx_free(spx_handle h)
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
     if (h->hs) cudaStreamDestroy(h->hs);
     if (h->h_noalloc_err) cudaFreeHost(h->h_noalloc_err);
+    for (int b = 0; b < 2; ++b) {
+        if (h->h_stage[b]) cudaFreeHost(h->h_stage[b]);
+        if (h->ev_stage[b]) cudaEventDestroy(h->ev_stage[b]);
+    }
     delete h;
 }
 
