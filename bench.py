@@ -76,7 +76,14 @@ def class_roofline(cls: str, st: dict, mode: str, peaks: dict) -> dict:
                              "peak_source": ("measured bf16" if mode == "bf16" else
                                              "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)")}
         return out
-    fp64_arith = mode == "fp64" or cls == "diag"
+    if cls == "queue" and mode != "fp64":
+        # the task-queue launch of the upper levels: its flops are mostly tensor-core updates
+        tpeak = peaks["bf16_tflops"] * (1.0 if mode == "bf16" else NOMINAL_TF32_OVER_BF16)
+        tach = st["flops"] / (ms / 1e3) / 1e12
+        out.update({"bound": "tensor", "achieved": tach, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": tach / tpeak, "peak_source": peaks["source"]})
+        return out
+    fp64_arith = mode == "fp64" or cls in ("diag", "queue")
     peak = FP64_ALU_PEAK_GFLOPS if fp64_arith else FP32_ALU_PEAK_GFLOPS
     ach = st["flops"] / (ms / 1e3) / 1e9
     out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
@@ -679,6 +686,7 @@ def main():
     roofline["kernel"] = {"diag": "potrf_ldl_kernel / potrf_kernel (FP64 diagonal blocks)",
                           "trsm": "trsm_gemm_kernel", "update": "update_kernel (CUDA cores)",
                           "update_tc": "update_tc_kernel (tcgen05)",
+                          "queue": "factor_queue_kernel (persistent task queue of the upper levels)",
                           "assemble": "assemble_kernel"}[dominant]
 
     extra = {}

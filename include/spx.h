@@ -78,7 +78,11 @@ typedef struct {
     double amalg_ratio;     /* amalgamation may add this fraction of nnz(L) as explicit zeros (Sec. V: 12%); <0 = default 0.12 */
     const int64_t *perm;    /* SPX_ORDER_GIVEN: new -> old permutation of length n (copied) */
     int32_t lower_only;     /* 1: the CSC holds only the lower triangle of a symmetric matrix (LLT only) */
-    int32_t reserved0;
+    int32_t queue_panels;   /* levels of the panel tree run as one persistent launch over a device-side
+                               task queue (Cholesky, LDL^T; panels at most 64 wide): > 0 = the top levels
+                               holding at most this many panels; < 0 = none (every level launched on its
+                               own); 0 = default: the whole tree for an FP64 factor, none for the
+                               single-precision factors (the policy that measured fastest) */
     double pivot_tau;       /* LU static-pivot threshold; < 0 = sqrt(2^-52) * ||A||_inf at factorize */
 } spx_options;
 
@@ -272,7 +276,8 @@ enum {
     SPX_K_TRSM = 2,       /* panel triangular solves */
     SPX_K_UPDATE = 3,     /* supernodal updates with fused scatter, CUDA cores */
     SPX_K_UPDATE_TC = 4,  /* supernodal updates with fused scatter, tensor cores (tcgen05) */
-    SPX_K_CLASSES = 5
+    SPX_K_QUEUE = 5,      /* the upper levels' persistent task-queue launch (all three steps) */
+    SPX_K_CLASSES = 6
 };
 
 typedef struct {
@@ -284,7 +289,8 @@ typedef struct {
 
 /* on = 1: the next factorizations run launch by launch (no graph) with CUDA
  * events around every kernel class of every level, on the library's stream,
- * and spx_get_kernel_stats reports the accumulated per-class device time. */
+ * and spx_get_kernel_stats reports the accumulated per-class device time.
+ * The work of the levels in the task queue is counted in SPX_K_QUEUE. */
 spx_status spx_set_profiling(spx_handle h, int on);
 spx_status spx_get_kernel_stats(spx_handle h, spx_kernel_stats *out);
 

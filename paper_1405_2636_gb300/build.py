@@ -23,14 +23,14 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 
 CU_SOURCES = ["api.cu", "factor.cu", "solve.cu", "update_tc.cu", "batch_api.cu", "batch_lu.cu", "selinv.cu",
-              "sweep.cu", "study.cu"]
+              "sweep.cu", "study.cu", "fqueue_f64.cu", "fqueue_tc.cu", "fqueue_ldlt.cu"]
 CXX_SOURCES = ["analyze.cpp"]
-HEADERS = ["kernels.cuh", "spx_plan.h", "batch_kernel.cuh", "operand.cuh"]
+HEADERS = ["kernels.cuh", "spx_plan.h", "batch_kernel.cuh", "operand.cuh", "blocks.cuh", "tc_common.cuh", "fqueue.cuh"]
 
 
 def _sources():
     return [os.path.join(CSRC, f) for f in CU_SOURCES + CXX_SOURCES + HEADERS] + [
-        os.path.join(INCLUDE, "spx.h")]
+        os.path.join(INCLUDE, "spx.h"), os.path.abspath(__file__)]
 
 
 def needs_build() -> bool:
@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("libspx build failed:\n" + "\n".join(failed))
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
+    link = [NVCC] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("libspx link failed:\n" + r.stdout.decode(errors="replace"))

@@ -15,7 +15,9 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <queue>
 #include <string>
+#include <utility>
 #include <vector>
 
 using spx::DevTask;
@@ -45,7 +47,7 @@ struct spx_handle_s {
     // panels of a level sorted by width class (kWidthClass); class c of level l
     // is d_level_panels[cls_ptr[l * kNumClasses + c] .. cls_ptr[l * kNumClasses + c + 1])
     std::vector<int32_t> cls_ptr;
-    int64_t dinv_elems = 0;           // sum of w^2 over panels
+    int64_t dinv_elems = 0;           // sum over panels of w^2 rounded up to 32
     std::vector<int64_t> chunk_ptr;   // per level, into d_chunks
     RowChunk *d_chunks = nullptr;
     // Each per-level tile list holds the 64 x 64 tiles first, then the 256 x 16
@@ -68,6 +70,16 @@ struct spx_handle_s {
     void *h_stage[2] = {nullptr, nullptr};  // pinned staging buffers for host-buffer copies
     cudaEvent_t ev_stage[2] = {nullptr, nullptr};
     UpdTile *d_tcsmall = nullptr;
+    // persistent task queue of the upper levels (Cholesky and LDL^T, panels
+    // at most 64 wide): levels [q_level, nlevels) run as one launch.  Two item
+    // lists: updates on the tensor cores (tc modes) or all on the CUDA cores.
+    int32_t queue_panels = 0;         // option: 0 default policy, > 0 region bound, < 0 no queue
+    int32_t q_level = 0;              // first level of the region the item lists were built for
+    spx::FqItem *d_fq_items[2] = {nullptr, nullptr};   // [0] CUDA cores, [1] tensor cores
+    int32_t fq_nitems[2] = {0, 0};
+    int32_t *d_fq_need[2] = {nullptr, nullptr};
+    int32_t *d_fq_pchunk = nullptr, *d_fq_state = nullptr;
+    int64_t fq_nchunks = 0;
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
     int kpad = 0;                     // operand-copy row length
@@ -210,6 +222,270 @@ __global__ void set_tau_kernel(const unsigned long long *anorm_bits, double fixe
     *tau = fixed >= 0.0 ? fixed : scale * a;
 }
 
+// Algorithmic work of every panel and update task, as the kernel classes
+// count it: fn(class, level, flops, elements of the factor's type, elements
+// of the tensor-core operand copy, FP32 target elements) -- diagonal block
+// and TRSM per panel (Sec. III steps 1, 2), one update per task (step 3).
+template <typename F>
+void visit_work(const spx::Plan &P, bool tcm, F fn)
+{
+    const bool lu = P.method == SPX_LU;
+    const double nfac = lu ? 2.0 : 1.0;
+    for (int32_t q = 0; q < P.npanels; ++q) {
+        const double w = P.pw[q], off = (double)P.ph[q] - P.pw[q];
+        double df = 0.0;
+        for (int32_t j = 0; j < P.pw[q]; ++j) {
+            const double c = w - j;
+            df += lu ? 2.0 * (c - 1.0) * (c - 1.0) + (c - 1.0) : c * c;
+        }
+        fn(SPX_K_DIAG, P.plevel[q], df, 2.0 * w * w, 0.0, 0.0);
+        fn(SPX_K_TRSM, P.plevel[q], nfac * off * w * w, nfac * (2.0 * off * w + w * w), 0.0, 0.0);
+    }
+    for (const spx::Task &tk : P.tasks) {
+        const double M = (double)P.ph[tk.src] - tk.r0, N = (double)tk.r1 - tk.r0, K = P.pw[tk.src];
+        double flops, el_op, el_acc;
+        if (!lu) {
+            flops = 2.0 * (M - N) * N * K + N * (N + 1.0) * K;
+            el_op = (M + N) * K;
+            el_acc = 2.0 * ((M - N) * N + N * (N + 1.0) / 2.0);
+        } else {
+            flops = 2.0 * M * N * K + 2.0 * (M - N) * N * K;
+            el_op = (M + N) * K + M * K;
+            el_acc = 2.0 * (M * N + (M - N) * N);
+        }
+        const int lvl = P.plevel[tk.src];
+        if (tcm && P.pw[tk.src] >= kTcMinWidth) fn(SPX_K_UPDATE_TC, lvl, flops, 0.0, el_op, el_acc);
+        else fn(SPX_K_UPDATE, lvl, flops, el_op + el_acc, 0.0, 0.0);
+    }
+}
+
+// First level of the persistent queue region: the top levels whose panel
+// count is at most qmax and whose panels are at most 64 wide (the queue's
+// diagonal-block bodies); LU keeps the level-by-level walk.  nlevels: none.
+int queue_start_level(const spx::Plan &P, int qmax)
+{
+    if (P.method == SPX_LU || qmax < 0) return P.nlevels;
+    int l = P.nlevels;
+    while (l > 0) {
+        const int lv = l - 1;
+        if (P.level_ptr[lv + 1] - P.level_ptr[lv] > qmax) break;
+        bool narrow = true;
+        for (int32_t q = P.level_ptr[lv]; q < P.level_ptr[lv + 1]; ++q) narrow = narrow && P.pw[P.level_panels[q]] <= 64;
+        if (!narrow) break;
+        l = lv;
+    }
+    return l;
+}
+
+// The queue region a factorization in `prec` uses.  qopt > 0: the top
+// levels with at most qopt panels; qopt < 0: none; qopt = 0 (default): the
+// whole tree (as far as panels are at most 64 wide) for an FP64 factor,
+// where the queue measured faster than the level walk (its update tiles are
+// long FP64 products), and none for the single-precision factors, whose
+// short tensor-core and FP32 tiles ran faster as per-level launches.
+int queue_policy_level(const spx::Plan &P, int qopt, int prec)
+{
+    if (qopt < 0 || (qopt == 0 && prec != SPX_FP64)) return P.nlevels;
+    return queue_start_level(P, qopt == 0 ? INT32_MAX : qopt);
+}
+
+int32_t queue_level(spx_handle h, int prec)
+{
+    const spx::Plan &P = h->plan;
+    if (h->q_level >= P.nlevels) return P.nlevels;
+    return queue_policy_level(P, h->queue_panels, prec) >= P.nlevels ? P.nlevels : h->q_level;
+}
+
+// Item lists of the queue region (fqueue.cuh): per level l, its diagonal
+// blocks; the far update tiles of level l-1 (targets above level l); its
+// TRSM chunks; its near update tiles (targets at level l+1).  Every wait is
+// then on an earlier item, which is checked here before anything is uploaded.
+spx_status build_queue(spx_handle h, const std::vector<RowChunk> &chunks, const std::vector<UpdTile> &tiles,
+                       const std::vector<UpdTile> &small, const std::vector<spx::TcTile> &tct, int workers)
+{
+    const spx::Plan &P = h->plan;
+    const int L0 = queue_start_level(P, h->queue_panels == 0 ? INT32_MAX : h->queue_panels);
+    h->q_level = L0;
+    if (L0 >= P.nlevels) return SPX_OK;
+    const int32_t np = P.npanels;
+    const int64_t nch = (int64_t)chunks.size();
+    std::vector<int32_t> pchunk(np, -1);
+    for (int64_t c = 0; c < nch; ++c)
+        if (chunks[c].r0 == P.pw[chunks[c].panel]) pchunk[chunks[c].panel] = (int32_t)c;
+    spx_status st;
+    for (int mode = 0; mode < 2; ++mode) {   // 0: CUDA-core updates, 1: tensor-core updates
+        std::vector<spx::FqItem> items;
+        std::vector<int32_t> need(np, 0);
+        auto level_tiles = [&](int l, bool near) {
+            auto take = [&](int32_t kind, int64_t idx, int32_t task) {
+                const int32_t tgt = P.tasks[task].tgt;
+                if ((P.plevel[tgt] == l + 1) != near) return;
+                items.push_back(spx::FqItem{kind, (int32_t)idx});
+                ++need[tgt];
+            };
+            if (mode == 0) {
+                for (int64_t i = h->tile_ptr[l]; i < h->tile_nar[l]; ++i) take(spx::FQ_UPD64, i, tiles[i].task);
+                for (int64_t i = h->tile_nar[l]; i < h->tile_ptr[l + 1]; ++i) take(spx::FQ_UPD16, i, tiles[i].task);
+            } else {
+                for (int64_t i = h->tctile_ptr[l]; i < h->tctile_ptr[l + 1]; ++i) take(spx::FQ_TC, i, tct[i].task);
+                for (int64_t i = h->tcsmall_ptr[l]; i < h->tcsmall_nar[l]; ++i) take(spx::FQ_UPD64, i, small[i].task);
+                for (int64_t i = h->tcsmall_nar[l]; i < h->tcsmall_ptr[l + 1]; ++i)
+                    take(spx::FQ_UPD16, i, small[i].task);
+            }
+        };
+        int64_t ntiles = 0;
+        for (int l = L0; l < P.nlevels; ++l) {
+            ntiles += mode == 0 ? h->tile_ptr[l + 1] - h->tile_ptr[l]
+                                : (h->tctile_ptr[l + 1] - h->tctile_ptr[l]) + (h->tcsmall_ptr[l + 1] - h->tcsmall_ptr[l]);
+            for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q)
+                items.push_back(spx::FqItem{spx::FQ_DIAG, P.level_panels[q]});
+            if (l - 1 >= L0) level_tiles(l - 1, false);
+            for (int64_t c = h->chunk_ptr[l]; c < h->chunk_ptr[l + 1]; ++c)
+                items.push_back(spx::FqItem{spx::FQ_TRSM, (int32_t)c});
+            level_tiles(l, true);
+        }
+        // Dispatch order: list scheduling of the item DAG on `workers` CTAs
+        // with estimated durations, highest remaining critical path first
+        // (the diagonal-block chain), so that the bulk of the update tiles
+        // fills the time around the chain instead of queueing ahead of it.
+        // The order in which the simulation starts items is topological, so
+        // the no-stall property of the queue holds for it as well.
+        {
+            const int32_t N = (int32_t)items.size();
+            std::vector<int32_t> pos_d(np, -1), pos_c(nch, -1);
+            for (int32_t i = 0; i < N; ++i) {
+                if (items[i].kind == spx::FQ_DIAG) pos_d[items[i].idx] = i;
+                else if (items[i].kind == spx::FQ_TRSM) pos_c[items[i].idx] = i;
+            }
+            std::vector<std::vector<int32_t>> succ(N);
+            std::vector<int32_t> indeg(N, 0);
+            std::vector<double> dur(N, 8.0);   // microseconds, rough: a TRSM chunk or an update tile
+            auto edge = [&](int32_t a, int32_t b) {
+                succ[a].push_back(b);
+                ++indeg[b];
+            };
+            for (int32_t i = 0; i < N; ++i) {
+                const spx::FqItem &it = items[i];
+                if (it.kind == spx::FQ_DIAG) {
+                    const int w = P.pw[it.idx];
+                    dur[i] = w <= 16 ? 10.0 : (w <= 32 ? 20.0 : 60.0);
+                } else if (it.kind == spx::FQ_TRSM) {
+                    edge(pos_d[chunks[it.idx].panel], i);
+                } else {
+                    int32_t task, m0, n0, tm, tn;
+                    if (it.kind == spx::FQ_TC) {
+                        task = tct[it.idx].task, m0 = tct[it.idx].m0, n0 = tct[it.idx].n0, tm = tn = 128;
+                    } else {
+                        const UpdTile &t = mode == 0 ? tiles[it.idx] : small[it.idx];
+                        task = t.task, m0 = t.m0, n0 = t.n0;
+                        tn = it.kind == spx::FQ_UPD16 ? spx::kUpdNarrowN : spx::kUpdTile;
+                        tm = 4096 / tn;
+                    }
+                    const spx::Task &tk = P.tasks[task];
+                    const int hsrc = P.ph[tk.src], w = P.pw[tk.src];
+                    const int64_t lo[2] = {m0, n0}, hi[2] = {std::min(m0 + tm, hsrc), std::min(n0 + tn, tk.r1)};
+                    int64_t last = -1;
+                    for (int r = 0; r < 2; ++r) {
+                        for (int64_t c = pchunk[tk.src] + (lo[r] - w) / spx::kTrsmRows;
+                             c <= pchunk[tk.src] + (hi[r] - 1 - w) / spx::kTrsmRows; ++c) {
+                            if (c == last || c < 0 || c >= nch || pos_c[c] < 0) continue;
+                            edge(pos_c[c], i);
+                            last = c;
+                        }
+                    }
+                    edge(i, pos_d[tk.tgt]);
+                }
+            }
+            // remaining critical path of each item (items are in a topological order)
+            std::vector<double> prio(N, 0.0);
+            for (int32_t i = N - 1; i >= 0; --i) {
+                double m = 0.0;
+                for (int32_t j : succ[i]) m = std::max(m, prio[j]);
+                prio[i] = dur[i] + m;
+            }
+            std::priority_queue<std::pair<double, int32_t>> ready;   // (priority, -index)
+            std::priority_queue<std::pair<double, int32_t>, std::vector<std::pair<double, int32_t>>,
+                                std::greater<std::pair<double, int32_t>>>
+                running;   // (finish time, index)
+            for (int32_t i = 0; i < N; ++i)
+                if (indeg[i] == 0) ready.push({prio[i], -i});
+            std::vector<spx::FqItem> order;
+            order.reserve(N);
+            int free_workers = std::max(1, workers);
+            double now = 0.0;
+            while ((int32_t)order.size() < N) {
+                while (free_workers > 0 && !ready.empty()) {
+                    const int32_t i = -ready.top().second;
+                    ready.pop();
+                    order.push_back(items[i]);
+                    running.push({now + dur[i], i});
+                    --free_workers;
+                }
+                if (running.empty()) break;
+                const std::pair<double, int32_t> f = running.top();
+                running.pop();
+                now = f.first;
+                ++free_workers;
+                for (int32_t j : succ[f.second])
+                    if (--indeg[j] == 0) ready.push({prio[j], -j});
+            }
+            if ((int32_t)order.size() != N)
+                return fail(h, SPX_ERR_STATE, "internal: cycle in the factorization queue's task graph");
+            items.swap(order);
+        }
+        // dependency check: every wait names an earlier item
+        std::vector<int64_t> pos_diag(np, -1), pos_chunk(nch, -1);
+        int64_t ndiag = 0, ntrsm = 0, ntile = 0;
+        for (size_t i = 0; i < items.size(); ++i) {
+            const spx::FqItem &it = items[i];
+            if (it.kind == spx::FQ_DIAG) pos_diag[it.idx] = (int64_t)i, ++ndiag;
+            else if (it.kind == spx::FQ_TRSM) pos_chunk[it.idx] = (int64_t)i, ++ntrsm;
+            else ++ntile;
+        }
+        bool ok = ntile == ntiles && ndiag == P.level_ptr[P.nlevels] - P.level_ptr[L0] &&
+                  ntrsm == h->chunk_ptr[P.nlevels] - h->chunk_ptr[L0];
+        auto chunks_done_before = [&](int src, int r_lo, int r_hi, int64_t at) {
+            if (pchunk[src] < 0 || r_lo < P.pw[src] || r_hi <= r_lo) return false;
+            const int64_t c0 = pchunk[src] + (r_lo - P.pw[src]) / spx::kTrsmRows;
+            const int64_t c1 = pchunk[src] + (r_hi - 1 - P.pw[src]) / spx::kTrsmRows;
+            if (c1 - c0 + 1 > 32) return false;   // one waiting thread per chunk in the first warp
+            for (int64_t c = c0; c <= c1; ++c)
+                if (c >= nch || chunks[c].panel != src || pos_chunk[c] < 0 || pos_chunk[c] >= at) return false;
+            return true;
+        };
+        for (size_t i = 0; i < items.size() && ok; ++i) {
+            const spx::FqItem &it = items[i];
+            if (it.kind == spx::FQ_DIAG) continue;
+            if (it.kind == spx::FQ_TRSM) {
+                ok = pos_diag[chunks[it.idx].panel] >= 0 && pos_diag[chunks[it.idx].panel] < (int64_t)i;
+                continue;
+            }
+            int32_t task, m0, n0, tm, tn;
+            if (it.kind == spx::FQ_TC) {
+                task = tct[it.idx].task, m0 = tct[it.idx].m0, n0 = tct[it.idx].n0, tm = tn = 128;
+            } else {
+                const UpdTile &t = mode == 0 ? tiles[it.idx] : small[it.idx];
+                task = t.task, m0 = t.m0, n0 = t.n0;
+                tn = it.kind == spx::FQ_UPD16 ? spx::kUpdNarrowN : spx::kUpdTile;
+                tm = 4096 / tn;
+            }
+            const spx::Task &tk = P.tasks[task];
+            const int hsrc = P.ph[tk.src];
+            ok = P.plevel[tk.src] >= L0 && pos_diag[tk.tgt] > (int64_t)i &&
+                 chunks_done_before(tk.src, m0, std::min(m0 + tm, hsrc), (int64_t)i) &&
+                 chunks_done_before(tk.src, n0, std::min(n0 + tn, tk.r1), (int64_t)i);
+        }
+        if (!ok) return fail(h, SPX_ERR_STATE, "internal: factorization queue order violates a dependency");
+        h->fq_nitems[mode] = (int32_t)items.size();
+        if ((st = upload(h, &h->d_fq_items[mode], items)) || (st = upload(h, &h->d_fq_need[mode], need))) return st;
+    }
+    h->fq_nchunks = nch;
+    if ((st = upload(h, &h->d_fq_pchunk, pchunk)) ||
+        (st = dalloc(h, &h->d_fq_state, (size_t)2 * np + (size_t)nch + 2)))
+        return st;
+    return SPX_OK;
+}
+
 spx_status ensure_device(spx_handle h)
 {
     if (h->uploaded) return SPX_OK;
@@ -234,7 +510,12 @@ spx_status ensure_device(spx_handle h)
     int64_t *pfcol, *prow, *pval, *pinv;
     int32_t *pw, *ph, *rows, *relmap;
     std::vector<int64_t> hpinv(P.npanels + 1, 0);
-    for (int32_t q = 0; q < P.npanels; ++q) hpinv[q + 1] = hpinv[q] + (int64_t)P.pw[q] * P.pw[q];
+    // each inverted diagonal block starts on a 32-element (>= 128-byte)
+    // boundary, so that no cache line holds two panels' blocks: within one
+    // persistent factorization launch a block is read with plain loads by
+    // other CTAs right after its diagonal item wrote it
+    for (int32_t q = 0; q < P.npanels; ++q)
+        hpinv[q + 1] = hpinv[q] + (((int64_t)P.pw[q] * P.pw[q] + 31) & ~(int64_t)31);
     h->dinv_elems = hpinv[P.npanels];
     h->lvl_wmax.assign(P.nlevels, 1);
     for (int32_t l = 0; l < P.nlevels; ++l)
@@ -444,6 +725,11 @@ spx_status ensure_device(spx_handle h)
         }
         if ((st = upload(h, &h->d_tcsmall, small)) || (st = upload(h, &h->d_tctiles, tct)))
             return st;
+        int nsm = 0;
+        CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+        if ((st = build_queue(h, chunks, tiles, small, tct, 2 * nsm))) return st;   // two queue CTAs per SM
+    } else {
+        h->q_level = P.nlevels;
     }
     {
         int wmax_all = 1;
@@ -530,7 +816,8 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
     spx::launch_assemble<T>(P.nnz_a, h->d_vals, h->d_amap, L, U, s);
     cnt += P.nnz_a > 0;
     mk.mark(SPX_K_ASSEMBLE);
-    for (int32_t l = 0; l < P.nlevels; ++l) {
+    const int32_t qlev = queue_level(h, prec);
+    for (int32_t l = 0; l < qlev; ++l) {
         const int32_t *panels = h->d_level_panels + P.level_ptr[l];
         const int np = P.level_ptr[l + 1] - P.level_ptr[l];
         const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
@@ -601,6 +888,29 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
             cnt += (ntl > 0) + (ntln > 0) + (ntu > 0) + (ntun > 0);
             mk.mark(SPX_K_UPDATE);
         }
+    }
+    if (qlev < P.nlevels) {
+        // the upper levels: one persistent launch over the task queue
+        const int mode = tc ? 1 : 0;
+        const int32_t np = P.npanels;
+        int32_t *st = h->d_fq_state;
+        cudaMemsetAsync(st, 0, sizeof(int32_t) * ((size_t)2 * np + (size_t)h->fq_nchunks + 2), s);
+        spx::FactorQueue q{};
+        q.items = h->d_fq_items[mode];
+        q.nitems = h->fq_nitems[mode];
+        q.need = h->d_fq_need[mode];
+        q.pchunk = h->d_fq_pchunk;
+        q.cnt = st;
+        q.diag_done = st + np;
+        q.chunk_done = st + 2 * (size_t)np;
+        q.head = st + 2 * (size_t)np + h->fq_nchunks;
+        q.err = q.head + 1;
+        q.spin_limit = h->spin_limit;
+        spx::launch_factor_queue<T>(h->dp, q, h->d_tasks, h->d_chunks, tc ? h->d_tcsmall : h->d_tiles, h->d_tctiles,
+                                    L, Dinv, W, h->d_tau, h->d_err, h->d_nrepl, h->d_nneg, ldlt ? 1 : 0,
+                                    tc ? op_kind : -1, h->tmap, h->tmap_lo, opc, opc_lo, h->kpad, op_kind, s);
+        cnt += 2;
+        mk.mark(SPX_K_QUEUE);
     }
 }
 
@@ -1117,6 +1427,7 @@ spx_status spx_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, 
     }
     h->method = method;
     h->pivot_tau_opt = o.pivot_tau;
+    h->queue_panels = o.queue_panels < 0 ? -1 : o.queue_panels;
     const spx::Plan &P = h->plan;
     spx_info &I = h->info;
     I.n = P.n;
@@ -1221,12 +1532,18 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     CU(cudaMemcpyAsync(&bad, h->d_err, sizeof(bad), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaMemcpyAsync(&nrepl, h->d_nrepl, sizeof(nrepl), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaMemcpyAsync(&abits, h->d_anorm, sizeof(abits), cudaMemcpyDeviceToHost, h->hs));
-    int tcerr = 0;
+    int tcerr = 0, fqerr = 0;
     unsigned long long nneg = 0;
     CU(cudaMemcpyAsync(&tcerr, h->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->hs));
+    if (queue_level(h, precision) < P.nlevels)
+        CU(cudaMemcpyAsync(&fqerr, h->d_fq_state + 2 * (size_t)P.npanels + h->fq_nchunks + 1, sizeof(int),
+                           cudaMemcpyDeviceToHost, h->hs));
     CU(cudaMemcpyAsync(&nneg, h->d_nneg, sizeof(nneg), cudaMemcpyDeviceToHost, h->hs));
     CU(cudaStreamSynchronize(h->hs));
     if (tcerr) return fail(h, SPX_ERR_TIMEOUT, "a tensor-core update tile gave up waiting on its pipeline");
+    if (fqerr)
+        return fail(h, SPX_ERR_TIMEOUT, fqerr == 2 ? "the factorization queue's tensor-core pipeline gave up waiting"
+                                                   : "the factorization queue gave up waiting on a task counter");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
     if (h->profiling) {
@@ -1241,19 +1558,18 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         const double nfac = (P.method == SPX_LU) ? 2.0 : 1.0;
         const bool tcm = uses_tensor_cores(P.method, precision);
         const double eop = precision == SPX_BF16 ? 2.0 : (precision == SPX_FP32 ? 8.0 : 4.0);
+        const int32_t qlev = queue_level(h, precision);
         // (LDL^T reads its B operand from a second copy of the same size: the bytes are the same)
-        K.flops[SPX_K_DIAG] = P.diag_flops;
-        K.flops[SPX_K_TRSM] = P.trsm_flops;
-        K.flops[SPX_K_UPDATE] = P.update_flops - (tcm ? h->upd_flops_tc : 0.0);
-        K.flops[SPX_K_UPDATE_TC] = tcm ? h->upd_flops_tc : 0.0;
+        visit_work(P, tcm, [&](int cls, int lvl, double flops, double el, double el_op, double el_acc) {
+            const int c = lvl >= qlev ? (int)SPX_K_QUEUE : cls;
+            K.flops[c] += flops;
+            K.bytes[c] += el * e + el_op * eop + el_acc * 4.0;
+        });
         // zero fill of the factor (one write) + the scatter (value and map read, one write)
         K.bytes[SPX_K_ASSEMBLE] = (double)P.nnz_a * (16.0 + e * nfac) + (double)elems * e * nfac;
-        K.bytes[SPX_K_DIAG] = P.diag_elems * e;
-        K.bytes[SPX_K_TRSM] = P.trsm_elems * e;
-        K.bytes[SPX_K_UPDATE] = (P.update_elems - (tcm ? h->upd_op_elems_tc + h->upd_elems_tc : 0.0)) * e;
-        K.bytes[SPX_K_UPDATE_TC] = tcm ? h->upd_op_elems_tc * eop + h->upd_elems_tc * 4.0 : 0.0;
         K.launches[SPX_K_ASSEMBLE] = P.nnz_a > 0 ? 4 : 3;
-        for (int32_t l = 0; l < P.nlevels; ++l) {
+        K.launches[SPX_K_QUEUE] = qlev < P.nlevels ? 1 : 0;
+        for (int32_t l = 0; l < qlev; ++l) {
             for (int c = 0; c < kNumClasses; ++c)
                 K.launches[SPX_K_DIAG] += (h->cls_ptr[(size_t)l * kNumClasses + c + 1] >
                                            h->cls_ptr[(size_t)l * kNumClasses + c]);
@@ -1393,37 +1709,16 @@ spx_status spx_roofline_model(spx_handle h, spx_precision precision, const doubl
     const double simt = fp64 ? f64 : f32;
     const bool tcm = uses_tensor_cores(P.method, precision);
     const double eop = precision == SPX_BF16 ? 2.0 : (precision == SPX_FP32 ? 8.0 : 4.0);
-    auto t = [&](double flops, double bytes, double peak) { return std::max(flops / peak, bytes / bw); };
-    double ms[SPX_K_CLASSES] = {0, 0, 0, 0, 0};
+    const int qlev = P.method == SPX_LU ? P.nlevels
+                     : queue_policy_level(P, h->queue_panels, precision);
+    double ms[SPX_K_CLASSES] = {0, 0, 0, 0, 0, 0};
     const double nfac = lu ? 2.0 : 1.0;
     ms[SPX_K_ASSEMBLE] = ((double)P.nnz_a * (16.0 + e * nfac) + (double)P.pval[P.npanels] * e * nfac) / bw;
-    for (int32_t q = 0; q < P.npanels; ++q) {
-        const double w = P.pw[q], off = (double)P.ph[q] - P.pw[q];
-        double df = 0.0;
-        for (int32_t j = 0; j < P.pw[q]; ++j) {
-            const double c = w - j;
-            df += lu ? 2.0 * (c - 1.0) * (c - 1.0) + (c - 1.0) : c * c;
-        }
-        ms[SPX_K_DIAG] += t(df, 2.0 * w * w * e, f64);
-        ms[SPX_K_TRSM] += t(nfac * off * w * w, nfac * (2.0 * off * w + w * w) * e, simt);
-    }
-    for (const spx::Task &tk : P.tasks) {
-        const double M = (double)P.ph[tk.src] - tk.r0, N = (double)tk.r1 - tk.r0, K = P.pw[tk.src];
-        double flops, elems_op, elems_acc;
-        if (!lu) {
-            flops = 2.0 * (M - N) * N * K + N * (N + 1.0) * K;
-            elems_op = (M + N) * K;
-            elems_acc = 2.0 * ((M - N) * N + N * (N + 1.0) / 2.0);
-        } else {
-            flops = 2.0 * M * N * K + 2.0 * (M - N) * N * K;
-            elems_op = (M + N) * K + M * K;
-            elems_acc = 2.0 * (M * N + (M - N) * N);
-        }
-        if (tcm && P.pw[tk.src] >= kTcMinWidth)
-            ms[SPX_K_UPDATE_TC] += t(flops, elems_op * eop + elems_acc * 4.0, tc);
-        else
-            ms[SPX_K_UPDATE] += t(flops, (elems_op + elems_acc) * e, simt);
-    }
+    visit_work(P, tcm, [&](int cls, int lvl, double flops, double el, double el_op, double el_acc) {
+        const double peak = cls == SPX_K_DIAG ? f64 : (cls == SPX_K_UPDATE_TC ? tc : simt);
+        const double bytes = el * e + el_op * eop + el_acc * 4.0;
+        ms[lvl >= qlev ? (int)SPX_K_QUEUE : cls] += std::max(flops / peak, bytes / bw);
+    });
     for (int c = 0; c < SPX_K_CLASSES; ++c) model_ms[c] = ms[c] * 1e3;
     return SPX_OK;
 }
@@ -1433,6 +1728,11 @@ spx_status spx_set_wait_limit(spx_handle h, int64_t polls)
     if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
     if (polls < 0 || polls > (int64_t)UINT32_MAX) return fail(h, SPX_ERR_ARG, "polls outside [0, 2^32)");
     h->spin_limit = polls == 0 ? spx::kDefaultSpinLimit : (uint32_t)polls;
+    if (h->fgraph) {   // the captured factorization queue carries the old limit
+        cudaGraphExecDestroy(h->fgraph);
+        h->fgraph = nullptr;
+        h->fgraph_prec = -1;
+    }
     if (h->sgraph) {   // the captured sweeps carry the old limit
         cudaGraphExecDestroy(h->sgraph);
         h->sgraph = nullptr;

@@ -9,87 +9,13 @@
 // dimension = panel height h, the w x w diagonal block on top, the
 // off-diagonal rows below.  T is the storage type (double, or float for the
 // mixed-precision factor); the diagonal blocks are always factored in double.
-#include "kernels.cuh"
-#include "operand.cuh"
+#include "blocks.cuh"
 
 #include <cuda_bf16.h>
 #include <cstdio>
 
 namespace spx {
 
-// ---------------------------------------------------------------------------
-// Pivot arithmetic in FP64 with short dependency chains.  IEEE FP64 division
-// and square root expand into long chains of dependent FP64 instructions, and
-// a dependent FP64 instruction costs tens of times its throughput slot on
-// this part, so the column-by-column pivots would dominate the diagonal
-// kernels.  Instead:
-//  * a float seed is cut from the double's bits with integer operations (no
-//    FP64 conversion), refined by the FP32 unit (rsqrtf / reciprocal) and
-//    widened back the same way;
-//  * reciprocal: Newton's method on 1/y - d, written with the error term
-//    e = 1 - d y so that two steps need three dependent FP64 operations
-//    (y1 = y0 + y0 e, e1 = e^2, y2 = y1 + y1 e1);
-//  * square root and its reciprocal together: Goldschmidt's iteration
-//    (g -> sqrt(d), h -> 1/(2 sqrt(d)); r = 1/2 - g h; g += g r; h += h r),
-//    two iterations, five dependent FP64 operations.
-// Each iteration squares the relative error: 2^-22 -> 2^-44 -> below FP64
-// rounding.  Magnitudes outside the FP32 normal range fall back to IEEE.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool float_seed(double d, float *f)
-{
-    const long long b = __double_as_longlong(d);
-    const int e = (int)((b >> 52) & 0x7FF) - 1023;
-    if (e < -125 || e > 126) return false;
-    const unsigned fb = (unsigned)((b >> 32) & 0x80000000u) | ((unsigned)(e + 127) << 23) |
-                        (unsigned)((b >> 29) & 0x7FFFFF);
-    *f = __uint_as_float(fb);
-    return true;
-}
-
-__device__ __forceinline__ double widen(float f)
-{
-    const unsigned u = __float_as_uint(f);
-    const int e = (int)((u >> 23) & 0xFF) - 127;
-    const long long b = ((long long)(u & 0x80000000u) << 32) | ((long long)(e + 1023) << 52) |
-                        ((long long)(u & 0x7FFFFF) << 29);
-    return __longlong_as_double(b);
-}
-
-__device__ __forceinline__ double rcp_newton(double d)
-{
-    float f;
-    if (!float_seed(d, &f)) return 1.0 / d;
-    const float yf = 1.0f / f;
-    if (!(fabsf(yf) > 1e-37f && fabsf(yf) < 1e37f)) return 1.0 / d;
-    const double y0 = widen(yf);
-    const double e0 = fma(-d, y0, 1.0);
-    const double y1 = fma(y0, e0, y0);
-    const double e1 = e0 * e0;
-    return fma(y1, e1, y1);
-}
-
-// sqrt(d) and 1/sqrt(d) for d > 0.
-__device__ __forceinline__ void sqrt_rsqrt(double d, double *s, double *rs)
-{
-    float f;
-    if (d <= 0.0 || !float_seed(d, &f)) {
-        *s = sqrt(d);
-        *rs = 1.0 / *s;
-        return;
-    }
-    const double y = widen(rsqrtf(f));
-    double g = d * y, h = 0.5 * y;
-    double r = fma(-g, h, 0.5);
-    g = fma(g, r, g);
-    h = fma(h, r, h);
-    r = fma(-g, h, 0.5);
-    g = fma(g, r, g);
-    h = fma(h, r, h);
-    *s = g;
-    *rs = 2.0 * h;
-}
-
-__device__ __forceinline__ float rcp_newton(float d) { return 1.0f / d; }
 
 
 // ---------------------------------------------------------------------------
@@ -175,8 +101,6 @@ __device__ T *narrow_inplace(double *sm, int count)
 // that is not positive is reported (replace_tau <= 0: the smallest failing
 // column goes to *err_col) or replaced by replace_tau and counted.
 // ---------------------------------------------------------------------------
-constexpr int kDB = 8;
-
 __device__ void chol_blocked(double *a, int w, double replace_tau, int64_t col0, int64_t *err_col,
                              unsigned long long *nrepl)
 {
@@ -247,10 +171,6 @@ __device__ void chol_blocked(double *a, int w, double replace_tau, int64_t col0,
 // block values of its two trailing rows in registers and updates the
 // columns of its warp (j = kb + kDB + warp, + nw, ...), lower part only.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double shfl_d(double v, int src)
-{
-    return __shfl_sync(0xffffffffu, v, src);
-}
 
 __device__ void chol_reg64(double *a, int w, int ld, double replace_tau, int64_t col0,
                            int64_t *err_col, unsigned long long *nrepl)
@@ -437,20 +357,7 @@ __global__ void __launch_bounds__(256) potrf_kernel(DevPlan p, const int32_t *__
     for (int idx = tid; idx < w * w; idx += nt) Mi[idx] = a[idx];
 }
 
-// ---------------------------------------------------------------------------
-// Diagonal block of width <= W (W = 16, 32, 64; the block is padded with the
-// identity to W).  A dependent FP64 operation costs ~64 cycles on this part,
-// so the column chain is kept short:
-//  * the factorization runs in LDL^T form in FP64 -- per column one Newton
-//    reciprocal of the pivot, the multipliers, and the in-block updates,
-//    with no square root on the chain; warps 0 and 1 own each 8-column
-//    block panel in registers (rows 0-31 and 32-63 of the block; each warp
-//    runs the pivot chain itself), the other warps apply the trailing updates;
-//  * L = l diag(sqrt(d)) is formed afterwards, all columns in parallel;
-//  * L^{-1} = diag(1/sqrt(d)) l^{-1}: the unit-lower l is inverted by blocks
-//    (8 x 8 diagonal blocks by single lanes, then pairs of blocks merged with
-//    X21 = -C^{-1} (B A^{-1})), in the factor's arithmetic.
-// ---------------------------------------------------------------------------
+// The diagonal blocks of one width class, one CTA per panel.
 template <typename T, int W, bool ldlt>
 __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t *__restrict__ panels,
                                                         T *__restrict__ L, T *__restrict__ Dinv,
@@ -458,236 +365,8 @@ __global__ void __launch_bounds__(256) potrf_ldl_kernel(DevPlan p, const int32_t
                                                         int64_t *err_col, unsigned long long *nrepl,
                                                         unsigned long long *nneg)
 {
-    constexpr int LD = W + 1;
-    constexpr int NT = 256;
     extern __shared__ double sm[];
-    double *a = sm;                          // W x LD, FP64 working block
-    double *lA = a + W * LD;                 // 2 x (W x kDB) unscaled block columns (ld W)
-    double *dv = lA + 2 * W * kDB;           // pivots
-    double *rsv = dv + W;                    // 1 / sqrt(pivot)
-    T *x = reinterpret_cast<T *>(rsv + W);   // W x LD inverse workspace
-    T *tmp = x + W * LD;                     // (W/2)^2
-    const double replace_tau = *replace_tau_p;
-    const int pid = panels[blockIdx.x];
-    const int w = p.pw[pid], h = p.ph[pid];
-    const int64_t col0 = p.pfcol[pid];
-    T *D = L + p.pval[pid];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    // the block, padded with the identity to W: every load of a thread is
-    // issued before its first store, so the loads overlap
-    {
-        constexpr int NPER = (W * W + NT - 1) / NT;
-        T vv[NPER];
-#pragma unroll
-        for (int q = 0; q < NPER; ++q) {
-            const int idx = tid + q * NT;
-            const int i = idx % W, j = idx / W;
-            vv[q] = (idx < W * W && i < w && j < w && i >= j) ? D[i + (int64_t)j * h] : (T)0;
-        }
-#pragma unroll
-        for (int q = 0; q < NPER; ++q) {
-            const int idx = tid + q * NT;
-            if (idx >= W * W) continue;
-            const int i = idx % W, j = idx / W;
-            a[i + j * LD] = (i < w && j < w) ? (double)vv[q] : (i == j ? 1.0 : 0.0);
-        }
-    }
-    __syncthreads();
-
-    // Block panel b by warp 0 (registers, two row sets of 32), writing the
-    // multipliers into a and the unscaled block columns into lA (two buffers,
-    // one per block parity, so that the next panel can overlap the trailing
-    // update of the previous one).
-    // Block panel kb (8 columns), rows in registers, by one warp per row set:
-    //   role 0 (warp 0): rows kb .. kb+31, the pivots and their side effects;
-    //   role 1 (warp 1, when rows kb+32.. exist): rows kb+32 .. kb+63.
-    // Warp 1 recomputes the 8 x 8 diagonal part from its own copy of rows
-    // kb .. kb+7 (lane l holds row kb + (l & 7)) with the same operations in
-    // the same order as warp 0, so its pivots and multipliers are bit-equal
-    // and the two warps never wait for each other.  Multipliers go to a, the
-    // unscaled block columns to lA (two buffers, one per block parity, so
-    // that the next panel can overlap the trailing update of the previous).
-    auto panel = [&](int kb, int role) {
-        double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
-        const int rq = role == 0 ? kb + lane : kb + (lane & 7);   // rows of the pivot chain
-        const int r1 = kb + 32 + lane;                            // role 1: its own rows
-        double q[kDB], p1[kDB];
-#pragma unroll
-        for (int c = 0; c < kDB; ++c) {
-            q[c] = rq < W ? a[rq + (kb + c) * LD] : 0.0;
-            p1[c] = (role == 1 && r1 < W) ? a[r1 + (kb + c) * LD] : 0.0;
-        }
-#pragma unroll
-        for (int c = 0; c < kDB; ++c) {
-            const int k = kb + c;
-            double d = shfl_d(q[c], c);                  // A(k, k) from lane c
-            const bool report = role == 0 && lane == 0 && k < w;
-            if constexpr (!ldlt) {                        // Cholesky: positive pivots
-                if (!(d > 0.0)) {
-                    if (report) {
-                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
-                        else atomicMin((long long *)err_col, (long long)(col0 + k));
-                    }
-                    d = replace_tau > 0.0 ? replace_tau : 1.0;
-                }
-            } else {                                      // LDL^T: static pivoting
-                if (!(fabs(d) >= replace_tau) || (replace_tau <= 0.0 && d == 0.0)) {
-                    if (report) {
-                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
-                        else atomicMin((long long *)err_col, (long long)(col0 + k));
-                    }
-                    d = replace_tau > 0.0 ? (d < 0.0 ? -replace_tau : replace_tau) : 1.0;
-                }
-                if (report && d < 0.0) atomicAdd(nneg, 1ull);
-            }
-            const double r = 1.0 / d;   // measured faster here than the Newton form
-            const double u0 = rq > k ? q[c] : 0.0;
-            const double l0 = u0 * r;
-#pragma unroll
-            for (int c2 = c + 1; c2 < kDB; ++c2) {
-                const double ac = shfl_d(u0, c2);                   // A(kb + c2, k)
-                if (rq >= kb + c2) q[c2] = fma(-l0, ac, q[c2]);
-                if (role == 1) p1[c2] = fma(-(p1[c] * r), ac, p1[c2]);
-            }
-            if (role == 0) {
-                if (rq < W) lAb[rq + c * W] = u0;
-                q[c] = rq > k ? l0 : (rq == k ? 1.0 : 0.0);
-                if (lane == c) dv[k] = d;
-            } else {
-                if (r1 < W) lAb[r1 + c * W] = p1[c];
-                p1[c] = p1[c] * r;
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < kDB; ++c) {
-            if (role == 0 && rq < W) a[rq + (kb + c) * LD] = q[c];
-            if (role == 1 && r1 < W) a[r1 + (kb + c) * LD] = p1[c];
-        }
-    };
-    // Rank-kDB update by block kb of the lower part of columns [j0, j1),
-    // rows >= j; the (i, j) pairs are spread densely over the threads
-    // t0.. (stride ts) so that FP64 lanes are not wasted on the upper part.
-    auto update = [&](int kb, int j0, int j1, int t0, int ts) {
-        const double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
-        // pairs ordered column by column: column j holds W - j rows
-        int j = j0, rem = t0;      // pair e = t0, t0 + ts, ... decoded incrementally
-        while (j < j1 && rem >= W - j) {
-            rem -= W - j;
-            ++j;
-        }
-        for (; j < j1;) {
-            const int i = j + rem;
-            double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-            for (int c = 0; c < kDB; c += 2) {
-                s0 = fma(a[i + (kb + c) * LD], lAb[j + c * W], s0);
-                s1 = fma(a[i + (kb + c + 1) * LD], lAb[j + (c + 1) * W], s1);
-            }
-            a[i + j * LD] -= s0 + s1;
-            rem += ts;
-            while (j < j1 && rem >= W - j) {
-                rem -= W - j;
-                ++j;
-            }
-        }
-    };
-
-    if (warp == 0) panel(0, 0);
-    else if (warp == 1 && 32 < W) panel(0, 1);
-    __syncthreads();
-    for (int kb = 0; kb < W; kb += kDB) {
-        const int nb = kb + kDB;                 // next block
-        if (nb < W) {
-            // columns of the next block first, by every thread
-            update(kb, nb, nb + kDB, tid, NT);
-            __syncthreads();
-            // warps 0 (and 1) factor the next block while the others finish
-            // this block's update
-            const bool two = nb + 32 < W;
-            if (warp == 0) panel(nb, 0);
-            else if (warp == 1 && two) panel(nb, 1);
-            else update(kb, nb + kDB, W, tid - (two ? 64 : 32), NT - (two ? 64 : 32));
-            __syncthreads();
-        }
-    }
-
-    // Cholesky: L = l diag(sqrt(d)), keep 1/sqrt(d) for the inverse.
-    // LDL^T: store l (unit) with d on the diagonal, keep 1/d.
-    if (tid < W) {
-        if constexpr (ldlt) {
-            rsv[tid] = rcp_newton(dv[tid]);
-        } else {
-            double sq, rs;
-            sqrt_rsqrt(dv[tid], &sq, &rs);
-            dv[tid] = sq;
-            rsv[tid] = rs;
-        }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < W * W; idx += NT) {
-        const int i = idx % W, j = idx / W;
-        const T l = (T)a[i + j * LD];
-        if (i < w && j < w && i >= j)
-            D[i + (int64_t)j * h] = i == j ? (T)dv[j] : (ldlt ? l : l * (T)dv[j]);
-        x[i + j * LD] = i > j ? l : (i == j ? (T)1 : (T)0);
-    }
-    __syncthreads();
-
-    // unit-lower inverse: 8 x 8 diagonal blocks first
-    if (warp < W / kDB && lane < kDB) {
-        const int o = warp * kDB, jj = lane;
-        T xr[kDB];
-#pragma unroll
-        for (int q = 0; q < kDB; ++q) xr[q] = q == jj ? (T)1 : (T)0;
-#pragma unroll
-        for (int kk = 0; kk < kDB; ++kk) {
-            if (kk >= jj) {
-#pragma unroll
-                for (int ii = kk + 1; ii < kDB; ++ii) xr[ii] -= x[(o + ii) + (o + kk) * LD] * xr[kk];
-            }
-        }
-        __syncwarp(0xffu);
-#pragma unroll
-        for (int ii = 0; ii < kDB; ++ii)
-            if (ii > jj) x[(o + ii) + (o + jj) * LD] = xr[ii];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int sz = kDB; sz < W; sz *= 2) {
-        const int npair = W / (2 * sz);
-        for (int e = tid; e < npair * sz * sz; e += NT) {
-            const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
-            const int o = pr * 2 * sz;
-            T acc = (T)0;
-            for (int k = j; k < sz; ++k) acc += x[(o + sz + i) + (o + k) * LD] * x[(o + k) + (o + j) * LD];
-            tmp[pr * sz * sz + i + j * sz] = acc;
-        }
-        __syncthreads();
-        for (int e = tid; e < npair * sz * sz; e += NT) {
-            const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
-            const int o = pr * 2 * sz;
-            T acc = tmp[pr * sz * sz + i + j * sz];   // C^{-1} has a unit diagonal
-            for (int k = 0; k < i; ++k) acc += x[(o + sz + i) + (o + sz + k) * LD] * tmp[pr * sz * sz + k + j * sz];
-            x[(o + sz + i) + (o + j) * LD] = -acc;
-        }
-        __syncthreads();
-    }
-    // Cholesky: L^{-1} = diag(1/sqrt(d)) l^{-1}.  LDL^T: l^{-1} below the
-    // diagonal (unit), 1/d on it.
-    T *Mi = Dinv + p.pinv[pid];
-    for (int idx = tid; idx < w * w; idx += NT) {
-        const int i = idx % w, j = idx / w;
-        if constexpr (ldlt) Mi[idx] = i > j ? x[i + j * LD] : (i == j ? (T)rsv[i] : (T)0);
-        else Mi[idx] = i >= j ? x[i + j * LD] * (T)rsv[i] : (T)0;
-    }
-}
-
-template <typename T, int W>
-constexpr size_t ldl_smem_bytes()
-{
-    return sizeof(double) * ((size_t)W * (W + 1) + (size_t)2 * W * kDB + 2 * W) +
-           sizeof(T) * ((size_t)W * (W + 1) + (size_t)(W / 2) * (W / 2));
+    ldl_diag_block<T, W, ldlt>(p, panels[blockIdx.x], L, Dinv, *replace_tau_p, err_col, nrepl, nneg, sm);
 }
 
 template <typename T, int W, bool ldlt = false>
@@ -818,19 +497,6 @@ void launch_getrf(const DevPlan &p, const int32_t *panels, int count, int wmax, 
     getrf_kernel<T><<<count, threads, smem, s>>>(p, panels, L, Dinv, tau, err_col, nrepl);
 }
 
-// ---------------------------------------------------------------------------
-// Panel TRSM (Sec. III step 2) as a product with the inverted diagonal block:
-// rows [r0, r0+64) of the off-diagonal part X become X B with
-//   LLT : B = L^{-T}           (B(k,j) = Linv(j,k))
-//   LU_L: B = U^{-1}           (B(k,j) = Uinv(k,j))
-//   LU_U: B = L^{-T}, unit L   (B(k,j) = Linv(j,k), 1 on the diagonal)
-//   RIGHT_LINV: B = L^{-1}     (B(k,j) = Linv(k,j); the selected inversion's L_RJ L_JJ^{-1})
-// The CTA copies its rows and the whole B operand of a 64-column tile to
-// shared memory first (every load of a batch issued before its stores), so
-// writing the rows back in place is safe and the K loop runs without
-// barriers; 64 x 64 output tiles, 4 x 4 per thread, written back through
-// shared memory in whole segments.
-// ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChunk *__restrict__ chunks,
                                                         const T *__restrict__ Dinv,
@@ -838,138 +504,8 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(DevPlan p, const RowChun
                                                         void *opc_lo, int kpad, int op_kind,
                                                         T *__restrict__ Wout)
 {
-    constexpr int NB = 16;                     // loads in flight per thread while staging
     extern __shared__ unsigned char smraw[];
-    const RowChunk ch = chunks[blockIdx.x];
-    const int pid = ch.panel;
-    const int w = p.pw[pid], h = p.ph[pid];
-    const int wpad = (w + 15) & ~15;
-    T *Xs = reinterpret_cast<T *>(smraw);      // Xs[k * 64 + r], k < wpad
-    T *Bf = Xs + wpad * kTrsmRows;             // Bf[k * 65 + j], k < max(wpad, 64); then the output tile
-    const T *Mi = Dinv + p.pinv[pid];
-    T *Xg = X + p.pval[pid] + ch.r0;
-    const int nr = min(kTrsmRows, h - ch.r0);
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    // B(k, j) of the product X B (see the table above)
-    auto bval = [&](int k, int j) -> T {
-        if (k >= w || j >= w) return (T)0;
-        if (mode == TRSM_RIGHT_LINV) return k >= j ? Mi[k + j * w] : (T)0;
-        if (mode == TRSM_LU_L) return k <= j ? Mi[k + j * w] : (T)0;
-        if (j > k) return Mi[j + k * w];
-        if (j == k) return (mode == TRSM_LU_U || mode == TRSM_LDLT) ? (T)1 : Mi[j + k * w];
-        return (T)0;
-    };
-    // the chunk's rows, every load of a batch issued before its stores
-    for (int base = tid; base < wpad * kTrsmRows; base += 256 * NB) {
-        T v[NB];
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int e = base + 256 * q, r = e & 63, k = e >> 6;
-            v[q] = (e < wpad * kTrsmRows && r < nr && k < w) ? Xg[r + (int64_t)k * h] : (T)0;
-        }
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int e = base + 256 * q;
-            if (e < wpad * kTrsmRows) Xs[e] = v[q];
-        }
-    }
-    for (int c0 = 0; c0 < w; c0 += kUpdTile) {
-        if (c0 > 0) __syncthreads();           // the previous tile is out of Bf
-        for (int base = tid; base < wpad * kUpdTile; base += 256 * NB) {
-            T v[NB];
-#pragma unroll
-            for (int q = 0; q < NB; ++q) {
-                const int e = base + 256 * q;
-                v[q] = e < wpad * kUpdTile ? bval(e >> 6, c0 + (e & 63)) : (T)0;
-            }
-#pragma unroll
-            for (int q = 0; q < NB; ++q) {
-                const int e = base + 256 * q;
-                if (e < wpad * kUpdTile) Bf[(e >> 6) * (kUpdTile + 1) + (e & 63)] = v[q];
-            }
-        }
-        __syncthreads();
-        T acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-#pragma unroll 4
-        for (int k = 0; k < wpad; ++k) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = Xs[k * 64 + tx + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bf[k * (kUpdTile + 1) + ty + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-        }
-        if (mode == TRSM_LDLT) {
-            // acc = X l^{-T} is the D L^T buffer row (Sec. V-B: the update then
-            // multiplies L by it); L = acc D^{-1} goes back in place
-            T *Wg = Wout + p.pval[pid] + ch.r0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int j = c0 + ty + 16 * b;
-                const T dinv = j < w ? Mi[j + j * w] : (T)0;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int r = tx + 16 * a;
-                    if (r >= nr || j >= w) continue;
-                    Wg[r + (int64_t)j * h] = acc[a][b];
-                    const T l = acc[a][b] * dinv;
-                    Xg[r + (int64_t)j * h] = l;
-                    if (opc)   // A operand: L; B operand: D L^T
-                        put_operand(opc, opc_lo, (p.prow[pid] + ch.r0 + r) * kpad + j, op_kind, (float)l,
-                                    (float)acc[a][b]);
-                }
-            }
-            continue;
-        }
-        // the 64 x 64 result tile through shared memory, so that both the
-        // column-major panel and the row-major operand copy are written in
-        // whole segments
-        __syncthreads();                       // every read of Bf is done
-        T *Ot = Bf;                            // Ot[r * 65 + jj]
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) Ot[(tx + 16 * a) * (kUpdTile + 1) + ty + 16 * b] = acc[a][b];
-        __syncthreads();
-        const int nc = min(kUpdTile, w - c0);
-        for (int e = tid; e < nc * kTrsmRows; e += 256) {
-            const int r = e & 63, jj = e >> 6;
-            if (r < nr) Xg[r + (int64_t)(c0 + jj) * h] = Ot[r * (kUpdTile + 1) + jj];
-        }
-        if (opc) {
-            // the same rows, K-major, for the tensor-core updates; columns
-            // w .. c0+63 of the tile are zero and fill the row's padding
-            const int64_t orow0 = p.prow[pid] + ch.r0;
-            for (int e = tid; e < nr * kUpdTile; e += 256) {
-                const int r = e >> 6, jj = e & 63;
-                put_operand(opc, opc_lo, (orow0 + r) * kpad + c0 + jj, op_kind,
-                            (float)Ot[r * (kUpdTile + 1) + jj], 0.0f);
-            }
-        }
-    }
-    if (opc) {
-        // the rest of each operand row's padding
-        const int64_t orow0 = p.prow[pid] + ch.r0;
-        const int j0 = mode == TRSM_LDLT ? w : (w + kUpdTile - 1) / kUpdTile * kUpdTile;
-        const int padw = kpad - j0;
-        for (int e = tid; e < nr * padw; e += 256) {
-            const int r = e / padw, j = j0 + e % padw;
-            put_operand(opc, opc_lo, (orow0 + r) * kpad + j, op_kind, 0.0f, 0.0f);
-        }
-    }
-}
-
-template <typename T>
-constexpr size_t trsm_smem_bytes(int wpad)
-{
-    return sizeof(T) * ((size_t)wpad * kTrsmRows + (size_t)(wpad > kUpdTile ? wpad : kUpdTile) * (kUpdTile + 1));
+    trsm_chunk<T>(p, chunks[blockIdx.x], Dinv, X, mode, opc, opc_lo, kpad, op_kind, Wout, smraw);
 }
 
 template <typename T>
@@ -987,22 +523,6 @@ void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, 
     trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, opc_lo, kpad, op_kind, Wout);
 }
 
-// ---------------------------------------------------------------------------
-// Update with fused scatter (Sec. V-B).  One CTA computes a 64 x 64 tile of
-// W = A_rows(M) * B_rows(N)^T over the source panel's width, K-chunked
-// through shared memory, then subtracts it from the target panel at row
-// relmap(i) and column row(j) - first column(target), with atomic adds so
-// that sources of one level may hit the same target concurrently.
-//   lower   : skip entries with i < j (Cholesky diagonal-block region)
-//   from_r1 : rows below r1 only (the U^T side of an LU update)
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void atomic_sub(T *addr, T v);
-template <>
-__device__ __forceinline__ void atomic_sub<double>(double *addr, double v) { atomicAdd(addr, -v); }
-template <>
-__device__ __forceinline__ void atomic_sub<float>(float *addr, float v) { atomicAdd(addr, -v); }
-
 template <typename T, int TN>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(DevPlan p, const DevTask *__restrict__ tasks,
                                                      const UpdTile *__restrict__ tiles,
@@ -1010,91 +530,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(Dev
                                                      const T *__restrict__ Bop, T *__restrict__ C,
                                                      int lower, int from_r1)
 {
-    // TM x TN output tile (64 x 64, or 256 x 16 for tasks facing few rows),
-    // 4 x 4 outputs per thread, K-chunks of 16 staged in shared memory
-    constexpr int TM = 4096 / TN;
-    constexpr int RX = TM / 4, CX = TN / 4;      // thread grid: RX rows x 256/RX column groups
-    __shared__ T As[16][TM + 1];
-    __shared__ T Bs[16][TN + 1];
+    __shared__ T smem[update_smem_elems<T, TN>()];
     const UpdTile tl = tiles[blockIdx.x];
-    const DevTask tk = tasks[tl.task];
-    const int src = tk.src, tgt = tk.tgt;
-    const int h = p.ph[src], K = p.pw[src];
-    const int64_t sbase = p.pval[src];
-    const T *A = Aop + sbase;
-    const T *B = Bop + sbase;
-    const int tid = threadIdx.x;
-    const int tx = tid % RX, ty = tid / RX;
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        if constexpr (TN == TM) {
-            // loader: TM rows x 4 k per pass, A and B side by side
-            const int lr = tid % TM, lk = tid / TM;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int kk = lk + 4 * q;
-                const int kg = k0 + kk;
-                const int ra = tl.m0 + lr, rb = tl.n0 + lr;
-                As[kk][lr] = (kg < K && ra < h) ? A[ra + (int64_t)kg * h] : (T)0;
-                Bs[kk][lr] = (kg < K && rb < tk.r1) ? B[rb + (int64_t)kg * h] : (T)0;
-            }
-        } else {
-            // loader: 256 rows x 1 k per pass for A, one 16 x 16 block for B
-            static_assert(TM == 256 && TN == 16, "narrow tile is 256 x 16");
-#pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                const int kg = k0 + kk, ra = tl.m0 + tid;
-                As[kk][tid] = (kg < K && ra < h) ? A[ra + (int64_t)kg * h] : (T)0;
-            }
-            const int r = tid & 15, kk = tid >> 4;
-            const int kg = k0 + kk, rb = tl.n0 + r;
-            Bs[kk][r] = (kg < K && rb < tk.r1) ? B[rb + (int64_t)kg * h] : (T)0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + RX * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + CX * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-        }
-        __syncthreads();
-    }
-    const int hT = p.ph[tgt];
-    T *Ct = C + p.pval[tgt];
-    const int64_t fcolT = p.pfcol[tgt];
-    const int32_t *srow = p.rows + p.prow[src];
-    const int32_t *rmap = p.relmap + tk.relmap_off - tk.r0;
-    const int rlo = from_r1 ? tk.r1 : tk.r0;
-    int64_t coff[4];
-    bool cok[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int j = tl.n0 + ty + CX * b;
-        cok[b] = j < tk.r1;
-        coff[b] = cok[b] ? (int64_t)(srow[j] - fcolT) * hT : 0;
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = tl.m0 + tx + RX * a;
-        if (i >= h || i < rlo) continue;
-        const int64_t roff = rmap[i];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int j = tl.n0 + ty + CX * b;
-            if (!cok[b] || (lower && i < j)) continue;
-            atomic_sub<T>(Ct + roff + coff[b], acc[a][b]);
-        }
-    }
+    update_tile<T, TN>(p, tasks[tl.task], tl, Aop, Bop, C, lower, from_r1, smem);
 }
 
 template <typename T>

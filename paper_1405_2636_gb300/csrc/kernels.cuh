@@ -121,6 +121,40 @@ template <typename T>
 void launch_stage_operand(int64_t m, int k, const T *A, const T *W, int64_t lda, void *opc, void *opc_lo,
                           int kpad, int op_kind, cudaStream_t s);
 
+// ---- persistent task queue of the upper levels (fqueue.cu) ----------------
+// Items: a panel's diagonal block, a 64-row TRSM chunk, an update tile on the
+// tensor cores or on the CUDA cores (64 x 64, or 256 x 16 for tasks facing
+// at most 16 rows), listed so that every item's inputs come from earlier items.
+enum FqKind : int32_t { FQ_DIAG = 0, FQ_TRSM = 1, FQ_TC = 2, FQ_UPD64 = 3, FQ_UPD16 = 4 };
+struct FqItem {
+    int32_t kind;
+    int32_t idx;   // panel (DIAG), chunk (TRSM), tile (TC: tensor-core tile list; UPD: CUDA-core tile list)
+};
+struct FactorQueue {
+    const FqItem *items;
+    int32_t nitems;
+    const int32_t *need;       // per panel: update tiles of the queue that target it
+    const int32_t *pchunk;     // per panel: index of its first TRSM chunk in the chunk list
+    int32_t *cnt;              // per panel: finished update tiles into it
+    int32_t *diag_done;        // per panel: 1 once its diagonal block is factored
+    int32_t *chunk_done;       // per chunk: 1 once its TRSM is done
+    int32_t *head;             // next item to hand out
+    int32_t *err;              // 1 when a counter wait gave up, 2 when a tensor-core pipeline wait did
+    uint32_t spin_limit;       // polls of ~256 ns before a counter wait gives up
+};
+// The counters cnt, diag_done, chunk_done, head and err are zeroed before
+// each launch.  T: factor storage; ldlt: LDL^T diagonal blocks and the
+// D L^T operand W; tc_kind: operand kind of the tensor-core tiles (-1: none).
+template <typename T>
+void launch_factor_queue(const DevPlan &p, const FactorQueue &q, const DevTask *tasks, const RowChunk *chunks,
+                         const UpdTile *tiles, const TcTile *tctiles, T *L, T *Dinv, T *W, const double *tau,
+                         int64_t *err_col, unsigned long long *nrepl, unsigned long long *nneg, int ldlt,
+                         int tc_kind, const void *tmap, const void *tmap_lo, void *opc, void *opc_lo, int kpad,
+                         int op_kind, cudaStream_t s);
+// Resident CTAs of the queue kernel on the current device (its grid size).
+template <typename T>
+int factor_queue_grid(int ldlt, int tc_kind);
+
 // ---- solves ----------------------------------------------------------------
 // Vectors in the permuted numbering are of the factor's type T, column-major
 // n x nrhs.  Forward: Z_p = D_p^{-1} Y_p, then Y(rows below) -= L_off Z_p.

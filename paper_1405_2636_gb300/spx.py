@@ -47,7 +47,7 @@ class spx_options(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("grid", ctypes.c_int32 * 3),
                 ("dof", ctypes.c_int32), ("max_width", ctypes.c_int32),
                 ("amalg_ratio", ctypes.c_double), ("perm", ctypes.POINTER(ctypes.c_int64)),
-                ("lower_only", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("lower_only", ctypes.c_int32), ("queue_panels", ctypes.c_int32),
                 ("pivot_tau", ctypes.c_double)]
 
 
@@ -77,12 +77,13 @@ class spx_info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
-KERNEL_CLASSES = ["assemble", "diag", "trsm", "update", "update_tc"]
+KERNEL_CLASSES = ["assemble", "diag", "trsm", "update", "update_tc", "queue"]
+_NK = len(KERNEL_CLASSES)
 
 
 class spx_kernel_stats(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5),
-                ("flops", ctypes.c_double * 5), ("bytes", ctypes.c_double * 5)]
+    _fields_ = [("ms", ctypes.c_double * _NK), ("launches", ctypes.c_int64 * _NK),
+                ("flops", ctypes.c_double * _NK), ("bytes", ctypes.c_double * _NK)]
 
     def as_dict(self) -> dict:
         return {c: {"ms": self.ms[i], "launches": self.launches[i], "flops": self.flops[i],

@@ -300,3 +300,27 @@ def test_panel_tree_invariants(method, maker, opts):
     has_child[par[par >= 0]] = True
     assert np.all(lev[~has_child] == 0) and info["nlevels"] == lev.max() + 1
     h.free()
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the ctypes binding mirrors has the size the C compiler
+    gives the declaration in include/spx.h (a field added on one side only
+    would make the library write past the binding's buffer)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    names = ["spx_options", "spx_refine", "spx_solve_info", "spx_info", "spx_kernel_stats",
+             "spx_batch_info"]
+    src.write_text('#include <stdio.h>\n#include "spx.h"\nint main(void){\n' +
+                   "".join(f'printf("%zu\\n", sizeof({n}));\n' for n in names) + "return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                            text=True).stdout.split()]
+    import ctypes
+    assert sizes == [ctypes.sizeof(getattr(spx, n)) for n in names]
+    assert spx.spx_kernel_stats.as_dict  # one entry per kernel class of the header
+    assert len(spx.KERNEL_CLASSES) == 6
