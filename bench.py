@@ -58,11 +58,28 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "of fallback"}
 
 
+# DRAM traffic per launch from one ncu capture of the committed kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the algorithmic bytes of
+# the same launch; profiles/ holds the captures and their commands.
+NCU_TRAFFIC = {
+    "diag": {"traffic": 107.3e3, "algorithmic_bytes": 2 * 64 * 64 * 4,
+             "launch": "potrf_ldl_kernel<float,64>, one 64-wide panel, 48^3 diffusion (cold caches)",
+             "source": "profiles/potrf_ldl_kernel_diffusion3d_48.md"},
+    "update_tc": {"traffic": 37.8e6, "algorithmic_bytes": None,
+                  "launch": "update_tc_kernel<0>, 4728 tiles of one mid-tree level, 48^3 diffusion",
+                  "source": "profiles/update_tc_kernel_diffusion3d_48.md"},
+}
+
+
 def class_roofline(cls: str, st: dict, mode: str, peaks: dict) -> dict:
     """Roofline of one kernel class from its algorithmic work and device time."""
     ms = st["ms"]
+    tr = NCU_TRAFFIC.get(cls) if mode != "fp64" else None
     out = {"kernel_class": cls, "launches": st["launches"], "device_ms": ms,
-           "algorithmic_flops": st["flops"], "algorithmic_bytes": st["bytes"], "traffic": None}
+           "algorithmic_flops": st["flops"], "algorithmic_bytes": st["bytes"],
+           "traffic": tr["traffic"] if tr else None}
+    if tr:
+        out["traffic_detail"] = tr
     if ms <= 0:
         return out
     if cls in ("assemble", "update_tc"):
@@ -470,6 +487,60 @@ def run_ldlt(torch, spx, inputs, steps: int) -> dict:
             min(out[m]["ms_per_step"] for m in ("fp32", "tf32", "bf16"))}
 
 
+def run_elasticity(torch, spx, inputs, steps: int) -> dict:
+    """The 27-point, 3-dof elasticity-like system on a 40^3 grid (n = 192,000,
+    14.8M nonzeros): plain FP64 against BF16 updates (FP32 accumulation, FP64
+    diagonal blocks) with FP64 refinement to backward error 1e-12; one step =
+    factorization + 16-RHS solve, CUDA events on the current stream."""
+    dims = (40, 40, 40)
+    A = inputs.elasticity_27pt(*dims, 7)
+    cp, ri, vals = inputs.csc_arrays(A)
+    n = A.shape[0]
+    B = inputs.rhs(n, NRHS, 7)
+    h = spx.analyze(cp, ri, "llt", ordering=spx.SPX_ORDER_GRID, grid=dims, dof=3, max_width=64)
+    flops = h.info()["flops"]
+    vd = torch.from_numpy(vals).cuda()
+    Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+    Xd = torch.empty((NRHS, n), dtype=torch.float64, device="cuda").t()
+    out = {}
+    for mode in ("fp64", "tf32", "bf16"):
+        ref = None if mode == "fp64" else spx.default_refine(tol=TARGET_BERR)
+        times, fms, sms = [], [], []
+        for it in range(max(2, steps) + 1):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.factorize(vd, mode)
+            _, si = h.solve(Bd, Xd, refine=ref)
+            e1.record()
+            torch.cuda.synchronize()
+            if it > 0:
+                times.append(e0.elapsed_time(e1))
+                fms.append(h.info()["factor_ms"])
+                sms.append(h.info()["solve_ms"])
+        X = Xd.cpu().numpy()
+        R = B - A @ X
+        den = abs(A).sum(axis=1).max() * np.abs(X).max(axis=0) + np.abs(B).max(axis=0)
+        out[mode] = {"ms_per_step": statistics.median(times), "factor_ms": statistics.median(fms),
+                     "solve_ms": statistics.median(sms),
+                     "time_to_solve_gflops": flops / (statistics.median(times) / 1e3) / 1e9,
+                     "factor_gflops": flops / (statistics.median(fms) / 1e3) / 1e9,
+                     "host_backward_error": float(np.max(np.abs(R).max(axis=0) / den)),
+                     "refine_iters": si["iters"], "gmres_iters": si["gmres_iters"],
+                     "converged": bool(si["converged"])}
+    info = h.info()
+    h.free()
+    return {"workload": "elasticity3d_40^3_27pt_3dof: K = R diag(mu) R^T per neighbour pair, "
+                        "mu ~ logU[1,1e3], 16 rhs",
+            "n": n, "nnz_a": int(cp[-1]), "nnz_l": info["nnz_l"], "flops_exact": flops,
+            "target_backward_error": TARGET_BERR, "modes": out,
+            "speedup_bf16_over_fp64": out["fp64"]["ms_per_step"] / out["bf16"]["ms_per_step"],
+            "speedup_best_mixed_over_fp64": out["fp64"]["ms_per_step"] /
+            min(out[m]["ms_per_step"] for m in ("tf32", "bf16") if out[m]["converged"])
+            if any(out[m]["converged"] for m in ("tf32", "bf16")) else None}
+
+
 # ---------------------------------------------------------------------------
 # the kernel study of Sec. V-B through the factorization's update kernels
 # ---------------------------------------------------------------------------
@@ -701,6 +772,7 @@ def main():
     if not args.no_extra:
         extra["differentiation"] = run_differentiation(torch, spx, inputs, args.steps)
         extra["ldlt"] = run_ldlt(torch, spx, inputs, args.steps)
+        extra["elasticity"] = run_elasticity(torch, spx, inputs, args.steps)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_rate((32, 32, 32), 12.0)   # about 12-15 s of single-core work

@@ -84,6 +84,12 @@ typedef struct {
                                own); 0 = default: the whole tree for an FP64 factor, none for the
                                single-precision factors (the policy that measured fastest) */
     double pivot_tau;       /* LU static-pivot threshold; < 0 = sqrt(2^-52) * ||A||_inf at factorize */
+    int32_t deterministic;  /* 1: bit-reproducible factors -- the updates of a level run in rounds, one
+                               task per target panel per round in task order, so that every target
+                               entry receives its contributions in a fixed order (every level launched
+                               on its own; more launches); 0 (default): concurrent updates with atomic
+                               reductions in whatever order they land */
+    int32_t reserved1;
 } spx_options;
 
 /* Fill *opt with the defaults above. */

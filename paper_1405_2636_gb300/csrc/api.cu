@@ -80,6 +80,15 @@ struct spx_handle_s {
     int32_t *d_fq_need[2] = {nullptr, nullptr};
     int32_t *d_fq_pchunk = nullptr, *d_fq_state = nullptr;
     int64_t fq_nchunks = 0;
+    // deterministic updates: each level's tiles sorted by round (the rank of
+    // their task among the level's tasks with the same target); rounds are
+    // launched one after the other, so that every target entry receives at
+    // most one reduction per launch, in task order.  det_ptr[s][det_base[l] + r]
+    // is where round r of segment s of level l starts (R_l + 1 entries).
+    bool deterministic = false;
+    std::vector<int32_t> det_rounds;   // per level
+    std::vector<int64_t> det_base;     // per level, into det_ptr[*]
+    std::vector<int64_t> det_ptr[7];   // segments: SIMT wide, SIMT narrow, U^T wide, U^T narrow, tc, tc-small wide, tc-small narrow
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
     int kpad = 0;                     // operand-copy row length
@@ -137,6 +146,7 @@ struct spx_handle_s {
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
     spx_kernel_stats kstats{};
+    int64_t class_launches[SPX_K_CLASSES] = {};   // kernels per class of the last enqueued factorization
     int64_t cnt = 0;                  // kernels enqueued by the current call
     int64_t sweep_launches = 0;       // kernels of one solve sweep
 
@@ -292,7 +302,7 @@ int queue_policy_level(const spx::Plan &P, int qopt, int prec)
 int32_t queue_level(spx_handle h, int prec)
 {
     const spx::Plan &P = h->plan;
-    if (h->q_level >= P.nlevels) return P.nlevels;
+    if (h->q_level >= P.nlevels || h->deterministic) return P.nlevels;
     return queue_policy_level(P, h->queue_panels, prec) >= P.nlevels ? P.nlevels : h->q_level;
 }
 
@@ -603,6 +613,41 @@ spx_status ensure_device(spx_handle h)
         h->tile_ptr[l + 1] = (int64_t)tiles.size();
         h->tileu_ptr[l + 1] = (int64_t)tilesu.size();
     }
+    // rounds of the deterministic mode; every per-level tile segment is kept
+    // sorted by round (the order inside a level does not matter otherwise)
+    std::vector<int32_t> task_round(P.tasks.size(), 0);
+    h->det_rounds.assign(P.nlevels, 0);
+    h->det_base.assign(P.nlevels + 1, 0);
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+        std::vector<int32_t> seen;   // the level's targets, sorted
+        int32_t R = 0;
+        for (int32_t t = P.level_task_ptr[l]; t < P.level_task_ptr[l + 1]; ++t) seen.push_back(P.tasks[t].tgt);
+        std::sort(seen.begin(), seen.end());
+        std::vector<int32_t> used(seen.size(), 0);
+        for (int32_t t = P.level_task_ptr[l]; t < P.level_task_ptr[l + 1]; ++t) {
+            const size_t k = std::lower_bound(seen.begin(), seen.end(), P.tasks[t].tgt) - seen.begin();
+            task_round[t] = used[k]++;
+            R = std::max(R, task_round[t] + 1);
+        }
+        h->det_rounds[l] = R;
+        h->det_base[l + 1] = h->det_base[l] + R + 1;
+    }
+    auto sort_segment = [&](std::vector<UpdTile> &v, int64_t a, int64_t b, int32_t l, std::vector<int64_t> &ptr) {
+        std::stable_sort(v.begin() + a, v.begin() + b, [&](const UpdTile &x, const UpdTile &y) {
+            return task_round[x.task] < task_round[y.task];
+        });
+        int64_t i = a;
+        for (int32_t r = 0; r <= h->det_rounds[l]; ++r) {
+            while (i < b && task_round[v[i].task] < r) ++i;
+            ptr.push_back(i);
+        }
+    };
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+        sort_segment(tiles, h->tile_ptr[l], h->tile_nar[l], l, h->det_ptr[0]);
+        sort_segment(tiles, h->tile_nar[l], h->tile_ptr[l + 1], l, h->det_ptr[1]);
+        sort_segment(tilesu, h->tileu_ptr[l], h->tileu_nar[l], l, h->det_ptr[2]);
+        sort_segment(tilesu, h->tileu_nar[l], h->tileu_ptr[l + 1], l, h->det_ptr[3]);
+    }
     if ((st = upload(h, &h->d_chunks, chunks)) || (st = upload(h, &h->d_tiles, tiles)) ||
         (st = upload(h, &h->d_tilesu, tilesu)))
         return st;
@@ -723,6 +768,19 @@ spx_status ensure_device(spx_handle h)
             h->tcsmall_ptr[l + 1] = (int64_t)small.size();
             h->tctile_ptr[l + 1] = (int64_t)tct.size();
         }
+        for (int32_t l = 0; l < P.nlevels; ++l) {
+            std::vector<UpdTile> tmp;   // the tensor-core tiles through the same sort
+            tmp.reserve((size_t)(h->tctile_ptr[l + 1] - h->tctile_ptr[l]));
+            for (int64_t i = h->tctile_ptr[l]; i < h->tctile_ptr[l + 1]; ++i)
+                tmp.push_back(UpdTile{tct[i].task, tct[i].m0, tct[i].n0, 0});
+            std::vector<int64_t> ptr;
+            sort_segment(tmp, 0, (int64_t)tmp.size(), l, ptr);
+            for (size_t i = 0; i < tmp.size(); ++i)
+                tct[h->tctile_ptr[l] + i] = spx::TcTile{tmp[i].task, tmp[i].m0, tmp[i].n0, 0};
+            for (int64_t v : ptr) h->det_ptr[4].push_back(v + h->tctile_ptr[l]);
+            sort_segment(small, h->tcsmall_ptr[l], h->tcsmall_nar[l], l, h->det_ptr[5]);
+            sort_segment(small, h->tcsmall_nar[l], h->tcsmall_ptr[l + 1], l, h->det_ptr[6]);
+        }
         if ((st = upload(h, &h->d_tcsmall, small)) || (st = upload(h, &h->d_tctiles, tct)))
             return st;
         int nsm = 0;
@@ -800,6 +858,7 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
     const int op_kind = operand_kind(P.method, prec);
     T *W = (T *)h->d_W;
     int64_t &cnt = h->cnt;
+    for (int c = 0; c < SPX_K_CLASSES; ++c) h->class_launches[c] = 0;
     mk.mark(-1);
     init_scalars_kernel<<<1, 1, 0, s>>>(h->d_err, h->d_nrepl, h->d_anorm);
     cudaMemsetAsync(h->d_tcerr, 0, sizeof(int), s);
@@ -842,51 +901,74 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
                 spx::launch_getrf<T>(h->dp, h->d_level_panels + a, b - a, cw, kClassThreads[c], L,
                                      Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
             cnt += 1;
+            h->class_launches[SPX_K_DIAG] += 1;
         }
         (void)panels;
         (void)np;
         mk.mark(SPX_K_DIAG);
+        // update launches of this level: one set, or one set per round in the
+        // deterministic mode (slices of the round-sorted tile segments)
+        const int nround = h->deterministic ? std::max(1, h->det_rounds[l]) : 1;
+        auto seg = [&](int sgi, int64_t a, int64_t b, int r, int64_t *lo) -> int {
+            if (!h->deterministic) {
+                *lo = a;
+                return (int)(b - a);
+            }
+            const int64_t *ptr = h->det_ptr[sgi].data() + h->det_base[l];
+            *lo = ptr[r];
+            return (int)(ptr[r + 1] - ptr[r]);
+        };
+        int64_t o;
         if (!lu) {
             spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, ldlt ? spx::TRSM_LDLT : spx::TRSM_LLT, opc, opc_lo,
                                 h->kpad, op_kind, s, W);
             cnt += nch > 0;
+            h->class_launches[SPX_K_TRSM] += nch > 0;
             mk.mark(SPX_K_TRSM);
             const T *Bop = ldlt ? W : L;   // LDL^T: C -= L (D L^T)
-            if (!tc) {
-                spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, Bop, L, 1, 0, s, 0);
-                spx::launch_update<T>(h->dp, h->d_tasks, tln, ntln, L, Bop, L, 1, 0, s, 1);
-                cnt += (ntl > 0) + (ntln > 0);
-                mk.mark(SPX_K_UPDATE);
-            } else {
-                const UpdTile *ts = h->d_tcsmall + h->tcsmall_ptr[l];
-                const int nts = (int)(h->tcsmall_nar[l] - h->tcsmall_ptr[l]);
-                const UpdTile *tsn = h->d_tcsmall + h->tcsmall_nar[l];
-                const int ntsn = (int)(h->tcsmall_ptr[l + 1] - h->tcsmall_nar[l]);
-                const spx::TcTile *tt = h->d_tctiles + h->tctile_ptr[l];
-                const int ntt = (int)(h->tctile_ptr[l + 1] - h->tctile_ptr[l]);
-                spx::launch_update<T>(h->dp, h->d_tasks, ts, nts, L, Bop, L, 1, 0, s, 0);
-                spx::launch_update<T>(h->dp, h->d_tasks, tsn, ntsn, L, Bop, L, 1, 0, s, 1);
-                mk.mark(SPX_K_UPDATE);
-                spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, tt, ntt,
-                                      (float *)L, 1, h->d_tcerr, s);
-                mk.mark(SPX_K_UPDATE_TC);
-                cnt += (nts > 0) + (ntsn > 0) + (ntt > 0);
+            for (int r = 0; r < nround; ++r) {
+                if (!tc) {
+                    const int a = seg(0, h->tile_ptr[l], h->tile_nar[l], r, &o);
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + o, a, L, Bop, L, 1, 0, s, 0);
+                    const int b = seg(1, h->tile_nar[l], h->tile_ptr[l + 1], r, &o);
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + o, b, L, Bop, L, 1, 0, s, 1);
+                    cnt += (a > 0) + (b > 0);
+                    h->class_launches[SPX_K_UPDATE] += (a > 0) + (b > 0);
+                    mk.mark(SPX_K_UPDATE);
+                } else {
+                    const int a = seg(5, h->tcsmall_ptr[l], h->tcsmall_nar[l], r, &o);
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tcsmall + o, a, L, Bop, L, 1, 0, s, 0);
+                    const int b = seg(6, h->tcsmall_nar[l], h->tcsmall_ptr[l + 1], r, &o);
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tcsmall + o, b, L, Bop, L, 1, 0, s, 1);
+                    mk.mark(SPX_K_UPDATE);
+                    const int c = seg(4, h->tctile_ptr[l], h->tctile_ptr[l + 1], r, &o);
+                    spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, h->d_tctiles + o, c,
+                                          (float *)L, 1, h->d_tcerr, s);
+                    mk.mark(SPX_K_UPDATE_TC);
+                    cnt += (a > 0) + (b > 0) + (c > 0);
+                    h->class_launches[SPX_K_UPDATE] += (a > 0) + (b > 0);
+                    h->class_launches[SPX_K_UPDATE_TC] += c > 0;
+                }
             }
         } else {
-            const UpdTile *tu = h->d_tilesu + h->tileu_ptr[l];
-            const int ntu = (int)(h->tileu_nar[l] - h->tileu_ptr[l]);
-            const UpdTile *tun = h->d_tilesu + h->tileu_nar[l];
-            const int ntun = (int)(h->tileu_ptr[l + 1] - h->tileu_nar[l]);
             spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, spx::TRSM_LU_L, nullptr, nullptr, 0, 0, s);
             spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, U, spx::TRSM_LU_U, nullptr, nullptr, 0, 0, s);
             cnt += 2 * (nch > 0);
+            h->class_launches[SPX_K_TRSM] += 2 * (nch > 0);
             mk.mark(SPX_K_TRSM);
-            spx::launch_update<T>(h->dp, h->d_tasks, tl, ntl, L, U, L, 0, 0, s, 0);
-            spx::launch_update<T>(h->dp, h->d_tasks, tln, ntln, L, U, L, 0, 0, s, 1);
-            spx::launch_update<T>(h->dp, h->d_tasks, tu, ntu, U, L, U, 0, 1, s, 0);
-            spx::launch_update<T>(h->dp, h->d_tasks, tun, ntun, U, L, U, 0, 1, s, 1);
-            cnt += (ntl > 0) + (ntln > 0) + (ntu > 0) + (ntun > 0);
-            mk.mark(SPX_K_UPDATE);
+            for (int r = 0; r < nround; ++r) {
+                const int a = seg(0, h->tile_ptr[l], h->tile_nar[l], r, &o);
+                spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + o, a, L, U, L, 0, 0, s, 0);
+                const int b = seg(1, h->tile_nar[l], h->tile_ptr[l + 1], r, &o);
+                spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + o, b, L, U, L, 0, 0, s, 1);
+                const int c = seg(2, h->tileu_ptr[l], h->tileu_nar[l], r, &o);
+                spx::launch_update<T>(h->dp, h->d_tasks, h->d_tilesu + o, c, U, L, U, 0, 1, s, 0);
+                const int d = seg(3, h->tileu_nar[l], h->tileu_ptr[l + 1], r, &o);
+                spx::launch_update<T>(h->dp, h->d_tasks, h->d_tilesu + o, d, U, L, U, 0, 1, s, 1);
+                cnt += (a > 0) + (b > 0) + (c > 0) + (d > 0);
+                h->class_launches[SPX_K_UPDATE] += (a > 0) + (b > 0) + (c > 0) + (d > 0);
+                mk.mark(SPX_K_UPDATE);
+            }
         }
     }
     if (qlev < P.nlevels) {
@@ -910,6 +992,7 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
                                     L, Dinv, W, h->d_tau, h->d_err, h->d_nrepl, h->d_nneg, ldlt ? 1 : 0,
                                     tc ? op_kind : -1, h->tmap, h->tmap_lo, opc, opc_lo, h->kpad, op_kind, s);
         cnt += 2;
+        h->class_launches[SPX_K_QUEUE] += 1;
         mk.mark(SPX_K_QUEUE);
     }
 }
@@ -1428,6 +1511,7 @@ spx_status spx_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, 
     h->method = method;
     h->pivot_tau_opt = o.pivot_tau;
     h->queue_panels = o.queue_panels < 0 ? -1 : o.queue_panels;
+    h->deterministic = o.deterministic != 0;
     const spx::Plan &P = h->plan;
     spx_info &I = h->info;
     I.n = P.n;
@@ -1568,23 +1652,7 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
         // zero fill of the factor (one write) + the scatter (value and map read, one write)
         K.bytes[SPX_K_ASSEMBLE] = (double)P.nnz_a * (16.0 + e * nfac) + (double)elems * e * nfac;
         K.launches[SPX_K_ASSEMBLE] = P.nnz_a > 0 ? 4 : 3;
-        K.launches[SPX_K_QUEUE] = qlev < P.nlevels ? 1 : 0;
-        for (int32_t l = 0; l < qlev; ++l) {
-            for (int c = 0; c < kNumClasses; ++c)
-                K.launches[SPX_K_DIAG] += (h->cls_ptr[(size_t)l * kNumClasses + c + 1] >
-                                           h->cls_ptr[(size_t)l * kNumClasses + c]);
-            K.launches[SPX_K_TRSM] += (int64_t)nfac * (h->chunk_ptr[l + 1] > h->chunk_ptr[l]);
-            if (tcm) {
-                K.launches[SPX_K_UPDATE] += (h->tcsmall_nar[l] > h->tcsmall_ptr[l]) +
-                                            (h->tcsmall_ptr[l + 1] > h->tcsmall_nar[l]);
-                K.launches[SPX_K_UPDATE_TC] += (h->tctile_ptr[l + 1] > h->tctile_ptr[l]);
-            } else {
-                K.launches[SPX_K_UPDATE] += (h->tile_nar[l] > h->tile_ptr[l]) +
-                                            (h->tile_ptr[l + 1] > h->tile_nar[l]) +
-                                            (h->tileu_nar[l] > h->tileu_ptr[l]) +
-                                            (h->tileu_ptr[l + 1] > h->tileu_nar[l]);
-            }
-        }
+        for (int c = 1; c < SPX_K_CLASSES; ++c) K.launches[c] = h->class_launches[c];
     }
     std::memcpy(&h->anorm, &abits, 8);
     h->info.factor_ms = ms;

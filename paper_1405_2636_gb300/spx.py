@@ -48,7 +48,8 @@ class spx_options(ctypes.Structure):
                 ("dof", ctypes.c_int32), ("max_width", ctypes.c_int32),
                 ("amalg_ratio", ctypes.c_double), ("perm", ctypes.POINTER(ctypes.c_int64)),
                 ("lower_only", ctypes.c_int32), ("queue_panels", ctypes.c_int32),
-                ("pivot_tau", ctypes.c_double)]
+                ("pivot_tau", ctypes.c_double), ("deterministic", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
 
 
 class spx_refine(ctypes.Structure):
