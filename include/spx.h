@@ -316,6 +316,52 @@ spx_status spx_roofline_model(spx_handle h, spx_precision precision, const doubl
 /* Release a handle and everything it owns.  NULL-safe. */
 void spx_free(spx_handle h);
 
+/* ---- Subtree-to-rank distribution with fan-in (Sec. VI) ------------------
+ *
+ * The paper's future work distributes the elimination tree's bottom
+ * subtrees over GPUs and accumulates their contributions to the top
+ * separators before those are factored (fan-in).  spx_partition maps whole
+ * subtrees of the panel tree to nranks ranks, balancing their flops within
+ * 5% where the tree allows; the panels above them (the top) belong to rank
+ * 0.  Every update task then stays inside one rank's subtrees or goes from
+ * them into the top, so one sum over the ranks of their top panels is the
+ * whole exchange.  A distributed factorization, one handle per rank on the
+ * same pattern:
+ *   every rank r: spx_partition, spx_factorize_part(h, values, ..., r) --
+ *                 rank r's subtrees factored, their updates subtracted into
+ *                 its copy of the top panels, which holds A's values on rank
+ *                 0 and zeros on the other ranks;
+ *                 spx_part_get(h, -1, 0, buf): its top panel values;
+ *   sum the buffers onto rank 0 (e.g. an NCCL or gloo reduce);
+ *   rank 0:       spx_part_set(h, -1, 0, sum); spx_factorize_part(h, NULL, ..., -1)
+ *                 factors the top.  For a solve on rank 0, copy each other
+ *                 rank's part in (spx_part_get / spx_part_set with inverses).
+ * Cholesky and LDL^T, panels at most 64 wide; every part runs on the
+ * device-side task queue.  Calls return after their device work completed. */
+
+/* Partition for nranks ranks.  panel_owner (host int32[npanels], or NULL):
+ * the rank owning each panel, -1 for the top.  part_values, part_inverses
+ * (host int64[nranks + 1], or NULL): elements of the factor's type in the
+ * packed values and inverse blocks of each part (index nranks: the top).
+ * SPX_ERR_ARG for LU, panels wider than 64, or nranks outside [1, 4096]. */
+spx_status spx_partition(spx_handle h, int32_t nranks, int32_t *panel_owner, int64_t *part_values,
+                         int64_t *part_inverses);
+
+/* part = r in [0, nranks): factor rank r's subtrees (values as for
+ * spx_factorize); part = -1: factor the top panels of this handle (after
+ * its own part and spx_part_set of the summed top values; `values` is not
+ * read).  After the top the handle reports a complete factor: a solve needs
+ * every other rank's part copied in first. */
+spx_status spx_factorize_part(spx_handle h, const double *values, int values_on_device,
+                              spx_precision precision, int32_t part, void *cuda_stream);
+
+/* Copy the panel values (and, with_inverses = 1, then the inverted diagonal
+ * blocks) of part `part` (-1: the top) between the handle's factor and a
+ * packed device buffer `buf` of the factor's type (sizes from spx_partition). */
+spx_status spx_part_get(spx_handle h, int32_t part, int32_t with_inverses, void *buf, void *cuda_stream);
+spx_status spx_part_set(spx_handle h, int32_t part, int32_t with_inverses, const void *buf,
+                        void *cuda_stream);
+
 /* ---- The supernodal update on its own (the kernel study of Sec. V-B) ------
  *
  * C = C - A B^T, where A (m x k) holds the rows of a source panel, B is its

@@ -80,6 +80,29 @@ struct spx_handle_s {
     int32_t *d_fq_need[2] = {nullptr, nullptr};
     int32_t *d_fq_pchunk = nullptr, *d_fq_state = nullptr;
     int64_t fq_nchunks = 0;
+    // host copies of the launch lists (for the item lists of partitions)
+    std::vector<RowChunk> hc_chunks;
+    std::vector<UpdTile> hc_tiles, hc_small;
+    std::vector<spx::TcTile> hc_tct;
+    std::vector<int32_t> h_pchunk;
+    int workers = 0;
+    // subtree-to-rank partition (spx_partition): owner rank of each panel's
+    // subtree, -1 for the top panels; per part (rank r at index r, the top at
+    // index nranks) the packed ranges of its panel values and inverse blocks
+    // and its queue item lists (built on first use, per update mode)
+    int32_t part_nranks = 0;
+    int part_done = 0;                 // 1: a rank's subtrees factored here, 2: the top factored here
+    std::vector<int32_t> panel_owner;
+    struct Part {
+        int64_t nval = 0, ninv = 0;          // packed elements
+        std::vector<int64_t> h_ranges;       // (storage offset, length, packed offset): values, then inverses
+        int64_t *d_ranges = nullptr;         // device copy
+        int32_t nr = 0;
+        spx::FqItem *d_items[2] = {nullptr, nullptr};
+        int32_t *d_need[2] = {nullptr, nullptr};
+        int32_t nitems[2] = {-1, -1};
+    };
+    std::vector<Part> parts;
     // deterministic updates: each level's tiles sorted by round (the rank of
     // their task among the level's tasks with the same target); rounds are
     // launched one after the other, so that every target entry receives at
@@ -306,30 +329,30 @@ int32_t queue_level(spx_handle h, int prec)
     return queue_policy_level(P, h->queue_panels, prec) >= P.nlevels ? P.nlevels : h->q_level;
 }
 
-// Item lists of the queue region (fqueue.cuh): per level l, its diagonal
-// blocks; the far update tiles of level l-1 (targets above level l); its
-// TRSM chunks; its near update tiles (targets at level l+1).  Every wait is
-// then on an earlier item, which is checked here before anything is uploaded.
-spx_status build_queue(spx_handle h, const std::vector<RowChunk> &chunks, const std::vector<UpdTile> &tiles,
-                       const std::vector<UpdTile> &small, const std::vector<spx::TcTile> &tct, int workers)
+// Item list of a queue over a set of panels (fqueue.cuh): their diagonal
+// blocks and TRSM chunks, and the update tiles of the tasks whose source is
+// in the set (targets outside the set receive their updates but are not
+// factored).  Built per level l: its diagonal blocks; the far update tiles of
+// level l-1 (targets above level l); its TRSM chunks; its near update tiles
+// (targets at level l+1); then reordered by list scheduling.  Every wait is
+// then on an earlier item, which is checked here.  mode 0: CUDA-core update
+// tiles (`tiles`), 1: tensor-core tiles (`tct`) and the narrow sources'
+// CUDA-core tiles (`small`).
+spx_status make_items(spx_handle h, const std::vector<RowChunk> &chunks, const std::vector<UpdTile> &tiles,
+                      const std::vector<UpdTile> &small, const std::vector<spx::TcTile> &tct,
+                      const std::vector<int32_t> &pchunk, const std::vector<char> &in_set, int workers, int mode,
+                      std::vector<spx::FqItem> &items, std::vector<int32_t> &need)
 {
     const spx::Plan &P = h->plan;
-    const int L0 = queue_start_level(P, h->queue_panels == 0 ? INT32_MAX : h->queue_panels);
-    h->q_level = L0;
-    if (L0 >= P.nlevels) return SPX_OK;
     const int32_t np = P.npanels;
     const int64_t nch = (int64_t)chunks.size();
-    std::vector<int32_t> pchunk(np, -1);
-    for (int64_t c = 0; c < nch; ++c)
-        if (chunks[c].r0 == P.pw[chunks[c].panel]) pchunk[chunks[c].panel] = (int32_t)c;
-    spx_status st;
-    for (int mode = 0; mode < 2; ++mode) {   // 0: CUDA-core updates, 1: tensor-core updates
-        std::vector<spx::FqItem> items;
-        std::vector<int32_t> need(np, 0);
+    items.clear();
+    need.assign(np, 0);
+    {
         auto level_tiles = [&](int l, bool near) {
             auto take = [&](int32_t kind, int64_t idx, int32_t task) {
                 const int32_t tgt = P.tasks[task].tgt;
-                if ((P.plevel[tgt] == l + 1) != near) return;
+                if (!in_set[P.tasks[task].src] || (P.plevel[tgt] == l + 1) != near) return;
                 items.push_back(spx::FqItem{kind, (int32_t)idx});
                 ++need[tgt];
             };
@@ -343,15 +366,19 @@ spx_status build_queue(spx_handle h, const std::vector<RowChunk> &chunks, const 
                     take(spx::FQ_UPD16, i, small[i].task);
             }
         };
-        int64_t ntiles = 0;
-        for (int l = L0; l < P.nlevels; ++l) {
-            ntiles += mode == 0 ? h->tile_ptr[l + 1] - h->tile_ptr[l]
-                                : (h->tctile_ptr[l + 1] - h->tctile_ptr[l]) + (h->tcsmall_ptr[l + 1] - h->tcsmall_ptr[l]);
+        // expected counts, for the check below
+        int64_t ntiles = 0, ndiag_want = 0, ntrsm_want = 0;
+        for (const UpdTile &t : (mode == 0 ? tiles : small)) ntiles += in_set[P.tasks[t.task].src];
+        if (mode == 1)
+            for (const spx::TcTile &t : tct) ntiles += in_set[P.tasks[t.task].src];
+        for (int32_t q = 0; q < np; ++q) ndiag_want += in_set[q];
+        for (int64_t c = 0; c < nch; ++c) ntrsm_want += in_set[chunks[c].panel];
+        for (int l = 0; l < P.nlevels; ++l) {
             for (int32_t q = P.level_ptr[l]; q < P.level_ptr[l + 1]; ++q)
-                items.push_back(spx::FqItem{spx::FQ_DIAG, P.level_panels[q]});
-            if (l - 1 >= L0) level_tiles(l - 1, false);
+                if (in_set[P.level_panels[q]]) items.push_back(spx::FqItem{spx::FQ_DIAG, P.level_panels[q]});
+            if (l >= 1) level_tiles(l - 1, false);
             for (int64_t c = h->chunk_ptr[l]; c < h->chunk_ptr[l + 1]; ++c)
-                items.push_back(spx::FqItem{spx::FQ_TRSM, (int32_t)c});
+                if (in_set[chunks[c].panel]) items.push_back(spx::FqItem{spx::FQ_TRSM, (int32_t)c});
             level_tiles(l, true);
         }
         // Dispatch order: list scheduling of the item DAG on `workers` CTAs
@@ -403,7 +430,7 @@ spx_status build_queue(spx_handle h, const std::vector<RowChunk> &chunks, const 
                             last = c;
                         }
                     }
-                    edge(i, pos_d[tk.tgt]);
+                    if (pos_d[tk.tgt] >= 0) edge(i, pos_d[tk.tgt]);
                 }
             }
             // remaining critical path of each item (items are in a topological order)
@@ -452,8 +479,7 @@ spx_status build_queue(spx_handle h, const std::vector<RowChunk> &chunks, const 
             else if (it.kind == spx::FQ_TRSM) pos_chunk[it.idx] = (int64_t)i, ++ntrsm;
             else ++ntile;
         }
-        bool ok = ntile == ntiles && ndiag == P.level_ptr[P.nlevels] - P.level_ptr[L0] &&
-                  ntrsm == h->chunk_ptr[P.nlevels] - h->chunk_ptr[L0];
+        bool ok = ntile == ntiles && ndiag == ndiag_want && ntrsm == ntrsm_want;
         auto chunks_done_before = [&](int src, int r_lo, int r_hi, int64_t at) {
             if (pchunk[src] < 0 || r_lo < P.pw[src] || r_hi <= r_lo) return false;
             const int64_t c0 = pchunk[src] + (r_lo - P.pw[src]) / spx::kTrsmRows;
@@ -481,18 +507,43 @@ spx_status build_queue(spx_handle h, const std::vector<RowChunk> &chunks, const 
             }
             const spx::Task &tk = P.tasks[task];
             const int hsrc = P.ph[tk.src];
-            ok = P.plevel[tk.src] >= L0 && pos_diag[tk.tgt] > (int64_t)i &&
+            ok = in_set[tk.src] && (!in_set[tk.tgt] || pos_diag[tk.tgt] > (int64_t)i) &&
                  chunks_done_before(tk.src, m0, std::min(m0 + tm, hsrc), (int64_t)i) &&
                  chunks_done_before(tk.src, n0, std::min(n0 + tn, tk.r1), (int64_t)i);
         }
         if (!ok) return fail(h, SPX_ERR_STATE, "internal: factorization queue order violates a dependency");
-        h->fq_nitems[mode] = (int32_t)items.size();
-        if ((st = upload(h, &h->d_fq_items[mode], items)) || (st = upload(h, &h->d_fq_need[mode], need))) return st;
     }
+    return SPX_OK;
+}
+
+// The queue of the upper levels [q_level, nlevels), both update modes.
+spx_status build_queue(spx_handle h, const std::vector<RowChunk> &chunks, const std::vector<UpdTile> &tiles,
+                       const std::vector<UpdTile> &small, const std::vector<spx::TcTile> &tct, int workers)
+{
+    const spx::Plan &P = h->plan;
+    const int L0 = queue_start_level(P, h->queue_panels == 0 ? INT32_MAX : h->queue_panels);
+    h->q_level = L0;
+    const int32_t np = P.npanels;
+    const int64_t nch = (int64_t)chunks.size();
+    std::vector<int32_t> pchunk(np, -1);
+    for (int64_t c = 0; c < nch; ++c)
+        if (chunks[c].r0 == P.pw[chunks[c].panel]) pchunk[chunks[c].panel] = (int32_t)c;
+    spx_status st;
     h->fq_nchunks = nch;
     if ((st = upload(h, &h->d_fq_pchunk, pchunk)) ||
         (st = dalloc(h, &h->d_fq_state, (size_t)2 * np + (size_t)nch + 2)))
         return st;
+    h->h_pchunk = pchunk;
+    if (L0 >= P.nlevels) return SPX_OK;
+    std::vector<char> in_set(np, 0);
+    for (int32_t q = 0; q < np; ++q) in_set[q] = P.plevel[q] >= L0;
+    for (int mode = 0; mode < 2; ++mode) {
+        std::vector<spx::FqItem> items;
+        std::vector<int32_t> need;
+        if ((st = make_items(h, chunks, tiles, small, tct, pchunk, in_set, workers, mode, items, need))) return st;
+        h->fq_nitems[mode] = (int32_t)items.size();
+        if ((st = upload(h, &h->d_fq_items[mode], items)) || (st = upload(h, &h->d_fq_need[mode], need))) return st;
+    }
     return SPX_OK;
 }
 
@@ -785,7 +836,12 @@ spx_status ensure_device(spx_handle h)
             return st;
         int nsm = 0;
         CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-        if ((st = build_queue(h, chunks, tiles, small, tct, 2 * nsm))) return st;   // two queue CTAs per SM
+        h->workers = 2 * nsm;   // two queue CTAs per SM
+        if ((st = build_queue(h, chunks, tiles, small, tct, h->workers))) return st;
+        h->hc_chunks = chunks;
+        h->hc_tiles = tiles;
+        h->hc_small = small;
+        h->hc_tct = tct;
     } else {
         h->q_level = P.nlevels;
     }
@@ -843,8 +899,38 @@ int operand_kind(int method, int prec)
     return prec == SPX_BF16 ? 1 : (prec == SPX_FP32 ? 2 : 0);
 }
 
+// One launch of the task queue over the item list of a partition part (rank
+// r >= 0, or -1 for the top panels); the lists were built by ensure_part_items.
 template <typename T>
-void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
+void enqueue_part_queue(spx_handle h, T *L, T *Dinv, T *W, void *opc, void *opc_lo, int op_kind, bool tc, bool ldlt,
+                        int part, cudaStream_t s)
+{
+    const spx::Plan &P = h->plan;
+    const int mode = tc ? 1 : 0;
+    const spx_handle_s::Part &pt = h->parts[part >= 0 ? part : h->part_nranks];
+    const int32_t np = P.npanels;
+    int32_t *st = h->d_fq_state;
+    cudaMemsetAsync(st, 0, sizeof(int32_t) * ((size_t)2 * np + (size_t)h->fq_nchunks + 2), s);
+    spx::FactorQueue q{};
+    q.items = pt.d_items[mode];
+    q.nitems = pt.nitems[mode];
+    q.need = pt.d_need[mode];
+    q.pchunk = h->d_fq_pchunk;
+    q.cnt = st;
+    q.diag_done = st + np;
+    q.chunk_done = st + 2 * (size_t)np;
+    q.head = st + 2 * (size_t)np + h->fq_nchunks;
+    q.err = q.head + 1;
+    q.spin_limit = h->spin_limit;
+    spx::launch_factor_queue<T>(h->dp, q, h->d_tasks, h->d_chunks, tc ? h->d_tcsmall : h->d_tiles, h->d_tctiles, L,
+                                Dinv, W, h->d_tau, h->d_err, h->d_nrepl, h->d_nneg, ldlt ? 1 : 0, tc ? op_kind : -1,
+                                h->tmap, h->tmap_lo, opc, opc_lo, h->kpad, op_kind, s);
+}
+
+constexpr int kWhole = INT32_MIN;   // enqueue_factorization: the whole factorization
+
+template <typename T>
+void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int part = kWhole)
 {
     const spx::Plan &P = h->plan;
     cudaStream_t s = h->hs;
@@ -860,6 +946,11 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
     int64_t &cnt = h->cnt;
     for (int c = 0; c < SPX_K_CLASSES; ++c) h->class_launches[c] = 0;
     mk.mark(-1);
+    if (part != kWhole && part < 0) {   // the top of a partition: its values came in by spx_part_set
+        enqueue_part_queue<T>(h, L, Dinv, W, opc, opc_lo, op_kind, tc, ldlt, part, s);
+        cnt += 2;
+        return;
+    }
     init_scalars_kernel<<<1, 1, 0, s>>>(h->d_err, h->d_nrepl, h->d_anorm);
     cudaMemsetAsync(h->d_tcerr, 0, sizeof(int), s);
     cudaMemsetAsync(h->d_nneg, 0, sizeof(unsigned long long), s);
@@ -875,6 +966,15 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
     spx::launch_assemble<T>(P.nnz_a, h->d_vals, h->d_amap, L, U, s);
     cnt += P.nnz_a > 0;
     mk.mark(SPX_K_ASSEMBLE);
+    if (part != kWhole) {
+        // a rank's subtrees: the top panels collect only this rank's
+        // contributions (rank 0 keeps A's values there, the others start from 0)
+        const spx_handle_s::Part &top = h->parts[h->part_nranks];
+        if (part > 0) spx::launch_pack_ranges<T>(top.d_ranges, top.nr, L, (T *)nullptr, 2, s);
+        enqueue_part_queue<T>(h, L, Dinv, W, opc, opc_lo, op_kind, tc, ldlt, part, s);
+        cnt += 2 + (part > 0);
+        return;
+    }
     const int32_t qlev = queue_level(h, prec);
     for (int32_t l = 0; l < qlev; ++l) {
         const int32_t *panels = h->d_level_panels + P.level_ptr[l];
@@ -908,15 +1008,22 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec)
         mk.mark(SPX_K_DIAG);
         // update launches of this level: one set, or one set per round in the
         // deterministic mode (slices of the round-sorted tile segments)
-        const int nround = h->deterministic ? std::max(1, h->det_rounds[l]) : 1;
+        // (a level without update tasks has no rounds: nothing to launch)
+        const int nround = h->deterministic ? h->det_rounds[l] : 1;
         auto seg = [&](int sgi, int64_t a, int64_t b, int r, int64_t *lo) -> int {
             if (!h->deterministic) {
                 *lo = a;
                 return (int)(b - a);
             }
+            // round r of the segment [a, b): det_rounds[l] + 1 boundaries from det_base[l]
             const int64_t *ptr = h->det_ptr[sgi].data() + h->det_base[l];
-            *lo = ptr[r];
-            return (int)(ptr[r + 1] - ptr[r]);
+            const int64_t x = ptr[r], y = ptr[r + 1];
+            if (r >= h->det_rounds[l] || x < a || y > b || y < x) {   // never: the lists were built so
+                *lo = a;
+                return 0;
+            }
+            *lo = x;
+            return (int)(y - x);
         };
         int64_t o;
         if (!lu) {
@@ -1437,6 +1544,200 @@ spx_status fgmres(spx_handle h, int nrhs, const spx_refine &rf, double *berr_out
     return SPX_OK;
 }
 
+// Factor storage of the handle for `precision` (reallocated when the storage
+// type changes).
+spx_status ensure_factor_storage(spx_handle h, spx_precision precision)
+{
+    const spx::Plan &P = h->plan;
+    const bool fp64 = precision == SPX_FP64;
+    const size_t elems = (size_t)P.pval[P.npanels];
+    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+    spx_status st;
+    if (h->factor_prec_alloc != (fp64 ? 1 : 0)) {
+        dfree(h, h->d_L);
+        dfree(h, h->d_U);
+        dfree(h, h->d_Dinv);
+        h->d_L = h->d_U = h->d_Dinv = nullptr;
+        h->factor_prec_alloc = -1;
+        char *pl = nullptr, *pd = nullptr;
+        if ((st = dalloc(h, &pl, elems * esz))) return st;
+        h->d_L = pl;
+        if ((st = dalloc(h, &pd, (size_t)h->dinv_elems * esz))) return st;
+        h->d_Dinv = pd;
+        dfree(h, h->d_W);
+        h->d_W = nullptr;
+        if (P.method == SPX_LDLT) {
+            char *pw = nullptr;
+            if ((st = dalloc(h, &pw, elems * esz))) return st;
+            h->d_W = pw;
+        }
+        if (P.method == SPX_LU) {
+            char *pu = nullptr;
+            if ((st = dalloc(h, &pu, elems * esz))) return st;
+            h->d_U = pu;
+        }
+        h->factor_prec_alloc = fp64 ? 1 : 0;
+        if (h->fgraph) {
+            cudaGraphExecDestroy(h->fgraph);
+            h->fgraph = nullptr;
+            h->fgraph_prec = -1;
+        }
+    }
+    if (uses_tensor_cores(P.method, precision)) {
+        if ((st = ensure_operand_copy(h, operand_kind(P.method, precision)))) return st;
+    }
+    return SPX_OK;
+}
+
+// Subtree-to-rank partition of the panel tree (the distribution of Sec. VI's
+// fan-in): subtrees are split from the top, heaviest first, until there are
+// at least nranks of them and a longest-first assignment to the ranks
+// balances their work within 5% (or no subtree can be split further); the
+// split roots and their ancestors are the top panels.  Work of a panel: its
+// diagonal block, TRSM and the updates it sources (flops).  Every update task
+// then stays inside one rank's subtree or goes from a subtree into the top,
+// so each rank's contributions to the top panels can be summed (fan-in)
+// before the top is factored.
+spx_status make_partition(spx_handle h, int nranks)
+{
+    const spx::Plan &P = h->plan;
+    const int32_t np = P.npanels;
+    std::vector<double> w(np, 0.0);
+    for (int32_t q = 0; q < np; ++q) {
+        const double wd = P.pw[q], off = (double)P.ph[q] - P.pw[q];
+        w[q] = wd * wd * wd / 3.0 + off * wd * wd;
+    }
+    for (const spx::Task &tk : P.tasks) {
+        const double M = (double)P.ph[tk.src] - tk.r0, N = (double)tk.r1 - tk.r0, K = P.pw[tk.src];
+        w[tk.src] += 2.0 * M * N * K;
+    }
+    std::vector<double> W(w);
+    std::vector<std::vector<int32_t>> kids(np);
+    for (int32_t q = 0; q < np; ++q) {
+        const int32_t par = P.pparent[q];
+        if (par >= 0) {
+            if (par <= q) return fail(h, SPX_ERR_STATE, "internal: panel tree not in postorder");
+            W[par] += W[q];
+            kids[par].push_back(q);
+        }
+    }
+    std::vector<int32_t> frontier;
+    for (int32_t q = 0; q < np; ++q)
+        if (P.pparent[q] < 0) frontier.push_back(q);
+    std::vector<char> top(np, 0);
+    std::vector<int32_t> root_rank;
+    for (int it = 0; it <= np; ++it) {
+        std::sort(frontier.begin(), frontier.end(), [&](int32_t a, int32_t b) { return W[a] > W[b] || (W[a] == W[b] && a < b); });
+        std::vector<double> load(nranks, 0.0);
+        root_rank.assign(frontier.size(), 0);
+        double total = 0.0;
+        for (size_t f = 0; f < frontier.size(); ++f) {
+            const int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            root_rank[f] = r;
+            load[r] += W[frontier[f]];
+            total += W[frontier[f]];
+        }
+        const double imbalance = total > 0.0 ? *std::max_element(load.begin(), load.end()) / (total / nranks) : 1.0;
+        if ((int)frontier.size() >= nranks && imbalance <= 1.05) break;
+        size_t pick = frontier.size();
+        for (size_t f = 0; f < frontier.size(); ++f)
+            if (!kids[frontier[f]].empty()) {
+                pick = f;
+                break;
+            }
+        if (pick == frontier.size()) break;
+        const int32_t q = frontier[pick];
+        top[q] = 1;
+        frontier.erase(frontier.begin() + pick);
+        for (int32_t c : kids[q]) frontier.push_back(c);
+    }
+    h->panel_owner.assign(np, -1);
+    for (size_t f = 0; f < frontier.size(); ++f) {
+        std::vector<int32_t> stack(1, frontier[f]);
+        while (!stack.empty()) {
+            const int32_t q = stack.back();
+            stack.pop_back();
+            h->panel_owner[q] = root_rank[f];
+            for (int32_t c : kids[q]) stack.push_back(c);
+        }
+    }
+    for (int32_t q = 0; q < np; ++q)
+        if ((h->panel_owner[q] < 0) != (top[q] != 0)) return fail(h, SPX_ERR_STATE, "internal: partition does not cover the tree");
+    for (const spx::Task &tk : P.tasks) {   // the fan-in property
+        const int a = h->panel_owner[tk.src], b = h->panel_owner[tk.tgt];
+        if (!(a == b || b < 0)) return fail(h, SPX_ERR_STATE, "internal: an update crosses two subtrees");
+    }
+    // packed ranges per part: values, then inverse blocks
+    for (auto &pt : h->parts) {
+        dfree(h, pt.d_ranges);
+        for (int m = 0; m < 2; ++m) {
+            dfree(h, pt.d_items[m]);
+            dfree(h, pt.d_need[m]);
+        }
+    }
+    h->parts.assign(nranks + 1, spx_handle_s::Part{});
+    std::vector<int64_t> hpinv(np + 1, 0);
+    for (int32_t q = 0; q < np; ++q) hpinv[q + 1] = hpinv[q] + (((int64_t)P.pw[q] * P.pw[q] + 31) & ~(int64_t)31);
+    for (int k = 0; k <= nranks; ++k) {
+        const int owner = k < nranks ? k : -1;
+        std::vector<int64_t> rv, ri;
+        int64_t pos = 0;
+        int32_t nr = 0;
+        for (int32_t q = 0; q < np; ++q)
+            if (h->panel_owner[q] == owner) {
+                const int64_t len = P.pval[q + 1] - P.pval[q];
+                rv.insert(rv.end(), {P.pval[q], len, pos});
+                pos += len;
+                ++nr;
+            }
+        const int64_t nval = pos;
+        for (int32_t q = 0; q < np; ++q)
+            if (h->panel_owner[q] == owner) {
+                const int64_t len = (int64_t)P.pw[q] * P.pw[q];
+                ri.insert(ri.end(), {hpinv[q], len, pos});
+                pos += len;
+            }
+        rv.insert(rv.end(), ri.begin(), ri.end());
+        spx_handle_s::Part &pt = h->parts[k];
+        pt.nr = nr;
+        pt.nval = nval;
+        pt.ninv = pos - nval;
+        pt.h_ranges.swap(rv);
+    }
+    h->part_nranks = nranks;
+    return SPX_OK;
+}
+
+// Device copies of the partition's range lists (first device use).
+spx_status ensure_part_device(spx_handle h)
+{
+    spx_status st = ensure_device(h);
+    if (st != SPX_OK) return st;
+    for (auto &pt : h->parts)
+        if (!pt.d_ranges && (st = upload(h, &pt.d_ranges, pt.h_ranges))) return st;
+    return SPX_OK;
+}
+
+// Queue item lists of partition part k (rank k, or nranks for the top) in
+// update mode `mode`, built on first use.
+spx_status ensure_part_items(spx_handle h, int k, int mode)
+{
+    spx_handle_s::Part &pt = h->parts[k];
+    if (pt.nitems[mode] >= 0) return SPX_OK;
+    const spx::Plan &P = h->plan;
+    const int owner = k < h->part_nranks ? k : -1;
+    std::vector<char> in_set(P.npanels, 0);
+    for (int32_t q = 0; q < P.npanels; ++q) in_set[q] = h->panel_owner[q] == owner;
+    std::vector<spx::FqItem> items;
+    std::vector<int32_t> need;
+    spx_status st = make_items(h, h->hc_chunks, h->hc_tiles, h->hc_small, h->hc_tct, h->h_pchunk, in_set, h->workers,
+                               mode, items, need);
+    if (st != SPX_OK) return st;
+    if ((st = upload(h, &pt.d_items[mode], items)) || (st = upload(h, &pt.d_need[mode], need))) return st;
+    pt.nitems[mode] = (int32_t)items.size();
+    return SPX_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1551,41 +1852,9 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     const bool fp64 = precision == SPX_FP64;
     const size_t elems = (size_t)P.pval[P.npanels];
     const size_t esz = fp64 ? sizeof(double) : sizeof(float);
-    if (h->factor_prec_alloc != (fp64 ? 1 : 0)) {
-        dfree(h, h->d_L);
-        dfree(h, h->d_U);
-        dfree(h, h->d_Dinv);
-        h->d_L = h->d_U = h->d_Dinv = nullptr;
-        h->factor_prec_alloc = -1;
-        char *pl = nullptr, *pd = nullptr;
-        if ((st = dalloc(h, &pl, elems * esz))) return st;
-        h->d_L = pl;
-        if ((st = dalloc(h, &pd, (size_t)h->dinv_elems * esz))) return st;
-        h->d_Dinv = pd;
-        dfree(h, h->d_W);
-        h->d_W = nullptr;
-        if (P.method == SPX_LDLT) {
-            char *pw = nullptr;
-            if ((st = dalloc(h, &pw, elems * esz))) return st;
-            h->d_W = pw;
-        }
-        if (P.method == SPX_LU) {
-            char *pu = nullptr;
-            if ((st = dalloc(h, &pu, elems * esz))) return st;
-            h->d_U = pu;
-        }
-        h->factor_prec_alloc = fp64 ? 1 : 0;
-        if (h->fgraph) {
-            cudaGraphExecDestroy(h->fgraph);
-            h->fgraph = nullptr;
-            h->fgraph_prec = -1;
-        }
-    }
+    if ((st = ensure_factor_storage(h, precision))) return st;
     h->factored = false;
     h->zready = false;
-    if (uses_tensor_cores(P.method, precision)) {
-        if ((st = ensure_operand_copy(h, operand_kind(P.method, precision)))) return st;
-    }
     fence_from(h, cuda_stream);
     if (values_on_device)
         CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a, cudaMemcpyDeviceToDevice, h->hs));
@@ -1668,6 +1937,129 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     }
     h->factored = true;
     return SPX_OK;
+}
+
+spx_status spx_partition(spx_handle h, int32_t nranks, int32_t *panel_owner, int64_t *part_values,
+                         int64_t *part_inverses)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (nranks < 1 || nranks > 4096) return fail(h, SPX_ERR_ARG, "nranks outside [1, 4096]");
+    const spx::Plan &P = h->plan;
+    if (P.method == SPX_LU) return fail(h, SPX_ERR_ARG, "the partitioned factorization takes Cholesky or LDL^T");
+    for (int32_t q = 0; q < P.npanels; ++q)
+        if (P.pw[q] > 64) return fail(h, SPX_ERR_ARG, "the partitioned factorization takes panels at most 64 wide");
+    spx_status st = make_partition(h, nranks);
+    if (st != SPX_OK) return st;
+    if (panel_owner) std::memcpy(panel_owner, h->panel_owner.data(), sizeof(int32_t) * (size_t)P.npanels);
+    for (int k = 0; k <= nranks; ++k) {
+        if (part_values) part_values[k] = h->parts[k].nval;
+        if (part_inverses) part_inverses[k] = h->parts[k].ninv;
+    }
+    return SPX_OK;
+}
+
+spx_status spx_factorize_part(spx_handle h, const double *values, int values_on_device, spx_precision precision,
+                              int32_t part, void *cuda_stream)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (h->part_nranks < 1) return fail(h, SPX_ERR_STATE, "spx_factorize_part before spx_partition");
+    if (part < -1 || part >= h->part_nranks) return fail(h, SPX_ERR_ARG, "part outside [-1, nranks)");
+    if (precision < SPX_FP64 || precision > SPX_BF16) return fail(h, SPX_ERR_ARG, "unknown precision");
+    const spx::Plan &P = h->plan;
+    const bool fp64 = precision == SPX_FP64;
+    spx_status st = ensure_part_device(h);
+    if (st != SPX_OK) return st;
+    if (part >= 0) {
+        if (!values && P.nnz_a > 0) return fail(h, SPX_ERR_ARG, "values is NULL");
+        if ((st = ensure_factor_storage(h, precision))) return st;
+    } else if (h->factor_prec_alloc != (fp64 ? 1 : 0) || h->part_done != 1) {
+        return fail(h, SPX_ERR_STATE, "the top part needs this handle's own subtrees factored first (same precision)");
+    }
+    const bool tc = uses_tensor_cores(P.method, precision) && !fp64;
+    if ((st = ensure_part_items(h, part >= 0 ? part : h->part_nranks, tc ? 1 : 0))) return st;
+    h->factored = false;
+    h->zready = false;
+    fence_from(h, cuda_stream);
+    if (part >= 0) {
+        if (values_on_device)
+            CU(cudaMemcpyAsync(h->d_vals, values, sizeof(double) * (size_t)P.nnz_a, cudaMemcpyDeviceToDevice, h->hs));
+        else if ((st = staged_h2d(h, h->d_vals, values, 0, sizeof(double) * (size_t)P.nnz_a, 1)))
+            return st;
+    }
+    Marks mk{h, false};
+    CU(cudaEventRecord(h->ev_t0, h->hs));
+    if (fp64) enqueue_factorization<double>(h, false, mk, (int)precision, part);
+    else enqueue_factorization<float>(h, true, mk, (int)precision, part);
+    CU(cudaGetLastError());
+    CU(cudaEventRecord(h->ev_t1, h->hs));
+    int64_t bad = 0;
+    unsigned long long nrepl = 0, abits = 0, nneg = 0;
+    int fqerr = 0;
+    CU(cudaMemcpyAsync(&bad, h->d_err, sizeof(bad), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&nrepl, h->d_nrepl, sizeof(nrepl), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&abits, h->d_anorm, sizeof(abits), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&nneg, h->d_nneg, sizeof(nneg), cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaMemcpyAsync(&fqerr, h->d_fq_state + 2 * (size_t)P.npanels + h->fq_nchunks + 1, sizeof(int),
+                       cudaMemcpyDeviceToHost, h->hs));
+    CU(cudaStreamSynchronize(h->hs));
+    h->part_done = part >= 0 ? 1 : 2;
+    if (fqerr)
+        return fail(h, SPX_ERR_TIMEOUT, fqerr == 2 ? "the factorization queue's tensor-core pipeline gave up waiting"
+                                                   : "the factorization queue gave up waiting on a task counter");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
+    std::memcpy(&h->anorm, &abits, 8);
+    h->info.factor_ms = ms;
+    h->info.precision = precision;
+    h->info.npivot_repl = (int64_t)nrepl;
+    h->info.npivot_neg = P.method == SPX_LDLT ? (int64_t)nneg : 0;
+    h->info.bad_col = (bad == LLONG_MAX) ? -1 : bad;
+    h->precision = precision;
+    if (bad != LLONG_MAX)
+        return fail(h, P.method == SPX_LLT ? SPX_ERR_NOT_SPD : SPX_ERR_ZERO_PIVOT,
+                    "pivot failure at permuted column " + std::to_string(bad));
+    h->factored = part < 0;
+    return SPX_OK;
+}
+
+// pack (get) or unpack (set) the values, and with_inverses the inverse blocks, of a part
+static spx_status part_copy(spx_handle h, int32_t part, int32_t with_inverses, void *buf, int dir, void *cuda_stream)
+{
+    if (!h) return fail(nullptr, SPX_ERR_ARG, "handle is NULL");
+    if (h->part_nranks < 1) return fail(h, SPX_ERR_STATE, "no partition");
+    if (part < -1 || part >= h->part_nranks) return fail(h, SPX_ERR_ARG, "part outside [-1, nranks)");
+    if (!buf) return fail(h, SPX_ERR_ARG, "buf is NULL");
+    if (h->factor_prec_alloc < 0) return fail(h, SPX_ERR_STATE, "no factor storage (factorize a part first)");
+    spx_status st = ensure_part_device(h);
+    if (st != SPX_OK) return st;
+    const spx_handle_s::Part &pt = h->parts[part >= 0 ? part : h->part_nranks];
+    fence_from(h, cuda_stream);
+    if (h->factor_prec_alloc == 1) {
+        spx::launch_pack_ranges<double>(pt.d_ranges, pt.nr, (double *)h->d_L, (double *)buf, dir, h->hs);
+        if (with_inverses)
+            spx::launch_pack_ranges<double>(pt.d_ranges + 3 * (size_t)pt.nr, pt.nr, (double *)h->d_Dinv, (double *)buf,
+                                            dir, h->hs);
+    } else {
+        spx::launch_pack_ranges<float>(pt.d_ranges, pt.nr, (float *)h->d_L, (float *)buf, dir, h->hs);
+        if (with_inverses)
+            spx::launch_pack_ranges<float>(pt.d_ranges + 3 * (size_t)pt.nr, pt.nr, (float *)h->d_Dinv, (float *)buf,
+                                           dir, h->hs);
+    }
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->hs));
+    return SPX_OK;
+}
+
+spx_status spx_part_get(spx_handle h, int32_t part, int32_t with_inverses, void *buf, void *cuda_stream)
+{
+    return part_copy(h, part, with_inverses, buf, 0, cuda_stream);
+}
+
+spx_status spx_part_set(spx_handle h, int32_t part, int32_t with_inverses, const void *buf, void *cuda_stream)
+{
+    spx_status st = part_copy(h, part, with_inverses, const_cast<void *>(buf), 1, cuda_stream);
+    if (st == SPX_OK && part >= 0 && h->part_done == 2) h->factored = true;
+    return st;
 }
 
 spx_status spx_solve(spx_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,

@@ -45,6 +45,32 @@ void launch_assemble(int64_t nnz, const double *vals, const int64_t *amap, T *L,
 }
 
 // ---------------------------------------------------------------------------
+// Packed copies of ranges of the panel storage (the parts of a subtree-to-rank
+// partition): ranges[3 r .. 3 r + 2] = (offset in the storage, length, offset
+// in the packed buffer).  mode 0: buf <- storage, 1: storage <- buf,
+// 2: storage <- 0.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void pack_ranges_kernel(const int64_t *__restrict__ ranges, int nr, T *store, T *buf, int mode)
+{
+    for (int r = blockIdx.x; r < nr; r += gridDim.x) {
+        const int64_t off = ranges[3 * r], len = ranges[3 * r + 1], pos = ranges[3 * r + 2];
+        for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
+            if (mode == 0) buf[pos + e] = store[off + e];
+            else if (mode == 1) store[off + e] = buf[pos + e];
+            else store[off + e] = (T)0;
+        }
+    }
+}
+
+template <typename T>
+void launch_pack_ranges(const int64_t *ranges, int nr, T *store, T *buf, int mode, cudaStream_t s)
+{
+    if (nr <= 0) return;
+    pack_ranges_kernel<T><<<nr < 152 * 8 ? nr : 152 * 8, 256, 0, s>>>(ranges, nr, store, buf, mode);
+}
+
+// ---------------------------------------------------------------------------
 // In-place inversion of a lower-triangular w x w block held in shared memory
 // (column-major, leading dimension w), read through element (i, j) at
 // a[trans ? j + i*w : i + j*w].  Columns are taken from the right:
@@ -545,6 +571,8 @@ void launch_update(const DevPlan &p, const DevTask *tasks, const UpdTile *tiles,
 }
 
 // explicit instantiations
+template void launch_pack_ranges<double>(const int64_t *, int, double *, double *, int, cudaStream_t);
+template void launch_pack_ranges<float>(const int64_t *, int, float *, float *, int, cudaStream_t);
 template void launch_assemble<double>(int64_t, const double *, const int64_t *, double *, double *, cudaStream_t);
 template void launch_assemble<float>(int64_t, const double *, const int64_t *, float *, float *, cudaStream_t);
 template void launch_potrf<double>(const DevPlan &, const int32_t *, int, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);

@@ -73,6 +73,10 @@ template <typename T>
 void launch_assemble(int64_t nnz, const double *vals, const int64_t *amap, T *L, T *U,
                      cudaStream_t s);
 
+// ranges[3 r ..]: (storage offset, length, packed offset); mode 0 pack, 1 unpack, 2 zero
+template <typename T>
+void launch_pack_ranges(const int64_t *ranges, int nr, T *store, T *buf, int mode, cudaStream_t s);
+
 template <typename T>
 void launch_potrf(const DevPlan &p, const int32_t *panels, int count, int wmax, int threads, T *L, T *Dinv,
                   const double *replace_tau, int64_t *err_col, unsigned long long *nrepl,

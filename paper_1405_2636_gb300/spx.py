@@ -36,6 +36,7 @@ EXPORTED = ["spx_default_options", "spx_default_refine", "spx_analyze", "spx_fac
             "spx_get_panels", "spx_solve_noalloc", "spx_set_wait_limit", "spx_roofline_model",
             "spx_update_create", "spx_update_stage", "spx_update_run", "spx_update_get_info",
             "spx_update_last_error", "spx_update_free",
+            "spx_partition", "spx_factorize_part", "spx_part_get", "spx_part_set",
             "spx_batch_analyze", "spx_batch_run", "spx_batch_tune", "spx_batch_set_config",
             "spx_batch_get_info", "spx_batch_system_info", "spx_batch_get_perm",
             "spx_batch_get_factor", "spx_batch_last_error", "spx_batch_free",
@@ -140,6 +141,10 @@ def load():
     lib.spx_free.argtypes = [_vp]
     lib.spx_free.restype = None
     lib.spx_set_wait_limit.argtypes = [_vp, _i64]
+    lib.spx_partition.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp]
+    lib.spx_factorize_part.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int32, _vp]
+    lib.spx_part_get.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+    lib.spx_part_set.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     lib.spx_roofline_model.argtypes = [_vp, ctypes.c_int, _vp, _vp]
     lib.spx_update_create.argtypes = [_i64, _i64, _i64, _i64, _i64, _vp, _vp, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
@@ -174,6 +179,7 @@ def load():
                  "spx_get_panels", "spx_solve_noalloc", "spx_set_wait_limit", "spx_roofline_model",
                  "spx_update_create",
                  "spx_update_stage", "spx_update_run", "spx_update_get_info",
+                 "spx_partition", "spx_factorize_part", "spx_part_get", "spx_part_set",
                  "spx_batch_analyze", "spx_batch_run",
                  "spx_batch_tune", "spx_batch_set_config", "spx_batch_get_info",
                  "spx_batch_system_info", "spx_batch_get_perm", "spx_batch_get_factor",
@@ -310,6 +316,44 @@ class Handle:
         out = np.zeros(len(KERNEL_CLASSES), dtype=np.float64)
         _check(load().spx_roofline_model(self._h, PRECISIONS[precision], _ptr(peaks), _ptr(out)), self._h)
         return {c: float(out[i]) for i, c in enumerate(KERNEL_CLASSES)}
+
+    # -- subtree-to-rank distribution with fan-in --------------------------------
+    def partition(self, nranks: int) -> dict:
+        """spx_partition: owner rank of every panel (-1: the top, factored by
+        rank 0 after the fan-in) and the packed sizes of every part (index
+        nranks: the top)."""
+        npn = self.info()["npanels"]
+        owner = np.empty(npn, np.int32)
+        vals = np.empty(nranks + 1, np.int64)
+        invs = np.empty(nranks + 1, np.int64)
+        _check(load().spx_partition(self._h, nranks, _ptr(owner), _ptr(vals), _ptr(invs)), self._h)
+        self._part = {"nranks": nranks, "owner": owner, "values": vals, "inverses": invs}
+        return self._part
+
+    def factorize_part(self, values, precision="fp64", part=0, stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if values is not None and not _is_device(values):
+            values = np.ascontiguousarray(values, dtype=np.float64)
+        on_dev = 1 if (values is not None and _is_device(values)) else 0
+        _check(load().spx_factorize_part(self._h, _ptr(values), on_dev, prec, int(part), _stream_ptr(stream)),
+               self._h)
+
+    def part_get(self, part: int, with_inverses: bool = False, out=None, stream=None):
+        """Packed panel values (then inverse blocks) of a part as a CUDA tensor
+        of the factor's type."""
+        import torch
+        k = part if part >= 0 else self._part["nranks"]
+        n = int(self._part["values"][k] + (self._part["inverses"][k] if with_inverses else 0))
+        if out is None:
+            dt = torch.float64 if self.info()["precision"] == SPX_FP64 else torch.float32
+            out = torch.empty(max(n, 1), dtype=dt, device="cuda")
+        _check(load().spx_part_get(self._h, int(part), 1 if with_inverses else 0, _ptr(out), _stream_ptr(stream)),
+               self._h)
+        return out
+
+    def part_set(self, part: int, buf, with_inverses: bool = False, stream=None):
+        _check(load().spx_part_set(self._h, int(part), 1 if with_inverses else 0, _ptr(buf), _stream_ptr(stream)),
+               self._h)
 
     def set_wait_limit(self, polls: int = 0):
         """Polls (~256 ns each) before a sweep wait gives up; 0 = default."""
