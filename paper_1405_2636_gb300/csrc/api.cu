@@ -34,7 +34,11 @@ struct spx_handle_s {
     bool uploaded = false;
     int device = -1;
     cudaStream_t hs = nullptr;
+    cudaStream_t aux[2] = {nullptr, nullptr};   // side branches of the captured factorization graph
     cudaEvent_t ev_fence = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    cudaStream_t fstream[2] = {nullptr, nullptr};   // far update tiles of alternate levels (look-ahead)
+    cudaEvent_t ev_trsm = nullptr, ev_far[2] = {nullptr, nullptr};
     std::vector<void *> allocs;
 
     spx::DevPlan dp{};
@@ -112,6 +116,10 @@ struct spx_handle_s {
     std::vector<int32_t> det_rounds;   // per level
     std::vector<int64_t> det_base;     // per level, into det_ptr[*]
     std::vector<int64_t> det_ptr[7];   // segments: SIMT wide, SIMT narrow, U^T wide, U^T narrow, tc, tc-small wide, tc-small narrow
+    // look-ahead: outside the deterministic mode each level's tile segments
+    // list the tiles into the next level's panels ("near") first;
+    // near_end[s][l] is where segment s's "far" tiles of level l begin
+    std::vector<int64_t> near_end[7];
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
     int kpad = 0;                     // operand-copy row length
@@ -560,6 +568,16 @@ spx_status ensure_device(spx_handle h)
                         std::to_string(prop.major * 10 + prop.minor));
     h->device = dev;
     CU(cudaStreamCreateWithFlags(&h->hs, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        CU(cudaStreamCreateWithFlags(&h->aux[k], cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming));
+    }
+    CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&h->ev_trsm, cudaEventDisableTiming));
+    for (int k = 0; k < 2; ++k) {
+        CU(cudaStreamCreateWithFlags(&h->fstream[k], cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&h->ev_far[k], cudaEventDisableTiming));
+    }
     CU(cudaEventCreateWithFlags(&h->ev_fence, cudaEventDisableTiming));
     CU(cudaEventCreate(&h->ev_t0));
     CU(cudaEventCreate(&h->ev_t1));
@@ -683,21 +701,34 @@ spx_status ensure_device(spx_handle h)
         h->det_rounds[l] = R;
         h->det_base[l + 1] = h->det_base[l] + R + 1;
     }
-    auto sort_segment = [&](std::vector<UpdTile> &v, int64_t a, int64_t b, int32_t l, std::vector<int64_t> &ptr) {
-        std::stable_sort(v.begin() + a, v.begin() + b, [&](const UpdTile &x, const UpdTile &y) {
-            return task_round[x.task] < task_round[y.task];
-        });
-        int64_t i = a;
-        for (int32_t r = 0; r <= h->det_rounds[l]; ++r) {
-            while (i < b && task_round[v[i].task] < r) ++i;
-            ptr.push_back(i);
+    // deterministic mode: sorted by round, with the round boundaries; else
+    // the near tiles (targets at level l + 1) first, with where they end
+    auto sort_segment = [&](std::vector<UpdTile> &v, int64_t a, int64_t b, int32_t l, std::vector<int64_t> &ptr,
+                            std::vector<int64_t> &near) {
+        auto is_far = [&](const UpdTile &x) { return P.plevel[P.tasks[x.task].tgt] != l + 1; };
+        if (h->deterministic) {
+            std::stable_sort(v.begin() + a, v.begin() + b, [&](const UpdTile &x, const UpdTile &y) {
+                return task_round[x.task] < task_round[y.task];
+            });
+            int64_t i = a;
+            for (int32_t r = 0; r <= h->det_rounds[l]; ++r) {
+                while (i < b && task_round[v[i].task] < r) ++i;
+                ptr.push_back(i);
+            }
+            near.push_back(b);
+        } else {
+            std::stable_partition(v.begin() + a, v.begin() + b, [&](const UpdTile &x) { return !is_far(x); });
+            int64_t i = a;
+            while (i < b && !is_far(v[i])) ++i;
+            near.push_back(i);
+            for (int32_t r = 0; r <= h->det_rounds[l]; ++r) ptr.push_back(r == 0 ? a : b);
         }
     };
     for (int32_t l = 0; l < P.nlevels; ++l) {
-        sort_segment(tiles, h->tile_ptr[l], h->tile_nar[l], l, h->det_ptr[0]);
-        sort_segment(tiles, h->tile_nar[l], h->tile_ptr[l + 1], l, h->det_ptr[1]);
-        sort_segment(tilesu, h->tileu_ptr[l], h->tileu_nar[l], l, h->det_ptr[2]);
-        sort_segment(tilesu, h->tileu_nar[l], h->tileu_ptr[l + 1], l, h->det_ptr[3]);
+        sort_segment(tiles, h->tile_ptr[l], h->tile_nar[l], l, h->det_ptr[0], h->near_end[0]);
+        sort_segment(tiles, h->tile_nar[l], h->tile_ptr[l + 1], l, h->det_ptr[1], h->near_end[1]);
+        sort_segment(tilesu, h->tileu_ptr[l], h->tileu_nar[l], l, h->det_ptr[2], h->near_end[2]);
+        sort_segment(tilesu, h->tileu_nar[l], h->tileu_ptr[l + 1], l, h->det_ptr[3], h->near_end[3]);
     }
     if ((st = upload(h, &h->d_chunks, chunks)) || (st = upload(h, &h->d_tiles, tiles)) ||
         (st = upload(h, &h->d_tilesu, tilesu)))
@@ -824,13 +855,14 @@ spx_status ensure_device(spx_handle h)
             tmp.reserve((size_t)(h->tctile_ptr[l + 1] - h->tctile_ptr[l]));
             for (int64_t i = h->tctile_ptr[l]; i < h->tctile_ptr[l + 1]; ++i)
                 tmp.push_back(UpdTile{tct[i].task, tct[i].m0, tct[i].n0, 0});
-            std::vector<int64_t> ptr;
-            sort_segment(tmp, 0, (int64_t)tmp.size(), l, ptr);
+            std::vector<int64_t> ptr, nr;
+            sort_segment(tmp, 0, (int64_t)tmp.size(), l, ptr, nr);
             for (size_t i = 0; i < tmp.size(); ++i)
                 tct[h->tctile_ptr[l] + i] = spx::TcTile{tmp[i].task, tmp[i].m0, tmp[i].n0, 0};
             for (int64_t v : ptr) h->det_ptr[4].push_back(v + h->tctile_ptr[l]);
-            sort_segment(small, h->tcsmall_ptr[l], h->tcsmall_nar[l], l, h->det_ptr[5]);
-            sort_segment(small, h->tcsmall_nar[l], h->tcsmall_ptr[l + 1], l, h->det_ptr[6]);
+            h->near_end[4].push_back(nr[0] + h->tctile_ptr[l]);
+            sort_segment(small, h->tcsmall_ptr[l], h->tcsmall_nar[l], l, h->det_ptr[5], h->near_end[5]);
+            sort_segment(small, h->tcsmall_nar[l], h->tcsmall_ptr[l + 1], l, h->det_ptr[6], h->near_end[6]);
         }
         if ((st = upload(h, &h->d_tcsmall, small)) || (st = upload(h, &h->d_tctiles, tct)))
             return st;
@@ -898,6 +930,39 @@ int operand_kind(int method, int prec)
     if (method == SPX_LDLT) return prec == SPX_BF16 ? 4 : 3;
     return prec == SPX_BF16 ? 1 : (prec == SPX_FP32 ? 2 : 0);
 }
+
+// Independent launches of one level (the diagonal blocks of different width
+// classes; the CUDA-core and tensor-core update tiles, which only meet in
+// atomic reductions) go on parallel branches of the captured graph: launch
+// k of a group runs on the main stream (k = 0) or on side stream k - 1 after
+// a fork, and the group ends with a join.  Off (one stream) when profiling,
+// so that the per-class events stay meaningful, and for the deterministic
+// rounds, whose order the launch order is.
+struct Branches {
+    spx_handle h;
+    bool on;
+    bool forked[2] = {false, false};
+    cudaStream_t pick(int k)
+    {
+        if (!on || k == 0) return h->hs;
+        const int a = (k - 1) % 2;
+        if (!forked[a]) {
+            if (!forked[0] && !forked[1]) cudaEventRecord(h->ev_fork, h->hs);
+            cudaStreamWaitEvent(h->aux[a], h->ev_fork, 0);
+            forked[a] = true;
+        }
+        return h->aux[a];
+    }
+    void join()
+    {
+        for (int a = 0; a < 2; ++a)
+            if (forked[a]) {
+                cudaEventRecord(h->ev_join[a], h->aux[a]);
+                cudaStreamWaitEvent(h->hs, h->ev_join[a], 0);
+                forked[a] = false;
+            }
+    }
+};
 
 // One launch of the task queue over the item list of a partition part (rank
 // r >= 0, or -1 for the top panels); the lists were built by ensure_part_items.
@@ -976,7 +1041,17 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
         return;
     }
     const int32_t qlev = queue_level(h, prec);
+    // look-ahead (graph runs outside the deterministic mode): a level's far
+    // update tiles (targets two or more levels up) run on a side stream
+    // beside the next level's diagonal blocks, TRSM and near tiles, and are
+    // joined before the diagonal blocks of level l + 2
+    const bool lookahead = !mk.on && !h->deterministic && !lu;
+    bool far_pending[2] = {false, false};
     for (int32_t l = 0; l < qlev; ++l) {
+        if (far_pending[l % 2]) {   // the far tiles of level l - 2
+            cudaStreamWaitEvent(s, h->ev_far[l % 2], 0);
+            far_pending[l % 2] = false;
+        }
         const int32_t *panels = h->d_level_panels + P.level_ptr[l];
         const int np = P.level_ptr[l + 1] - P.level_ptr[l];
         const RowChunk *ch = h->d_chunks + h->chunk_ptr[l];
@@ -986,23 +1061,27 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
         const UpdTile *tln = h->d_tiles + h->tile_nar[l];
         const int ntln = (int)(h->tile_ptr[l + 1] - h->tile_nar[l]);
         const int wmax = h->lvl_wmax[l];
+        Branches br{h, !mk.on};
+        int nlaunch = 0;
         for (int c = 0; c < kNumClasses; ++c) {
             const int32_t a = h->cls_ptr[(size_t)l * kNumClasses + c];
             const int32_t b = h->cls_ptr[(size_t)l * kNumClasses + c + 1];
             if (b <= a) continue;
             const int cw = std::min(kClassWidth[c], wmax);
+            const cudaStream_t sc = br.pick(nlaunch++);
             if (ldlt)
                 spx::launch_ldlt_diag<T>(h->dp, h->d_level_panels + a, b - a, cw, L, Dinv, h->d_tau, h->d_err,
-                                         h->d_nrepl, h->d_nneg, s);
+                                         h->d_nrepl, h->d_nneg, sc);
             else if (!lu)
                 spx::launch_potrf<T>(h->dp, h->d_level_panels + a, b - a, cw, kClassThreads[c], L,
-                                     Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
+                                     Dinv, h->d_tau, h->d_err, h->d_nrepl, sc);
             else
                 spx::launch_getrf<T>(h->dp, h->d_level_panels + a, b - a, cw, kClassThreads[c], L,
-                                     Dinv, h->d_tau, h->d_err, h->d_nrepl, s);
+                                     Dinv, h->d_tau, h->d_err, h->d_nrepl, sc);
             cnt += 1;
             h->class_launches[SPX_K_DIAG] += 1;
         }
+        br.join();
         (void)panels;
         (void)np;
         mk.mark(SPX_K_DIAG);
@@ -1033,28 +1112,63 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
             h->class_launches[SPX_K_TRSM] += nch > 0;
             mk.mark(SPX_K_TRSM);
             const T *Bop = ldlt ? W : L;   // LDL^T: C -= L (D L^T)
-            for (int r = 0; r < nround; ++r) {
+            // one set of update launches over tile ranges: wide and narrow
+            // CUDA-core tiles, and the tensor-core tiles in tc modes
+            auto launch_set = [&](int64_t a0, int64_t a1, int64_t b0, int64_t b1, int64_t c0, int64_t c1,
+                                  Branches &ub, cudaStream_t one) {
+                const int na = (int)(a1 - a0), nb = (int)(b1 - b0), nc = (int)(c1 - c0);
+                auto st = [&](int k) { return one ? one : ub.pick(k); };
                 if (!tc) {
-                    const int a = seg(0, h->tile_ptr[l], h->tile_nar[l], r, &o);
-                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + o, a, L, Bop, L, 1, 0, s, 0);
-                    const int b = seg(1, h->tile_nar[l], h->tile_ptr[l + 1], r, &o);
-                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + o, b, L, Bop, L, 1, 0, s, 1);
-                    cnt += (a > 0) + (b > 0);
-                    h->class_launches[SPX_K_UPDATE] += (a > 0) + (b > 0);
-                    mk.mark(SPX_K_UPDATE);
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + a0, na, L, Bop, L, 1, 0, st(0), 0);
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tiles + b0, nb, L, Bop, L, 1, 0,
+                                          st(na > 0 ? 1 : 0), 1);
                 } else {
-                    const int a = seg(5, h->tcsmall_ptr[l], h->tcsmall_nar[l], r, &o);
-                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tcsmall + o, a, L, Bop, L, 1, 0, s, 0);
-                    const int b = seg(6, h->tcsmall_nar[l], h->tcsmall_ptr[l + 1], r, &o);
-                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tcsmall + o, b, L, Bop, L, 1, 0, s, 1);
-                    mk.mark(SPX_K_UPDATE);
-                    const int c = seg(4, h->tctile_ptr[l], h->tctile_ptr[l + 1], r, &o);
-                    spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, h->d_tctiles + o, c,
-                                          (float *)L, 1, h->d_tcerr, s);
+                    // the tensor-core tiles on the main stream, the CUDA-core ones beside them
+                    spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, h->d_tctiles + c0, nc,
+                                          (float *)L, 1, h->d_tcerr, st(0));
                     mk.mark(SPX_K_UPDATE_TC);
-                    cnt += (a > 0) + (b > 0) + (c > 0);
-                    h->class_launches[SPX_K_UPDATE] += (a > 0) + (b > 0);
-                    h->class_launches[SPX_K_UPDATE_TC] += c > 0;
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tcsmall + a0, na, L, Bop, L, 1, 0,
+                                          st(nc > 0 ? 1 : 0), 0);
+                    spx::launch_update<T>(h->dp, h->d_tasks, h->d_tcsmall + b0, nb, L, Bop, L, 1, 0,
+                                          st((nc > 0) + (na > 0)), 1);
+                }
+                cnt += (na > 0) + (nb > 0) + (nc > 0);
+                h->class_launches[SPX_K_UPDATE] += (na > 0) + (nb > 0);
+                h->class_launches[SPX_K_UPDATE_TC] += nc > 0;
+            };
+            // segment ranges of this level: wide, narrow (CUDA cores), tensor cores
+            const int sa = tc ? 5 : 0, sb = tc ? 6 : 1;
+            const int64_t A0 = tc ? h->tcsmall_ptr[l] : h->tile_ptr[l], A1 = tc ? h->tcsmall_nar[l] : h->tile_nar[l];
+            const int64_t B0 = A1, B1 = tc ? h->tcsmall_ptr[l + 1] : h->tile_ptr[l + 1];
+            const int64_t C0 = tc ? h->tctile_ptr[l] : 0, C1 = tc ? h->tctile_ptr[l + 1] : 0;
+            if (h->deterministic) {
+                for (int r = 0; r < nround; ++r) {
+                    int64_t oa, ob, oc = 0;
+                    const int na = seg(sa, A0, A1, r, &oa), nb = seg(sb, B0, B1, r, &ob);
+                    const int nc = tc ? seg(4, C0, C1, r, &oc) : 0;
+                    Branches ub{h, false};
+                    launch_set(oa, oa + na, ob, ob + nb, oc, oc + nc, ub, nullptr);
+                    mk.mark(SPX_K_UPDATE);
+                }
+            } else if (!lookahead) {
+                Branches ub{h, !mk.on};
+                launch_set(A0, A1, B0, B1, C0, C1, ub, nullptr);
+                ub.join();
+                mk.mark(SPX_K_UPDATE);
+            } else {
+                const int64_t An = h->near_end[sa][l], Bn = h->near_end[sb][l], Cn = tc ? h->near_end[4][l] : 0;
+                const bool far = An < A1 || Bn < B1 || Cn < C1;
+                if (far) cudaEventRecord(h->ev_trsm, s);   // this level's TRSM is done
+                Branches ub{h, true};
+                launch_set(A0, An, B0, Bn, C0, Cn, ub, nullptr);
+                ub.join();
+                if (far) {
+                    cudaStream_t fs = h->fstream[l % 2];
+                    cudaStreamWaitEvent(fs, h->ev_trsm, 0);
+                    Branches none{h, false};
+                    launch_set(An, A1, Bn, B1, Cn, C1, none, fs);
+                    cudaEventRecord(h->ev_far[l % 2], fs);
+                    far_pending[l % 2] = true;
                 }
             }
         } else {
@@ -1078,6 +1192,8 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
             }
         }
     }
+    for (int k = 0; k < 2; ++k)
+        if (far_pending[k]) cudaStreamWaitEvent(s, h->ev_far[k], 0);
     if (qlev < P.nlevels) {
         // the upper levels: one persistent launch over the task queue
         const int mode = tc ? 1 : 0;
@@ -2541,6 +2657,16 @@ void spx_free(spx_handle h)
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
     if (h->hs) cudaStreamDestroy(h->hs);
+    for (int k = 0; k < 2; ++k) {
+        if (h->aux[k]) cudaStreamDestroy(h->aux[k]);
+        if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_trsm) cudaEventDestroy(h->ev_trsm);
+    for (int k = 0; k < 2; ++k) {
+        if (h->fstream[k]) cudaStreamDestroy(h->fstream[k]);
+        if (h->ev_far[k]) cudaEventDestroy(h->ev_far[k]);
+    }
     if (h->h_noalloc_err) cudaFreeHost(h->h_noalloc_err);
     for (int b = 0; b < 2; ++b) {
         if (h->h_stage[b]) cudaFreeHost(h->h_stage[b]);
