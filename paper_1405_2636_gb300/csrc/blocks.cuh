@@ -11,6 +11,8 @@
 #include "kernels.cuh"
 #include "operand.cuh"
 
+#include <type_traits>
+
 namespace spx {
 
 // ---------------------------------------------------------------------------
@@ -87,6 +89,73 @@ __device__ __forceinline__ void sqrt_rsqrt(double d, double *s, double *rs)
 
 __device__ __forceinline__ float rcp_newton(float d) { return 1.0f / d; }
 
+// 1/d for a pivot on the diagonal-block chain, three dependent FP64
+// operations: the seed y0 is the approximate FP32 reciprocal (rcp.approx,
+// relative error below 2^-23) of d's leading bits, cut with integer
+// operations, so |1 - d y0| < 2^-22; one third-order Newton-Raphson step
+// y = y0 (1 + e + e^2), e = 1 - d y0, leaves the error e^3 < 2^-66, below
+// FP64 rounding.  Magnitudes outside [2^-125, 2^126) take IEEE division.
+__device__ __forceinline__ double rcp_pivot(double d)
+{
+    const long long b = __double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < -125 || e > 125) return 1.0 / d;
+    const unsigned fb = (unsigned)((b >> 32) & 0x80000000u) | ((unsigned)(e + 127) << 23) |
+                        (unsigned)((b >> 29) & 0x7FFFFF);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float(fb)));
+    const double y0 = widen(yf);
+    const double er = fma(-d, y0, 1.0);
+    const double t = fma(er, er, er);
+    return fma(y0, t, y0);
+}
+
+// FP64 <-> FP32 conversions with integer operations (the conversion
+// instructions occupy the FP64 pipe): round to nearest even, with zeros and
+// the FP32 normal range handled inline and anything else (subnormal,
+// overflow, inf, NaN) through the conversion instruction.
+__device__ __forceinline__ float narrow_rn(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    if (((hi & 0x7FFFFFFFu) | lo) == 0u) return __uint_as_float(sign);
+    const int fe = (int)((hi >> 20) & 0x7FF) - 896;
+    if (fe < 1 || fe > 254) return __double2float_rn(d);
+    unsigned f = sign | ((unsigned)fe << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;   // the 29 dropped bits: round half to even
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+}
+
+__device__ __forceinline__ double widen_exact(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    if ((u << 1) == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 255u) return (double)f;
+    return widen(f);
+}
+
+template <typename T> __device__ __forceinline__ T from_f64(double d) { return (T)d; }
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return narrow_rn(d); }
+template <typename T> __device__ __forceinline__ double to_f64(T v) { return (double)v; }
+template <> __device__ __forceinline__ double to_f64<float>(float v) { return widen_exact(v); }
+
+// d > 0 on the bit pattern (an integer compare instead of an FP64 one)
+__device__ __forceinline__ bool pos_bits(long long db) { return db > 0 && db <= 0x7FF0000000000000LL; }
+
+// D = A B + D on the FP64 tensor path (mma m8n8k4): A(r, k) at lane 4r + k,
+// B(k, n) at lane 4n + k, D(r, 2q + {0, 1}) at lane 4r + q.  It shares the
+// SM's FP64 datapath, so it is used only in phases where no FP64 chain runs
+// beside it.
+__device__ __forceinline__ void dmma_f64(double &d0, double &d1, double a, double b)
+{
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(d0), "+d"(d1)
+                 : "d"(a), "d"(b));
+}
+
 constexpr int kDB = 8;
 
 __device__ __forceinline__ double shfl_d(double v, int src)
@@ -96,17 +165,23 @@ __device__ __forceinline__ double shfl_d(double v, int src)
 
 // ---------------------------------------------------------------------------
 // Diagonal block of width <= W (W = 16, 32, 64; the block is padded with the
-// identity to W).  A dependent FP64 operation costs ~64 cycles on this part,
-// so the column chain is kept short:
-//  * the factorization runs in LDL^T form in FP64 -- per column one Newton
-//    reciprocal of the pivot, the multipliers, and the in-block updates,
-//    with no square root on the chain; warps 0 and 1 own each 8-column
-//    block panel in registers (rows 0-31 and 32-63 of the block; each warp
-//    runs the pivot chain itself), the other warps apply the trailing updates;
+// identity to W).  On this part a warp issues one FP64 instruction per ~64
+// cycles and the SM as a whole one per ~19 (conversions included), so the
+// FP64 work is counted in instructions:
+//  * the factorization runs in LDL^T form in FP64 -- per column one
+//    reciprocal of the pivot (three FP64 operations), the multipliers, and
+//    the in-block updates, with no square root on the chain; warps 0 and 1
+//    own each 8-column block panel in registers (rows 0-31 and 32-63 of the
+//    block; each warp runs the pivot chain itself), the other warps apply
+//    the trailing updates; the next block's columns are updated between the
+//    panels (on the FP64 tensor path for W = 64, where nothing else runs);
+//  * pivot tests and FP64 <-> FP32 conversions on the bit patterns;
 //  * L = l diag(sqrt(d)) is formed afterwards, all columns in parallel;
-//  * L^{-1} = diag(1/sqrt(d)) l^{-1}: the unit-lower l is inverted by blocks
-//    (8 x 8 diagonal blocks by single lanes, then pairs of blocks merged with
-//    X21 = -C^{-1} (B A^{-1})), in the factor's arithmetic.
+//  * L^{-1} = diag(1/sqrt(d)) l^{-1}: FP32 factors invert the unit-lower l
+//    by forward substitution in registers (warp v owns columns v, v + 8, ...);
+//    FP64 factors by blocks (8 x 8 diagonal blocks by single lanes, then
+//    pairs of blocks merged with X21 = -C^{-1} (B A^{-1})), which does a
+//    sixth of the multiply-adds.
 // ---------------------------------------------------------------------------
 template <typename T, int W, bool ldlt>
 __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__restrict__ L,
@@ -120,7 +195,9 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
     double *dv = lA + 2 * W * kDB;           // pivots
     double *rsv = dv + W;                    // 1 / sqrt(pivot)
     T *x = reinterpret_cast<T *>(rsv + W);   // W x LD inverse workspace
-    T *tmp = x + W * LD;                     // (W/2)^2
+    T *tmp = x + W * LD;                     // (W/2)^2, the FP64 factors' inverse
+    T *dvf = tmp + (W / 2) * (W / 2);        // pivots (Cholesky: their square roots) in T
+    T *rvf = dvf + W;                        // and their reciprocals
     const int w = p.pw[pid], h = p.ph[pid];
     const int64_t col0 = p.pfcol[pid];
     T *D = L + p.pval[pid];
@@ -142,7 +219,7 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
             const int idx = tid + q * NT;
             if (idx >= W * W) continue;
             const int i = idx % W, j = idx / W;
-            a[i + j * LD] = (i < w && j < w) ? (double)vv[q] : (i == j ? 1.0 : 0.0);
+            a[i + j * LD] = (i < w && j < w) ? to_f64<T>(vv[q]) : (i == j ? 1.0 : 0.0);
         }
     }
     __syncthreads();
@@ -160,6 +237,8 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
     // and the two warps never wait for each other.  Multipliers go to a, the
     // unscaled block columns to lA (two buffers, one per block parity, so
     // that the next panel can overlap the trailing update of the previous).
+    const bool tau_pos = replace_tau > 0.0;
+    const long long tau_bits = tau_pos ? __double_as_longlong(replace_tau) : 0;
     auto panel = [&](int kb, int role) {
         double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
         const int rq = role == 0 ? kb + lane : kb + (lane & 7);   // rows of the pivot chain
@@ -175,25 +254,28 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
             const int k = kb + c;
             double d = shfl_d(q[c], c);                  // A(k, k) from lane c
             const bool report = role == 0 && lane == 0 && k < w;
+            const long long db = __double_as_longlong(d);
             if constexpr (!ldlt) {                        // Cholesky: positive pivots
-                if (!(d > 0.0)) {
+                if (!pos_bits(db)) {
                     if (report) {
-                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                        if (tau_pos) atomicAdd(nrepl, 1ull);
                         else atomicMin((long long *)err_col, (long long)(col0 + k));
                     }
-                    d = replace_tau > 0.0 ? replace_tau : 1.0;
+                    d = tau_pos ? replace_tau : 1.0;
                 }
             } else {                                      // LDL^T: static pivoting
-                if (!(fabs(d) >= replace_tau) || (replace_tau <= 0.0 && d == 0.0)) {
+                const long long ab = db & 0x7FFFFFFFFFFFFFFFLL;   // |d| >= tau on the bits
+                if (!(ab >= tau_bits && ab <= 0x7FF0000000000000LL) || (!tau_pos && ab == 0)) {
                     if (report) {
-                        if (replace_tau > 0.0) atomicAdd(nrepl, 1ull);
+                        if (tau_pos) atomicAdd(nrepl, 1ull);
                         else atomicMin((long long *)err_col, (long long)(col0 + k));
                     }
-                    d = replace_tau > 0.0 ? (d < 0.0 ? -replace_tau : replace_tau) : 1.0;
+                    d = tau_pos ? ((db < 0 && ab != 0 && ab <= 0x7FF0000000000000LL) ? -replace_tau : replace_tau)
+                                : 1.0;
                 }
-                if (report && d < 0.0) atomicAdd(nneg, 1ull);
+                if (report && __double_as_longlong(d) < 0) atomicAdd(nneg, 1ull);
             }
-            const double r = 1.0 / d;   // measured faster here than the Newton form
+            const double r = rcp_pivot(d);
             const double u0 = rq > k ? q[c] : 0.0;
             const double l0 = u0 * r;
 #pragma unroll
@@ -251,8 +333,26 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
     for (int kb = 0; kb < W; kb += kDB) {
         const int nb = kb + kDB;                 // next block
         if (nb < W) {
-            // columns of the next block first, by every thread
-            update(kb, nb, nb + kDB, tid, NT);
+            // columns of the next block first: W = 64 on the FP64 tensor path,
+            // one 8-row tile per warp with the block's 8 columns split in two
+            // k halves on independent accumulators; narrower blocks by every
+            // thread on the FP64 pipe (measured faster there)
+            if constexpr (W == 64) {
+                if (warp < (W - nb) / 8) {
+                    const int i0 = nb + 8 * warp, r = lane >> 2, q4 = lane & 3;
+                    const double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
+                    double *c = a + (i0 + r) + (nb + 2 * q4) * LD;
+                    double c0 = c[0], c1 = c[LD], e0 = 0.0, e1 = 0.0;
+                    const double a0 = -a[(i0 + r) + (kb + q4) * LD], a1 = -a[(i0 + r) + (kb + 4 + q4) * LD];
+                    const double b0 = lAb[(nb + r) + q4 * W], b1 = lAb[(nb + r) + (4 + q4) * W];
+                    dmma_f64(c0, c1, a0, b0);
+                    dmma_f64(e0, e1, a1, b1);
+                    c[0] = c0 + e0;
+                    c[LD] = c1 + e1;
+                }
+            } else {
+                update(kb, nb, nb + kDB, tid, NT);
+            }
             __syncthreads();
             // warps 0 (and 1) factor the next block while the others finish
             // this block's update
@@ -275,63 +375,116 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
             dv[tid] = sq;
             rsv[tid] = rs;
         }
+        dvf[tid] = from_f64<T>(dv[tid]);
+        rvf[tid] = from_f64<T>(rsv[tid]);
     }
     __syncthreads();
     for (int idx = tid; idx < W * W; idx += NT) {
         const int i = idx % W, j = idx / W;
-        const T l = (T)a[i + j * LD];
+        const T l = i > j ? from_f64<T>(a[i + j * LD]) : (T)0;
         if (i < w && j < w && i >= j)
-            D[i + (int64_t)j * h] = i == j ? (T)dv[j] : (ldlt ? l : l * (T)dv[j]);
+            D[i + (int64_t)j * h] = i == j ? dvf[j] : (ldlt ? l : l * dvf[j]);
         x[i + j * LD] = i > j ? l : (i == j ? (T)1 : (T)0);
     }
     __syncthreads();
 
-    // unit-lower inverse: 8 x 8 diagonal blocks first
-    if (warp < W / kDB && lane < kDB) {
-        const int o = warp * kDB, jj = lane;
-        T xr[kDB];
+    T *Mi = Dinv + p.pinv[pid];
+    if constexpr (std::is_same<T, float>::value) {
+        // forward substitution in registers: warp v owns columns v, v + 8, ...
+        // of X = l^{-1}, W / 32 rows per lane; at step k the lane holding row
+        // k broadcasts x_k and every lane subtracts l(i, k) x_k.  The k loop
+        // is split at the row-group boundary so that the broadcast reads a
+        // fixed register.
+        constexpr int CPW = W / 8;
+        constexpr int RG = (W + 31) / 32;
+        T xr[CPW][RG];
 #pragma unroll
-        for (int q = 0; q < kDB; ++q) xr[q] = q == jj ? (T)1 : (T)0;
+        for (int t = 0; t < CPW; ++t)
 #pragma unroll
-        for (int kk = 0; kk < kDB; ++kk) {
-            if (kk >= jj) {
+            for (int g = 0; g < RG; ++g) xr[t][g] = (32 * g + lane == warp + 8 * t) ? (T)1 : (T)0;
+        auto step = [&](int k, auto gk) {
+            constexpr int G = decltype(gk)::value;
+            T lk[RG];
 #pragma unroll
-                for (int ii = kk + 1; ii < kDB; ++ii) xr[ii] -= x[(o + ii) + (o + kk) * LD] * xr[kk];
+            for (int g = 0; g < RG; ++g) {
+                const int i = 32 * g + lane;
+                const T v = x[min(i, W - 1) + k * LD];
+                lk[g] = (i > k && i < W) ? v : (T)0;
+            }
+#pragma unroll
+            for (int t = 0; t < CPW; ++t) {
+                const T xk = __shfl_sync(0xffffffffu, xr[t][G], k & 31);
+#pragma unroll
+                for (int g = 0; g < RG; ++g) xr[t][g] = fmaf(-lk[g], xk, xr[t][g]);
+            }
+        };
+        const int kmid = W < 32 ? W - 1 : 32;
+        for (int k = warp; k < kmid; ++k) step(k, std::integral_constant<int, 0>());
+        if constexpr (RG > 1)
+            for (int k = 32; k < W - 1; ++k) step(k, std::integral_constant<int, RG - 1>());
+        // Cholesky: L^{-1} = diag(1/sqrt(d)) l^{-1}.  LDL^T: l^{-1} below the
+        // diagonal (unit), 1/d on it.
+#pragma unroll
+        for (int t = 0; t < CPW; ++t) {
+            const int j = warp + 8 * t;
+#pragma unroll
+            for (int g = 0; g < RG; ++g) {
+                const int i = 32 * g + lane;
+                if (i < w && j < w) {
+                    T v;
+                    if constexpr (ldlt) v = i > j ? xr[t][g] : (i == j ? rvf[i] : (T)0);
+                    else v = i >= j ? xr[t][g] * rvf[i] : (T)0;
+                    Mi[i + j * w] = v;
+                }
             }
         }
-        __syncwarp(0xffu);
+    } else {
+        // unit-lower inverse: 8 x 8 diagonal blocks first
+        if (warp < W / kDB && lane < kDB) {
+            const int o = warp * kDB, jj = lane;
+            T xr[kDB];
 #pragma unroll
-        for (int ii = 0; ii < kDB; ++ii)
-            if (ii > jj) x[(o + ii) + (o + jj) * LD] = xr[ii];
-    }
-    __syncthreads();
+            for (int q = 0; q < kDB; ++q) xr[q] = q == jj ? (T)1 : (T)0;
 #pragma unroll
-    for (int sz = kDB; sz < W; sz *= 2) {
-        const int npair = W / (2 * sz);
-        for (int e = tid; e < npair * sz * sz; e += NT) {
-            const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
-            const int o = pr * 2 * sz;
-            T acc = (T)0;
-            for (int k = j; k < sz; ++k) acc += x[(o + sz + i) + (o + k) * LD] * x[(o + k) + (o + j) * LD];
-            tmp[pr * sz * sz + i + j * sz] = acc;
+            for (int kk = 0; kk < kDB; ++kk) {
+                if (kk >= jj) {
+#pragma unroll
+                    for (int ii = kk + 1; ii < kDB; ++ii) xr[ii] -= x[(o + ii) + (o + kk) * LD] * xr[kk];
+                }
+            }
+            __syncwarp(0xffu);
+#pragma unroll
+            for (int ii = 0; ii < kDB; ++ii)
+                if (ii > jj) x[(o + ii) + (o + jj) * LD] = xr[ii];
         }
         __syncthreads();
-        for (int e = tid; e < npair * sz * sz; e += NT) {
-            const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
-            const int o = pr * 2 * sz;
-            T acc = tmp[pr * sz * sz + i + j * sz];   // C^{-1} has a unit diagonal
-            for (int k = 0; k < i; ++k) acc += x[(o + sz + i) + (o + sz + k) * LD] * tmp[pr * sz * sz + k + j * sz];
-            x[(o + sz + i) + (o + j) * LD] = -acc;
+#pragma unroll
+        for (int sz = kDB; sz < W; sz *= 2) {
+            const int npair = W / (2 * sz);
+            for (int e = tid; e < npair * sz * sz; e += NT) {
+                const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
+                const int o = pr * 2 * sz;
+                T acc = (T)0;
+                for (int k = j; k < sz; ++k) acc += x[(o + sz + i) + (o + k) * LD] * x[(o + k) + (o + j) * LD];
+                tmp[pr * sz * sz + i + j * sz] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < npair * sz * sz; e += NT) {
+                const int pr = e / (sz * sz), rem = e % (sz * sz), i = rem % sz, j = rem / sz;
+                const int o = pr * 2 * sz;
+                T acc = tmp[pr * sz * sz + i + j * sz];   // C^{-1} has a unit diagonal
+                for (int k = 0; k < i; ++k) acc += x[(o + sz + i) + (o + sz + k) * LD] * tmp[pr * sz * sz + k + j * sz];
+                x[(o + sz + i) + (o + j) * LD] = -acc;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-    }
-    // Cholesky: L^{-1} = diag(1/sqrt(d)) l^{-1}.  LDL^T: l^{-1} below the
-    // diagonal (unit), 1/d on it.
-    T *Mi = Dinv + p.pinv[pid];
-    for (int idx = tid; idx < w * w; idx += NT) {
-        const int i = idx % w, j = idx / w;
-        if constexpr (ldlt) Mi[idx] = i > j ? x[i + j * LD] : (i == j ? (T)rsv[i] : (T)0);
-        else Mi[idx] = i >= j ? x[i + j * LD] * (T)rsv[i] : (T)0;
+        // Cholesky: L^{-1} = diag(1/sqrt(d)) l^{-1}.  LDL^T: l^{-1} below the
+        // diagonal (unit), 1/d on it.
+        for (int idx = tid; idx < w * w; idx += NT) {
+            const int i = idx % w, j = idx / w;
+            if constexpr (ldlt) Mi[idx] = i > j ? x[i + j * LD] : (i == j ? rvf[i] : (T)0);
+            else Mi[idx] = i >= j ? x[i + j * LD] * rvf[i] : (T)0;
+        }
     }
 }
 
@@ -339,7 +492,7 @@ template <typename T, int W>
 __host__ __device__ constexpr size_t ldl_smem_bytes()
 {
     return sizeof(double) * ((size_t)W * (W + 1) + (size_t)2 * W * kDB + 2 * W) +
-           sizeof(T) * ((size_t)W * (W + 1) + (size_t)(W / 2) * (W / 2));
+           sizeof(T) * ((size_t)W * (W + 1) + (size_t)(W / 2) * (W / 2) + 2 * (size_t)W);
 }
 
 // ---------------------------------------------------------------------------
