@@ -13,6 +13,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include <cstring>
 #include <new>
 #include <queue>
@@ -39,6 +40,7 @@ struct spx_handle_s {
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     cudaStream_t fstream[2] = {nullptr, nullptr};   // far update tiles of alternate levels (look-ahead)
     cudaEvent_t ev_trsm = nullptr, ev_far[2] = {nullptr, nullptr};
+    cudaEvent_t ev_near[2] = {nullptr, nullptr};    // a chain link's TRSM and near tiles, done beside the next diagonal block
     std::vector<void *> allocs;
 
     spx::DevPlan dp{};
@@ -122,6 +124,15 @@ struct spx_handle_s {
     std::vector<int64_t> near_end[7];
     std::vector<int64_t> tctile_ptr;  // per level, 128 x 128 tensor-core tiles
     spx::TcTile *d_tctiles = nullptr;
+    // chain links (Cholesky, tensor-core modes): level l holds one 64-wide
+    // panel p and level l + 1 one 64-wide panel q whose columns are p's first
+    // 64 off-diagonal rows.  link_task[l] is the task p -> q (-1: not a link);
+    // d_link_tct[link_ptr[l] ..) the level's near tensor-core tiles with that
+    // task's tiles starting below q's diagonal block, which the look-ahead
+    // step updates instead.
+    std::vector<int32_t> link_task;
+    std::vector<int64_t> link_ptr;
+    spx::TcTile *d_link_tct = nullptr;
     int kpad = 0;                     // operand-copy row length
     int64_t op_rows = 0;              // operand-copy rows (sum of panel heights)
     void *d_opc = nullptr;            // operand copy (TF32 floats, BF16, or the hi half of split TF32)
@@ -577,6 +588,7 @@ spx_status ensure_device(spx_handle h)
     for (int k = 0; k < 2; ++k) {
         CU(cudaStreamCreateWithFlags(&h->fstream[k], cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&h->ev_far[k], cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&h->ev_near[k], cudaEventDisableTiming));
     }
     CU(cudaEventCreateWithFlags(&h->ev_fence, cudaEventDisableTiming));
     CU(cudaEventCreate(&h->ev_t0));
@@ -864,7 +876,50 @@ spx_status ensure_device(spx_handle h)
             sort_segment(small, h->tcsmall_ptr[l], h->tcsmall_nar[l], l, h->det_ptr[5], h->near_end[5]);
             sort_segment(small, h->tcsmall_nar[l], h->tcsmall_ptr[l + 1], l, h->det_ptr[6], h->near_end[6]);
         }
-        if ((st = upload(h, &h->d_tcsmall, small)) || (st = upload(h, &h->d_tctiles, tct)))
+        // chain links: see link_task.  The link's own task keeps only the rows
+        // below q's diagonal block: 128-row tiles from its row r1 = r0 + 64
+        // instead of from r0
+        h->link_task.assign(P.nlevels, -1);
+        h->link_ptr.assign(P.nlevels + 1, 0);
+        std::vector<spx::TcTile> ltct;
+        for (int32_t l = 0; l < P.nlevels; ++l) {
+            h->link_ptr[l] = (int64_t)ltct.size();
+            if (P.method != SPX_LLT || l + 1 >= P.nlevels || P.level_ptr[l + 1] - P.level_ptr[l] != 1 ||
+                P.level_ptr[l + 2] - P.level_ptr[l + 1] != 1)
+                continue;
+            const int32_t pk = P.level_panels[P.level_ptr[l]], qk = P.level_panels[P.level_ptr[l + 1]];
+            const int32_t w = P.pw[pk];
+            if (P.pparent[pk] != qk || w != spx::kUpdTile || P.pw[qk] != spx::kUpdTile || w < kTcMinWidth ||
+                P.ph[pk] < w + spx::kUpdTile || h->chunk_ptr[l + 1] - h->chunk_ptr[l] < 1 ||
+                chunks[h->chunk_ptr[l]].panel != pk || chunks[h->chunk_ptr[l]].r0 != w)
+                continue;
+            bool rows_ok = true;
+            for (int32_t i = 0; i < spx::kUpdTile && rows_ok; ++i)
+                rows_ok = P.rows[P.prow[pk] + w + i] == P.pfcol[qk] + i;
+            if (!rows_ok) continue;
+            int32_t lt = -1;
+            for (int32_t t = P.level_task_ptr[l]; t < P.level_task_ptr[l + 1]; ++t)
+                if (P.tasks[t].src == pk && P.tasks[t].tgt == qk && P.tasks[t].r0 == w &&
+                    P.tasks[t].r1 == w + spx::kUpdTile)
+                    lt = t;
+            if (lt < 0) continue;
+            const int64_t n0 = h->tctile_ptr[l], n1 = h->near_end[4][l];
+            int64_t ntask = 0;
+            for (int64_t i = h->tctile_ptr[l]; i < h->tctile_ptr[l + 1]; ++i)
+                if (tct[i].task == lt) {
+                    if (i >= n1) ntask = -1;   // the link's tiles must all be near ones
+                    if (ntask >= 0) ++ntask;
+                }
+            if (ntask <= 0) continue;
+            for (int64_t i = n0; i < n1; ++i)
+                if (tct[i].task != lt) ltct.push_back(tct[i]);
+            const spx::Task &tk = P.tasks[lt];
+            for (int32_t m0 = tk.r1; m0 < P.ph[pk]; m0 += 128) ltct.push_back(spx::TcTile{lt, m0, tk.r0, 0});
+            h->link_task[l] = lt;
+        }
+        h->link_ptr[P.nlevels] = (int64_t)ltct.size();
+        if ((st = upload(h, &h->d_tcsmall, small)) || (st = upload(h, &h->d_tctiles, tct)) ||
+            (!ltct.empty() && (st = upload(h, &h->d_link_tct, ltct))))
             return st;
         int nsm = 0;
         CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
@@ -1047,6 +1102,13 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
     // joined before the diagonal blocks of level l + 2
     const bool lookahead = !mk.on && !h->deterministic && !lu;
     bool far_pending[2] = {false, false};
+    // chain links (look-ahead by one diagonal block): after panel p's diagonal
+    // block a one-CTA step solves p's rows facing q and updates q's diagonal
+    // block with them; q's diagonal block follows at once on the main stream,
+    // while p's other TRSM chunks and update tiles run on a side stream whose
+    // near part is joined before q's own TRSM (or link step)
+    bool near_pending = false;
+    int near_slot = 0;
     for (int32_t l = 0; l < qlev; ++l) {
         if (far_pending[l % 2]) {   // the far tiles of level l - 2
             cudaStreamWaitEvent(s, h->ev_far[l % 2], 0);
@@ -1085,6 +1147,12 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
         (void)panels;
         (void)np;
         mk.mark(SPX_K_DIAG);
+        if (near_pending) {   // the previous link's TRSM and near tiles
+            cudaStreamWaitEvent(s, h->ev_near[near_slot], 0);
+            near_pending = false;
+        }
+        const bool link = lookahead && tc && !ldlt && l + 1 < qlev && h->link_task.size() == (size_t)P.nlevels &&
+                          h->link_task[l] >= 0;
         // update launches of this level: one set, or one set per round in the
         // deterministic mode (slices of the round-sorted tile segments)
         // (a level without update tasks has no rounds: nothing to launch)
@@ -1106,14 +1174,17 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
         };
         int64_t o;
         if (!lu) {
-            spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, ldlt ? spx::TRSM_LDLT : spx::TRSM_LLT, opc, opc_lo,
-                                h->kpad, op_kind, s, W);
-            cnt += nch > 0;
-            h->class_launches[SPX_K_TRSM] += nch > 0;
+            if (!link) {
+                spx::launch_trsm<T>(h->dp, ch, nch, wmax, Dinv, L, ldlt ? spx::TRSM_LDLT : spx::TRSM_LLT, opc,
+                                    opc_lo, h->kpad, op_kind, s, W);
+                cnt += nch > 0;
+                h->class_launches[SPX_K_TRSM] += nch > 0;
+            }
             mk.mark(SPX_K_TRSM);
             const T *Bop = ldlt ? W : L;   // LDL^T: C -= L (D L^T)
             // one set of update launches over tile ranges: wide and narrow
             // CUDA-core tiles, and the tensor-core tiles in tc modes
+            const spx::TcTile *tcbase = h->d_tctiles;
             auto launch_set = [&](int64_t a0, int64_t a1, int64_t b0, int64_t b1, int64_t c0, int64_t c1,
                                   Branches &ub, cudaStream_t one) {
                 const int na = (int)(a1 - a0), nb = (int)(b1 - b0), nc = (int)(c1 - c0);
@@ -1124,7 +1195,7 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
                                           st(na > 0 ? 1 : 0), 1);
                 } else {
                     // the tensor-core tiles on the main stream, the CUDA-core ones beside them
-                    spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, h->d_tctiles + c0, nc,
+                    spx::launch_update_tc(h->tmap, h->tmap_lo, op_kind, h->dp, h->d_tasks, tcbase + c0, nc,
                                           (float *)L, 1, h->d_tcerr, st(0));
                     mk.mark(SPX_K_UPDATE_TC);
                     spx::launch_update<T>(h->dp, h->d_tasks, h->d_tcsmall + a0, na, L, Bop, L, 1, 0,
@@ -1155,6 +1226,34 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
                 launch_set(A0, A1, B0, B1, C0, C1, ub, nullptr);
                 ub.join();
                 mk.mark(SPX_K_UPDATE);
+            } else if (link) {
+                if constexpr (std::is_same<T, float>::value) {
+                    const int32_t lt = h->link_task[l];
+                    spx::launch_lead<T>(h->dp, h->hc_chunks[h->chunk_ptr[l]], h->d_tasks, lt, Dinv, L, opc, opc_lo,
+                                        h->kpad, op_kind, s);
+                    cnt += 1;
+                    h->class_launches[SPX_K_TRSM] += 1;
+                    cudaEventRecord(h->ev_trsm, s);
+                    cudaStream_t fs = h->fstream[l % 2];
+                    cudaStreamWaitEvent(fs, h->ev_trsm, 0);
+                    spx::launch_trsm<T>(h->dp, ch + 1, nch - 1, wmax, Dinv, L, spx::TRSM_LLT, opc, opc_lo, h->kpad,
+                                        op_kind, fs, W);
+                    cnt += nch > 1;
+                    h->class_launches[SPX_K_TRSM] += nch > 1;
+                    const int64_t An = h->near_end[sa][l], Bn = h->near_end[sb][l], Cn = h->near_end[4][l];
+                    Branches none{h, false};
+                    tcbase = h->d_link_tct;
+                    launch_set(A0, An, B0, Bn, h->link_ptr[l], h->link_ptr[l + 1], none, fs);
+                    tcbase = h->d_tctiles;
+                    cudaEventRecord(h->ev_near[l % 2], fs);
+                    near_pending = true;
+                    near_slot = l % 2;
+                    if (An < A1 || Bn < B1 || Cn < C1) {
+                        launch_set(An, A1, Bn, B1, Cn, C1, none, fs);
+                        cudaEventRecord(h->ev_far[l % 2], fs);
+                        far_pending[l % 2] = true;
+                    }
+                }
             } else {
                 const int64_t An = h->near_end[sa][l], Bn = h->near_end[sb][l], Cn = tc ? h->near_end[4][l] : 0;
                 const bool far = An < A1 || Bn < B1 || Cn < C1;
@@ -1194,6 +1293,7 @@ void enqueue_factorization(spx_handle h, bool mixed, Marks &mk, int prec, int pa
     }
     for (int k = 0; k < 2; ++k)
         if (far_pending[k]) cudaStreamWaitEvent(s, h->ev_far[k], 0);
+    if (near_pending) cudaStreamWaitEvent(s, h->ev_near[near_slot], 0);
     if (qlev < P.nlevels) {
         // the upper levels: one persistent launch over the task queue
         const int mode = tc ? 1 : 0;
@@ -2666,6 +2766,7 @@ void spx_free(spx_handle h)
     for (int k = 0; k < 2; ++k) {
         if (h->fstream[k]) cudaStreamDestroy(h->fstream[k]);
         if (h->ev_far[k]) cudaEventDestroy(h->ev_far[k]);
+        if (h->ev_near[k]) cudaEventDestroy(h->ev_near[k]);
     }
     if (h->h_noalloc_err) cudaFreeHost(h->h_noalloc_err);
     for (int b = 0; b < 2; ++b) {

@@ -12,6 +12,7 @@
 #include "blocks.cuh"
 
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cstdio>
 
 namespace spx {
@@ -549,6 +550,40 @@ void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, 
     trsm_gemm_kernel<T><<<count, 256, smem, s>>>(p, chunks, Dinv, X, mode, opc, opc_lo, kpad, op_kind, Wout);
 }
 
+// Look-ahead step of a chain link (Sec. III's task order, with the next
+// diagonal block first): panel p's single level is followed by a single
+// panel q whose columns are p's first 64 off-diagonal rows.  One CTA solves
+// those rows against p's inverted diagonal block (chunk 0 of p's TRSM, with
+// its operand copy) and subtracts their product L_qp L_qp^T from q's diagonal
+// block (the lower triangle, in the factor's arithmetic on the CUDA cores,
+// with reductions like every update).  q's diagonal block then needs
+// nothing else from p, so it is factored right after this step while p's
+// other TRSM chunks and update tiles run beside it.
+template <typename T>
+__global__ void __launch_bounds__(256) lead_kernel(DevPlan p, RowChunk ch, const DevTask *__restrict__ tasks,
+                                                   int32_t task, const T *__restrict__ Dinv, T *__restrict__ L,
+                                                   void *opc, void *opc_lo, int kpad, int op_kind)
+{
+    extern __shared__ unsigned char smraw[];
+    trsm_chunk<T>(p, ch, Dinv, L, TRSM_LLT, opc, opc_lo, kpad, op_kind, nullptr, smraw);
+    __syncthreads();   // the chunk's rows, written above, are read back through L2
+    const DevTask tk = tasks[task];
+    update_tile<T, kUpdTile>(p, tk, UpdTile{task, tk.r0, tk.r0, 0}, L, L, L, 1, 0, reinterpret_cast<T *>(smraw));
+}
+
+template <typename T>
+void launch_lead(const DevPlan &p, RowChunk ch, const DevTask *tasks, int32_t task, const T *Dinv, T *L,
+                 void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s)
+{
+    const size_t smem = std::max(trsm_smem_bytes<T>(kUpdTile), update_smem_elems<T, kUpdTile>() * sizeof(T));
+    static bool once = false;
+    if (!once) {
+        cudaFuncSetAttribute(lead_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        once = true;
+    }
+    lead_kernel<T><<<1, 256, smem, s>>>(p, ch, tasks, task, Dinv, L, opc, opc_lo, kpad, op_kind);
+}
+
 template <typename T, int TN>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) update_kernel(DevPlan p, const DevTask *__restrict__ tasks,
                                                      const UpdTile *__restrict__ tiles,
@@ -580,6 +615,7 @@ template void launch_potrf<float>(const DevPlan &, const int32_t *, int, int, in
 template void launch_getrf<double>(const DevPlan &, const int32_t *, int, int, int, double *, double *, const double *, int64_t *, unsigned long long *, cudaStream_t);
 template void launch_getrf<float>(const DevPlan &, const int32_t *, int, int, int, float *, float *, const double *, int64_t *, unsigned long long *, cudaStream_t);
 template void launch_trsm<double>(const DevPlan &, const RowChunk *, int, int, const double *, double *, int, void *, void *, int, int, cudaStream_t, double *);
+template void launch_lead<float>(const DevPlan &, RowChunk, const DevTask *, int32_t, const float *, float *, void *, void *, int, int, cudaStream_t);
 template void launch_ldlt_diag<double>(const DevPlan &, const int32_t *, int, int, double *, double *, const double *, int64_t *, unsigned long long *, unsigned long long *, cudaStream_t);
 template void launch_trsm<float>(const DevPlan &, const RowChunk *, int, int, const float *, float *, int, void *, void *, int, int, cudaStream_t, float *);
 template void launch_ldlt_diag<float>(const DevPlan &, const int32_t *, int, int, float *, float *, const double *, int64_t *, unsigned long long *, unsigned long long *, cudaStream_t);

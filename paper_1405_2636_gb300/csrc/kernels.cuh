@@ -96,6 +96,13 @@ void launch_trsm(const DevPlan &p, const RowChunk *chunks, int count, int wmax, 
                  T *X, int mode, void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s,
                  T *Wout = nullptr);
 
+// Chain-link look-ahead step: chunk 0 of panel ch.panel's TRSM and the
+// update of the next panel's diagonal block by it (task `task`).
+template <typename T>
+void launch_lead(const DevPlan &p, RowChunk ch, const DevTask *tasks, int32_t task, const T *Dinv, T *L,
+                 void *opc, void *opc_lo, int kpad, int op_kind, cudaStream_t s);
+
+
 // LDL^T diagonal blocks, panels at most 64 wide (factor.cu): l with d on the
 // diagonal, l^{-1} with 1/d on its diagonal at Dinv; static pivoting with
 // threshold *tau; negative pivots counted in *nneg.
