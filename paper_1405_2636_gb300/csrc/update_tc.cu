@@ -18,6 +18,8 @@
 // code, skips the epilogue and still releases its tensor memory.
 #include "tc_common.cuh"
 
+#include <algorithm>
+
 namespace spx {
 namespace {
 
@@ -174,6 +176,186 @@ __global__ void __launch_bounds__(128, 1)
                      "r"(kTmemCols));
 }
 
+// Persistent form, for launches of more tiles than SMs: CTA b takes tiles
+// b, b + gridDim.x, ... with two TMEM accumulators, so that the epilogue of
+// one tile overlaps the loads and MMAs of the next.
+//   warp 4 (one thread)  the TMA loads into the operand ring and the MMAs
+//                        of tile i into accumulator i & 1;
+//   warps 0-3            the epilogue of every tile from its accumulator,
+//                        each warp with its own copy of the tile's target
+//                        column offsets (no barrier among them).
+// Hand-offs: full / empty per ring stage (TMA bytes / MMA completion),
+// acc_full per accumulator (MMA completion), acc_empty per accumulator (one
+// arrival per epilogue warp).  Every wait is bounded and also gives up once
+// another role has failed; the CTA then records an error and still releases
+// its tensor memory.
+constexpr uint32_t kPersistCols = 2 * kTmemCols;
+constexpr int kPersistThreads = 160;
+
+template <int KIND>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    update_tc_persistent(const __grid_constant__ CUtensorMap opmap,
+                         const __grid_constant__ CUtensorMap opmap_lo, DevPlan p,
+                         const DevTask *__restrict__ tasks, const TcTile *__restrict__ tiles, int count,
+                         float *__restrict__ C, int lower, int *err)
+{
+    constexpr int kBase = KIND == 3 ? 0 : (KIND == 4 ? 1 : KIND);
+    constexpr bool kSepB = KIND >= 3;
+    constexpr int kElems = kBase == 1 ? 64 : 32;
+    constexpr uint32_t kIdesc = make_idesc(kBase == 1 ? 1u : 2u);
+    constexpr int kParts = KIND == 2 ? 2 : 1;
+    constexpr uint32_t kStageTx = 2u * kParts * kTileBytes;
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;
+    unsigned char *sB = base + kStages * kTileBytes;
+    unsigned char *sAl = base + 2 * kStages * kTileBytes;
+    unsigned char *sBl = base + 3 * kStages * kTileBytes;
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ __align__(8) uint64_t empty[kStages];
+    __shared__ __align__(8) uint64_t acc_full[2];
+    __shared__ __align__(8) uint64_t acc_empty[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_fail;
+    __shared__ int64_t s_coff[4][kN];   // per epilogue warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kPersistCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            const CUtensorMap *mapb = kSepB ? &opmap_lo : &opmap;
+            uint32_t it = 0;   // operand chunks loaded so far: the ring position
+            int lt = 0;        // this CTA's tiles so far
+            bool ok = true;
+            for (int t = blockIdx.x; t < count && ok; t += gridDim.x, ++lt) {
+                const TcTile tl = tiles[t];
+                const DevTask tk = tasks[tl.task];
+                const int src = tk.src, K = p.pw[src];
+                const int nk = (K + kElems - 1) / kElems;
+                const int64_t rbase = p.prow[src];
+                const int ya = (int)(rbase + tl.m0), yb = (int)(rbase + tl.n0);
+                const int b = lt & 1;
+                const uint32_t acc = tmem + (uint32_t)(b * (int)kTmemCols);
+                // chunk kc of this tile into ring slot j (after the slot's previous MMAs)
+                auto load = [&](int kc, uint32_t j) -> bool {
+                    const int s = (int)(j % kStages);
+                    const uint32_t u = j / kStages;
+                    if (u >= 1 && !mbar_wait_or(&empty[s], (u - 1) & 1u, &s_fail)) return false;
+                    mbar_expect_tx(&full[s], kStageTx);
+                    tma_load_2d(sA + s * kTileBytes, &opmap, &full[s], kc * kElems, ya);
+                    tma_load_2d(sB + s * kTileBytes, mapb, &full[s], kc * kElems, yb);
+                    if (KIND == 2) {
+                        tma_load_2d(sAl + s * kTileBytes, &opmap_lo, &full[s], kc * kElems, ya);
+                        tma_load_2d(sBl + s * kTileBytes, &opmap_lo, &full[s], kc * kElems, yb);
+                    }
+                    return true;
+                };
+                const uint32_t it0 = it;
+                for (int kc = 0; kc < nk && kc < kStages && ok; ++kc) ok = load(kc, it0 + (uint32_t)kc);
+                // the accumulator must be drained of tile lt - 2
+                if (ok && lt >= 2) ok = mbar_wait_or(&acc_empty[b], (uint32_t)((lt >> 1) - 1) & 1u, &s_fail);
+                for (int kc = 0; kc < nk && ok; ++kc) {
+                    const uint32_t j = it0 + (uint32_t)kc;
+                    const int s = (int)(j % kStages);
+                    if (!mbar_wait_or(&full[s], (j / kStages) & 1u, &s_fail)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+                    const uint32_t al = smem_u32(sAl + s * kTileBytes), bl = smem_u32(sBl + s * kTileBytes);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        if (KIND == 2) {
+                            mma<0>(acc, sw128_desc(al + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
+                                   (kc > 0 || ks > 0) ? 1u : 0u);
+                            mma<0>(acc, sw128_desc(a0 + 32 * ks), sw128_desc(bl + 32 * ks), kIdesc, 1u);
+                            mma<0>(acc, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc, 1u);
+                        } else {
+                            mma<kBase>(acc, sw128_desc(a0 + 32 * ks), sw128_desc(b0 + 32 * ks), kIdesc,
+                                       (kc > 0 || ks > 0) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                    if (kc + kStages < nk) ok = load(kc + kStages, j + kStages);
+                }
+                if (ok) mma_commit(&acc_full[b]);   // arrives once this tile's MMAs completed
+                it = it0 + (uint32_t)nk;
+            }
+            if (!ok) s_fail = 1;
+        }
+    } else {
+        int lt = 0;
+        for (int t = blockIdx.x; t < count; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            const TcTile tl = tiles[t];
+            const DevTask tk = tasks[tl.task];
+            const int src = tk.src, tgt = tk.tgt, h = p.ph[src];
+            // this warp's copy of the target column offsets of the tile's facing rows
+            for (int c = lane; c < kN; c += 32) {
+                const int j = tl.n0 + c;
+                s_coff[warp][c] = j < tk.r1 ? (int64_t)(p.rows[p.prow[src] + j] - p.pfcol[tgt]) * p.ph[tgt] : 0;
+            }
+            __syncwarp();
+            if (!mbar_wait_or(&acc_full[b], (uint32_t)(lt >> 1) & 1u, &s_fail)) {
+                s_fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float *Ct = C + p.pval[tgt];
+            const int32_t *rmap = p.relmap + tk.relmap_off - tk.r0;
+            const int i = tl.m0 + warp * 32 + lane;
+            const bool row_ok = i < h;
+            const int64_t roff = row_ok ? (int64_t)rmap[i] : 0;
+            const int jend = min(tk.r1, tl.n0 + kN);
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * (int)kTmemCols);
+            for (int c0 = 0; tl.n0 + c0 < jend; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+                for (int cc = 0; cc < 16; ++cc) {
+                    const int j = tl.n0 + c0 + cc;
+                    if (j >= jend) break;
+                    if (row_ok && (!lower || i >= j))
+                        atomicAdd(Ct + roff + s_coff[warp][c0 + cc], -__uint_as_float(v[cc]));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kPersistCols));
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -208,6 +390,32 @@ int make_operand_map(void *tmap_out, void *base, int64_t rows, int kpad, int bf1
     return r == CUDA_SUCCESS ? 0 : -2;
 }
 
+template <int KIND>
+void launch_tc_kind(const CUtensorMap &m, const CUtensorMap &ml, const DevPlan &p, const DevTask *tasks,
+                    const TcTile *tiles, int count, float *C, int lower, int *err, cudaStream_t s)
+{
+    static int nsm = 0;
+    static bool once = false;
+    const size_t smem = tc_smem_bytes(KIND);
+    // the persistent form at most two CTAs per SM: their 2 x 256 TMEM columns fill the SM's 512
+    const size_t psmem = std::max(smem, (size_t)80 * 1024);
+    if (!once) {
+        cudaFuncSetAttribute(update_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(update_tc_persistent<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        once = true;
+    }
+    const int per_sm = KIND == 2 ? 1 : 2;
+    if (count > nsm) {
+        const int grid = std::min(count, per_sm * std::max(nsm, 1));
+        update_tc_persistent<KIND><<<grid, kPersistThreads, psmem, s>>>(m, ml, p, tasks, tiles, count, C, lower, err);
+    } else {
+        update_tc_kernel<KIND><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
+    }
+}
+
 void launch_update_tc(const void *tmap, const void *tmap_lo, int kind, const DevPlan &p,
                       const DevTask *tasks, const TcTile *tiles, int count, float *C, int lower,
                       int *err, cudaStream_t s)
@@ -215,34 +423,12 @@ void launch_update_tc(const void *tmap, const void *tmap_lo, int kind, const Dev
     if (count <= 0) return;
     const CUtensorMap &m = *reinterpret_cast<const CUtensorMap *>(tmap);
     const CUtensorMap &ml = *reinterpret_cast<const CUtensorMap *>(kind >= 2 ? tmap_lo : tmap);
-    const size_t smem = tc_smem_bytes(kind);
-    static bool once[5] = {false, false, false, false, false};
-    if (kind == 3 || kind == 4) {
-        if (!once[kind]) {
-            cudaFuncSetAttribute(kind == 3 ? update_tc_kernel<3> : update_tc_kernel<4>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            once[kind] = true;
-        }
-        if (kind == 3) update_tc_kernel<3><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
-        else update_tc_kernel<4><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
-    } else if (kind == 1) {
-        if (!once[1]) {
-            cudaFuncSetAttribute(update_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            once[1] = true;
-        }
-        update_tc_kernel<1><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
-    } else if (kind == 2) {
-        if (!once[2]) {
-            cudaFuncSetAttribute(update_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            once[2] = true;
-        }
-        update_tc_kernel<2><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
-    } else {
-        if (!once[0]) {
-            cudaFuncSetAttribute(update_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            once[0] = true;
-        }
-        update_tc_kernel<0><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
+    switch (kind) {
+    case 1: return launch_tc_kind<1>(m, ml, p, tasks, tiles, count, C, lower, err, s);
+    case 2: return launch_tc_kind<2>(m, ml, p, tasks, tiles, count, C, lower, err, s);
+    case 3: return launch_tc_kind<3>(m, ml, p, tasks, tiles, count, C, lower, err, s);
+    case 4: return launch_tc_kind<4>(m, ml, p, tasks, tiles, count, C, lower, err, s);
+    default: return launch_tc_kind<0>(m, ml, p, tasks, tiles, count, C, lower, err, s);
     }
 }
 
