@@ -65,8 +65,8 @@ NCU_TRAFFIC = {
     "diag": {"traffic": 125.8e3, "algorithmic_bytes": 2 * 64 * 64 * 4,
              "launch": "potrf_ldl_kernel<float,64>, one 64-wide panel, 48^3 diffusion (cold caches)",
              "source": "profiles/potrf_ldl_kernel_diffusion3d_48.md"},
-    "update_tc": {"traffic": 37.8e6, "algorithmic_bytes": None,
-                  "launch": "update_tc_kernel<0>, 4728 tiles of one mid-tree level, 48^3 diffusion",
+    "update_tc": {"traffic": 23.3e6, "algorithmic_bytes": None,
+                  "launch": "update_tc_persistent<0>, one low level (304 CTAs over its tiles), 48^3 diffusion",
                   "source": "profiles/update_tc_kernel_diffusion3d_48.md"},
 }
 
