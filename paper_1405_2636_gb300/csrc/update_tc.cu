@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(128, 1)
                      "r"(kTmemCols));
 }
 
-// Persistent form, for launches of more tiles than SMs: CTA b takes tiles
-// b, b + gridDim.x, ... with two TMEM accumulators, so that the epilogue of
+// Persistent form, for launches of more tiles than SMs: one CTA per SM,
+// CTA b taking tiles b, b + gridDim.x, ... with two TMEM accumulators, so that the epilogue of
 // one tile overlaps the loads and MMAs of the next.
 //   warp 4 (one thread)  the TMA loads into the operand ring and the MMAs
 //                        of tile i into accumulator i & 1;
@@ -397,7 +397,10 @@ void launch_tc_kind(const CUtensorMap &m, const CUtensorMap &ml, const DevPlan &
     static int nsm = 0;
     static bool once = false;
     const size_t smem = tc_smem_bytes(KIND);
-    // the persistent form at most two CTAs per SM: their 2 x 256 TMEM columns fill the SM's 512
+    // the persistent form: one CTA per SM, which leaves room for the update
+    // launches running beside it (measured faster than two); 80 KB of shared
+    // memory each, so that at most two (of two launches) share an SM and
+    // their 2 x 256 TMEM columns fit its 512
     const size_t psmem = std::max(smem, (size_t)80 * 1024);
     if (!once) {
         cudaFuncSetAttribute(update_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -407,9 +410,8 @@ void launch_tc_kind(const CUtensorMap &m, const CUtensorMap &ml, const DevPlan &
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         once = true;
     }
-    const int per_sm = KIND == 2 ? 1 : 2;
     if (count > nsm) {
-        const int grid = std::min(count, per_sm * std::max(nsm, 1));
+        const int grid = std::max(nsm, 1);
         update_tc_persistent<KIND><<<grid, kPersistThreads, psmem, s>>>(m, ml, p, tasks, tiles, count, C, lower, err);
     } else {
         update_tc_kernel<KIND><<<count, 128, smem, s>>>(m, ml, p, tasks, tiles, C, lower, err);
