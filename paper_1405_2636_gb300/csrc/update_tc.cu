@@ -179,18 +179,21 @@ __global__ void __launch_bounds__(128, 1)
 // Persistent form, for launches of more tiles than SMs: one CTA per SM,
 // CTA b taking tiles b, b + gridDim.x, ... with two TMEM accumulators, so that the epilogue of
 // one tile overlaps the loads and MMAs of the next.
-//   warp 4 (one thread)  the TMA loads into the operand ring and the MMAs
+//   warp 8 (one thread)  the TMA loads into the operand ring and the MMAs
 //                        of tile i into accumulator i & 1;
-//   warps 0-3            the epilogue of every tile from its accumulator,
-//                        each warp with its own copy of the tile's target
-//                        column offsets (no barrier among them).
+//   warps 0-7            the epilogue of every tile from its accumulator:
+//                        warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+//                        scatters columns 64 (w / 4) .. + 63, with its own
+//                        copy of their target column offsets (no barrier
+//                        among the epilogue warps).
 // Hand-offs: full / empty per ring stage (TMA bytes / MMA completion),
 // acc_full per accumulator (MMA completion), acc_empty per accumulator (one
-// arrival per epilogue warp).  Every wait is bounded and also gives up once
+// arrival per epilogue warp, eight).  Every wait is bounded and also gives up once
 // another role has failed; the CTA then records an error and still releases
 // its tensor memory.
 constexpr uint32_t kPersistCols = 2 * kTmemCols;
-constexpr int kPersistThreads = 160;
+constexpr int kEpiWarps = 8;
+constexpr int kPersistThreads = 32 * (kEpiWarps + 1);
 
 template <int KIND>
 __global__ void __launch_bounds__(kPersistThreads, 1)
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     __shared__ __align__(8) uint64_t acc_empty[2];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_fail;
-    __shared__ int64_t s_coff[4][kN];   // per epilogue warp
+    __shared__ int64_t s_coff[kEpiWarps][kN / 2];   // per epilogue warp, its half of the columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
+            mbar_init(&acc_empty[b], kEpiWarps);
         }
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    if (warp == 4) {
+    if (warp == kEpiWarps) {
         if (lane == 0) {
             const CUtensorMap *mapb = kSepB ? &opmap_lo : &opmap;
             uint32_t it = 0;   // operand chunks loaded so far: the ring position
@@ -314,9 +317,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             const TcTile tl = tiles[t];
             const DevTask tk = tasks[tl.task];
             const int src = tk.src, tgt = tk.tgt, h = p.ph[src];
-            // this warp's copy of the target column offsets of the tile's facing rows
-            for (int c = lane; c < kN; c += 32) {
-                const int j = tl.n0 + c;
+            const int quad = warp & 3, cbase = (warp >> 2) * (kN / 2);
+            // this warp's copy of the target column offsets of its facing rows
+            for (int c = lane; c < kN / 2; c += 32) {
+                const int j = tl.n0 + cbase + c;
                 s_coff[warp][c] = j < tk.r1 ? (int64_t)(p.rows[p.prow[src] + j] - p.pfcol[tgt]) * p.ph[tgt] : 0;
             }
             __syncwarp();
@@ -327,12 +331,12 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float *Ct = C + p.pval[tgt];
             const int32_t *rmap = p.relmap + tk.relmap_off - tk.r0;
-            const int i = tl.m0 + warp * 32 + lane;
+            const int i = tl.m0 + quad * 32 + lane;
             const bool row_ok = i < h;
             const int64_t roff = row_ok ? (int64_t)rmap[i] : 0;
             const int jend = min(tk.r1, tl.n0 + kN);
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * (int)kTmemCols);
-            for (int c0 = 0; tl.n0 + c0 < jend; c0 += 16) {
+            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * (int)kTmemCols);
+            for (int c0 = cbase; c0 < cbase + kN / 2 && tl.n0 + c0 < jend; c0 += 16) {
                 uint32_t v[16];
                 tmem_ld16(taddr + (uint32_t)c0, v);
 #pragma unroll
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                     const int j = tl.n0 + c0 + cc;
                     if (j >= jend) break;
                     if (row_ok && (!lower || i >= j))
-                        atomicAdd(Ct + roff + s_coff[warp][c0 + cc], -__uint_as_float(v[cc]));
+                        atomicAdd(Ct + roff + s_coff[warp][c0 - cbase + cc], -__uint_as_float(v[cc]));
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
