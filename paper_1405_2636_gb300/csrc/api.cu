@@ -9,7 +9,11 @@
 
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -24,6 +28,64 @@
 using spx::DevTask;
 using spx::RowChunk;
 using spx::UpdTile;
+
+// Host threads for the copies between caller buffers and the pinned staging
+// buffers: one host memcpy thread moves ~16 GB/s, eight ~80 GB/s (Grace).
+// run(f) calls f(part, parts) on every worker and on the caller, and returns
+// once all parts are done.
+struct CopyPool {
+    std::vector<std::thread> workers;
+    std::mutex m;
+    std::condition_variable wake, done;
+    std::function<void(int, int)> job;
+    int gen = 0, pending = 0, parts = 1;
+    bool stop = false;
+    explicit CopyPool(int nworkers)
+    {
+        parts = nworkers + 1;
+        for (int k = 1; k <= nworkers; ++k) workers.emplace_back([this, k] { loop(k); });
+    }
+    void loop(int k)
+    {
+        int seen = 0;
+        for (;;) {
+            std::function<void(int, int)> f;
+            {
+                std::unique_lock<std::mutex> l(m);
+                wake.wait(l, [&] { return stop || gen != seen; });
+                if (stop) return;
+                seen = gen;
+                f = job;
+            }
+            f(k, parts);
+            std::lock_guard<std::mutex> l(m);
+            if (--pending == 0) done.notify_one();
+        }
+    }
+    void run(const std::function<void(int, int)> &f)
+    {
+        if (workers.empty()) return f(0, 1);
+        {
+            std::lock_guard<std::mutex> l(m);
+            job = f;
+            pending = parts - 1;
+            ++gen;
+        }
+        wake.notify_all();
+        f(0, parts);
+        std::unique_lock<std::mutex> l(m);
+        done.wait(l, [&] { return pending == 0; });
+    }
+    ~CopyPool()
+    {
+        {
+            std::lock_guard<std::mutex> l(m);
+            stop = true;
+        }
+        wake.notify_all();
+        for (auto &t : workers) t.join();
+    }
+};
 
 struct spx_handle_s {
     spx::Plan plan;
@@ -74,6 +136,7 @@ struct spx_handle_s {
     uint32_t spin_limit = spx::kDefaultSpinLimit;   // polls before a sweep wait gives up
     int32_t *h_noalloc_err = nullptr;   // pinned: the error word of the last completed spx_solve_noalloc
     void *h_stage[2] = {nullptr, nullptr};  // pinned staging buffers for host-buffer copies
+    std::unique_ptr<CopyPool> copy_pool;    // host threads packing and unpacking them
     cudaEvent_t ev_stage[2] = {nullptr, nullptr};
     UpdTile *d_tcsmall = nullptr;
     // persistent task queue of the upper levels (Cholesky and LDL^T, panels
@@ -1447,8 +1510,13 @@ spx_status ensure_stage(spx_handle h)
         if (!h->h_stage[b]) CU(cudaHostAlloc(&h->h_stage[b], kStageBytes, cudaHostAllocDefault));
         if (!h->ev_stage[b]) CU(cudaEventCreateWithFlags(&h->ev_stage[b], cudaEventDisableTiming));
     }
+    if (!h->copy_pool) {
+        const unsigned hw = std::thread::hardware_concurrency();
+        h->copy_pool.reset(new CopyPool((int)std::min(7u, hw > 1 ? hw - 1 : 0u)));
+    }
     return SPX_OK;
 }
+
 
 // walk the host side of a (cols x col_bytes) block in chunks of at most
 // kStageBytes; fn(host_piece, bytes, offset_in_chunk) for each piece
@@ -1466,6 +1534,31 @@ size_t chunk_pieces(size_t pos, size_t total, size_t col_bytes, size_t hpitch, c
     return len;
 }
 
+// Copy one staging chunk between the pinned buffer and the caller's pieces
+// of it, the chunk's bytes split evenly over the copy threads.
+template <bool TO_STAGE>
+void copy_chunk(spx_handle h, char *stage, size_t pos, size_t total, size_t col_bytes, size_t hpitch, char *host)
+{
+    struct Piece {
+        char *host;
+        size_t bytes, at;
+    };
+    std::vector<Piece> pieces;
+    const size_t len = chunk_pieces(pos, total, col_bytes, hpitch, host, [&](const char *hp, size_t bytes, size_t at) {
+        pieces.push_back(Piece{const_cast<char *>(hp), bytes, at});
+    });
+    h->copy_pool->run([&](int k, int parts) {
+        const size_t lo = (len * (size_t)k / (size_t)parts) & ~(size_t)63;
+        const size_t hi = k + 1 == parts ? len : (len * (size_t)(k + 1) / (size_t)parts) & ~(size_t)63;
+        for (const Piece &pc : pieces) {
+            const size_t a = std::max(lo, pc.at), b = std::min(hi, pc.at + pc.bytes);
+            if (a >= b) continue;
+            if (TO_STAGE) std::memcpy(stage + a, pc.host + (a - pc.at), b - a);
+            else std::memcpy(pc.host + (a - pc.at), stage + a, b - a);
+        }
+    });
+}
+
 spx_status staged_h2d(spx_handle h, void *dev, const void *host, size_t hpitch, size_t col_bytes, size_t cols)
 {
     spx_status st = ensure_stage(h);
@@ -1476,10 +1569,8 @@ spx_status staged_h2d(spx_handle h, void *dev, const void *host, size_t hpitch, 
     for (size_t pos = 0; pos < total; b ^= 1) {
         if (busy[b]) CU(cudaEventSynchronize(h->ev_stage[b]));
         char *stage = (char *)h->h_stage[b];
-        const size_t len = chunk_pieces(pos, total, col_bytes, hpitch, (char *)host,
-                                        [&](const char *src, size_t bytes, size_t at) {
-                                            std::memcpy(stage + at, src, bytes);
-                                        });
+        const size_t len = std::min(kStageBytes, total - pos);
+        copy_chunk<true>(h, stage, pos, total, col_bytes, hpitch, (char *)host);
         CU(cudaMemcpyAsync((char *)dev + pos, stage, len, cudaMemcpyHostToDevice, h->hs));
         CU(cudaEventRecord(h->ev_stage[b], h->hs));
         busy[b] = true;
@@ -1497,11 +1588,7 @@ spx_status staged_d2h(spx_handle h, void *host, size_t hpitch, const void *dev, 
     bool busy[2] = {false, false};
     auto drain = [&](int b) -> spx_status {
         CU(cudaEventSynchronize(h->ev_stage[b]));
-        const char *stage = (const char *)h->h_stage[b];
-        chunk_pieces(pend_pos[b], total, col_bytes, hpitch, (char *)host,
-                     [&](const char *dst, size_t bytes, size_t at) {
-                         std::memcpy(const_cast<char *>(dst), stage + at, bytes);
-                     });
+        copy_chunk<false>(h, (char *)h->h_stage[b], pend_pos[b], total, col_bytes, hpitch, (char *)host);
         busy[b] = false;
         return SPX_OK;
     };
