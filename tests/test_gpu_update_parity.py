@@ -56,6 +56,7 @@ CASES = [  # m, k (source width), nb (facing rows), lower, seed
     (777, 45, 16, False, 4),     # facing block of 16 rows: narrow CUDA-core tiles
     (2048, 256, 511, True, 5),   # wide source panel, K = 256
     (8192, 64, 400, False, 6),   # more tiles than one wave of the GPU
+    (8192, 160, 300, False, 7),  # more tiles than SMs, K spanning several operand-ring turns per tile
 ]
 
 COMBOS = [  # precision, engine, ldlt
