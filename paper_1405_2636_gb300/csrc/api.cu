@@ -2234,6 +2234,8 @@ spx_status spx_factorize(spx_handle h, const double *values, int values_on_devic
     h->info.bad_col = (bad == LLONG_MAX) ? -1 : bad;
     h->info.factor_bytes = (int64_t)(elems * esz * (P.method == SPX_LLT ? 1 : 2));
     h->precision = precision;
+    if (bad == -1)
+        return fail(h, SPX_ERR_TIMEOUT, "a diagonal block's warps gave up waiting on each other");
     if (bad != LLONG_MAX) {
         return fail(h, P.method == SPX_LLT ? SPX_ERR_NOT_SPD : SPX_ERR_ZERO_PIVOT,
                     "pivot failure at permuted column " + std::to_string(bad));
@@ -2318,6 +2320,8 @@ spx_status spx_factorize_part(spx_handle h, const double *values, int values_on_
     h->info.npivot_neg = P.method == SPX_LDLT ? (int64_t)nneg : 0;
     h->info.bad_col = (bad == LLONG_MAX) ? -1 : bad;
     h->precision = precision;
+    if (bad == -1)
+        return fail(h, SPX_ERR_TIMEOUT, "a diagonal block's warps gave up waiting on each other");
     if (bad != LLONG_MAX)
         return fail(h, P.method == SPX_LLT ? SPX_ERR_NOT_SPD : SPX_ERR_ZERO_PIVOT,
                     "pivot failure at permuted column " + std::to_string(bad));

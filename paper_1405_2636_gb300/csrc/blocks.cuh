@@ -157,6 +157,7 @@ __device__ __forceinline__ void dmma_f64(double &d0, double &d1, double a, doubl
 }
 
 constexpr int kDB = 8;
+constexpr long kDiagSpin = 1l << 22;   // polls of the hand-off counter before a diagonal block gives up
 
 __device__ __forceinline__ double shfl_d(double v, int src)
 {
@@ -171,10 +172,12 @@ __device__ __forceinline__ double shfl_d(double v, int src)
 //  * the factorization runs in LDL^T form in FP64 -- per column one
 //    reciprocal of the pivot (three FP64 operations), the multipliers, and
 //    the in-block updates, with no square root on the chain; warps 0 and 1
-//    own each 8-column block panel in registers (rows 0-31 and 32-63 of the
-//    block; each warp runs the pivot chain itself), the other warps apply
-//    the trailing updates; the next block's columns are updated between the
-//    panels (on the FP64 tensor path for W = 64, where nothing else runs);
+//    own each 8-column block panel in registers (rows kb .. kb+31 and the
+//    rest of the block); warp 0 runs the pivot chain and hands each column's
+//    reciprocal and block-row entries to warp 1 through shared memory (a
+//    counter, bounded wait), the other warps apply the trailing updates; the
+//    next block's columns are updated between the panels (on the FP64 tensor
+//    path for W = 64, where nothing else runs);
 //  * pivot tests and FP64 <-> FP32 conversions on the bit patterns;
 //  * L = l diag(sqrt(d)) is formed afterwards, all columns in parallel;
 //  * L^{-1} = diag(1/sqrt(d)) l^{-1}: FP32 factors invert the unit-lower l
@@ -194,7 +197,9 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
     double *lA = a + W * LD;                 // 2 x (W x kDB) unscaled block columns (ld W)
     double *dv = lA + 2 * W * kDB;           // pivots
     double *rsv = dv + W;                    // 1 / sqrt(pivot)
-    T *x = reinterpret_cast<T *>(rsv + W);   // W x LD inverse workspace
+    double *hand = rsv + W;                  // per block-panel column: block rows' entries (8) and 1 / pivot
+    volatile int *hflag = reinterpret_cast<volatile int *>(hand + 9 * kDB);   // columns handed to warp 1
+    T *x = reinterpret_cast<T *>(hand + 9 * kDB + 8);   // W x LD inverse workspace
     T *tmp = x + W * LD;                     // (W/2)^2, the FP64 factors' inverse
     T *dvf = tmp + (W / 2) * (W / 2);        // pivots (Cholesky: their square roots) in T
     T *rvf = dvf + W;                        // and their reciprocals
@@ -221,6 +226,7 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
             const int i = idx % W, j = idx / W;
             a[i + j * LD] = (i < w && j < w) ? to_f64<T>(vv[q]) : (i == j ? 1.0 : 0.0);
         }
+        if (tid == 0) *hflag = 0;
     }
     __syncthreads();
 
@@ -239,15 +245,43 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
     // that the next panel can overlap the trailing update of the previous).
     const bool tau_pos = replace_tau > 0.0;
     const long long tau_bits = tau_pos ? __double_as_longlong(replace_tau) : 0;
-    auto panel = [&](int kb, int role) {
+    auto panel = [&](int kb, int role, bool two) {
         double *lAb = lA + ((kb / kDB) & 1) * (W * kDB);
-        const int rq = role == 0 ? kb + lane : kb + (lane & 7);   // rows of the pivot chain
+        const int rq = kb + lane;                                 // role 0: rows of the pivot chain
         const int r1 = kb + 32 + lane;                            // role 1: its own rows
         double q[kDB], p1[kDB];
 #pragma unroll
         for (int c = 0; c < kDB; ++c) {
-            q[c] = rq < W ? a[rq + (kb + c) * LD] : 0.0;
+            q[c] = (role == 0 && rq < W) ? a[rq + (kb + c) * LD] : 0.0;
             p1[c] = (role == 1 && r1 < W) ? a[r1 + (kb + c) * LD] : 0.0;
+        }
+        if (role == 1) {
+            // the rows below: per column, the pivot's reciprocal and the block
+            // rows' unscaled entries from warp 0 (bounded wait on its counter)
+#pragma unroll
+            for (int c = 0; c < kDB; ++c) {
+                bool got = false;
+                for (long it = 0; it < kDiagSpin; ++it)
+                    if (*hflag >= kb + c + 1) {
+                        got = true;
+                        break;
+                    }
+                if (!got) {
+                    if (lane == 0) atomicMin((long long *)err_col, -1ll);
+                    break;
+                }
+                __threadfence_block();
+                const double r = hand[c * 9 + 8];
+                const double pl = p1[c] * r;
+#pragma unroll
+                for (int c2 = c + 1; c2 < kDB; ++c2) p1[c2] = fma(-pl, hand[c * 9 + c2], p1[c2]);
+                if (r1 < W) lAb[r1 + c * W] = p1[c];
+                p1[c] = pl;
+            }
+#pragma unroll
+            for (int c = 0; c < kDB; ++c)
+                if (r1 < W) a[r1 + (kb + c) * LD] = p1[c];
+            return;
         }
 #pragma unroll
         for (int c = 0; c < kDB; ++c) {
@@ -278,26 +312,25 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
             const double r = rcp_pivot(d);
             const double u0 = rq > k ? q[c] : 0.0;
             const double l0 = u0 * r;
+            if (two) {   // hand the column to warp 1
+                if (lane < kDB) hand[c * 9 + lane] = u0;
+                if (lane == 0) hand[c * 9 + 8] = r;
+                __syncwarp();
+                __threadfence_block();
+                if (lane == 0) *hflag = k + 1;
+            }
 #pragma unroll
             for (int c2 = c + 1; c2 < kDB; ++c2) {
                 const double ac = shfl_d(u0, c2);                   // A(kb + c2, k)
                 if (rq >= kb + c2) q[c2] = fma(-l0, ac, q[c2]);
-                if (role == 1) p1[c2] = fma(-(p1[c] * r), ac, p1[c2]);
             }
-            if (role == 0) {
-                if (rq < W) lAb[rq + c * W] = u0;
-                q[c] = rq > k ? l0 : (rq == k ? 1.0 : 0.0);
-                if (lane == c) dv[k] = d;
-            } else {
-                if (r1 < W) lAb[r1 + c * W] = p1[c];
-                p1[c] = p1[c] * r;
-            }
+            if (rq < W) lAb[rq + c * W] = u0;
+            q[c] = rq > k ? l0 : (rq == k ? 1.0 : 0.0);
+            if (lane == c) dv[k] = d;
         }
 #pragma unroll
-        for (int c = 0; c < kDB; ++c) {
-            if (role == 0 && rq < W) a[rq + (kb + c) * LD] = q[c];
-            if (role == 1 && r1 < W) a[r1 + (kb + c) * LD] = p1[c];
-        }
+        for (int c = 0; c < kDB; ++c)
+            if (rq < W) a[rq + (kb + c) * LD] = q[c];
     };
     // Rank-kDB update by block kb of the lower part of columns [j0, j1),
     // rows >= j; the (i, j) pairs are spread densely over the threads
@@ -327,8 +360,8 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
         }
     };
 
-    if (warp == 0) panel(0, 0);
-    else if (warp == 1 && 32 < W) panel(0, 1);
+    if (warp == 0) panel(0, 0, 32 < W);
+    else if (warp == 1 && 32 < W) panel(0, 1, true);
     __syncthreads();
     for (int kb = 0; kb < W; kb += kDB) {
         const int nb = kb + kDB;                 // next block
@@ -357,8 +390,8 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
             // warps 0 (and 1) factor the next block while the others finish
             // this block's update
             const bool two = nb + 32 < W;
-            if (warp == 0) panel(nb, 0);
-            else if (warp == 1 && two) panel(nb, 1);
+            if (warp == 0) panel(nb, 0, two);
+            else if (warp == 1 && two) panel(nb, 1, true);
             else update(kb, nb + kDB, W, tid - (two ? 64 : 32), NT - (two ? 64 : 32));
             __syncthreads();
         }
@@ -491,7 +524,7 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
 template <typename T, int W>
 __host__ __device__ constexpr size_t ldl_smem_bytes()
 {
-    return sizeof(double) * ((size_t)W * (W + 1) + (size_t)2 * W * kDB + 2 * W) +
+    return sizeof(double) * ((size_t)W * (W + 1) + (size_t)2 * W * kDB + 2 * W + 9 * kDB + 8) +
            sizeof(T) * ((size_t)W * (W + 1) + (size_t)(W / 2) * (W / 2) + 2 * (size_t)W);
 }
 
