@@ -62,11 +62,11 @@ def measured_peaks() -> dict:
 # (dram__bytes_read.sum + dram__bytes_write.sum), with the algorithmic bytes of
 # the same launch; profiles/ holds the captures and their commands.
 NCU_TRAFFIC = {
-    "diag": {"traffic": 125.8e3, "algorithmic_bytes": 2 * 64 * 64 * 4,
+    "diag": {"traffic": 132.6e3, "algorithmic_bytes": 2 * 64 * 64 * 4,
              "launch": "potrf_ldl_kernel<float,64>, one 64-wide panel, 48^3 diffusion (cold caches)",
              "source": "profiles/potrf_ldl_kernel_diffusion3d_48.md"},
-    "update_tc": {"traffic": 23.3e6, "algorithmic_bytes": None,
-                  "launch": "update_tc_persistent<0>, one low level (304 CTAs over its tiles), 48^3 diffusion",
+    "update_tc": {"traffic": 22.6e6, "algorithmic_bytes": None,
+                  "launch": "update_tc_persistent<0>, one low level (152 CTAs over its tiles), 48^3 diffusion",
                   "source": "profiles/update_tc_kernel_diffusion3d_48.md"},
 }
 
