@@ -153,7 +153,12 @@ spx_status spx_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, 
  * update computes A_i A_j^T and subtracts it directly at the positions of the
  * target panel's block structure).  `values` are the CSC values in the order
  * of the analysed pattern, host or device memory (`values_on_device`).  May
- * be called again with new values. */
+ * be called again with new values.  Returns SPX_ERR_NOT_SPD (Cholesky in FP64)
+ * or SPX_ERR_ZERO_PIVOT (LU / LDL^T without a replacement threshold) at a pivot
+ * failure (spx_info.bad_col), and SPX_ERR_TIMEOUT when one of the bounded
+ * device waits ran out: a tensor-core pipeline wait, a task-queue counter
+ * (spx_set_wait_limit), or the hand-off between the two warps of a diagonal
+ * block; the factor is then undefined and the handle stays usable. */
 spx_status spx_factorize(spx_handle h, const double *values, int values_on_device,
                          spx_precision precision, void *cuda_stream);
 
