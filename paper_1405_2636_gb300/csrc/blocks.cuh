@@ -345,13 +345,12 @@ __device__ __forceinline__ void ldl_diag_block(const DevPlan &p, int pid, T *__r
         }
         for (; j < j1;) {
             const int i = j + rem;
-            double s0 = 0.0, s1 = 0.0;
+            // one accumulator from the entry itself: eight FP64 instructions
+            // a pair, the fewest for the FP64 units the pivot chain shares
+            double s = a[i + j * LD];
 #pragma unroll
-            for (int c = 0; c < kDB; c += 2) {
-                s0 = fma(a[i + (kb + c) * LD], lAb[j + c * W], s0);
-                s1 = fma(a[i + (kb + c + 1) * LD], lAb[j + (c + 1) * W], s1);
-            }
-            a[i + j * LD] -= s0 + s1;
+            for (int c = 0; c < kDB; ++c) s = fma(-a[i + (kb + c) * LD], lAb[j + c * W], s);
+            a[i + j * LD] = s;
             rem += ts;
             while (j < j1 && rem >= W - j) {
                 rem -= W - j;
