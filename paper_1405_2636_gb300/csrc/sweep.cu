@@ -242,9 +242,11 @@ __device__ __forceinline__ void chunk_dot4(const T *Lc, const T *Xs, int k, int 
 // Shared memory: A (q.mat_elems: a diagonal block, or a chunk), B
 // (q.matb_elems: the chunk a panel item takes along), a vector of
 // q.vec_elems and, when panel items take chunks along, a second one.
-// Threads work as (row, column quad) = (tid & 63, tid >> 6).
+// Threads work as (row, column quad) = (tid & 63, tid >> 6).  FP32 factors:
+// five CTAs per SM (41.5 KB of shared memory each for 64-wide panels, at
+// most 48 registers a thread), so that more items' loads are in flight.
 template <typename T>
-__global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, SweepQueue q,
+__global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) fwd_queue_kernel(DevPlan p, SweepQueue q,
                                                               const RowChunk *__restrict__ chunks,
                                                               const T *__restrict__ Dinv, int unit,
                                                               const T *__restrict__ L, T *Y, T *Z, int nrhs)
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kQThreads, 4) fwd_queue_kernel(DevPlan p, Swee
 // lu: 0 Cholesky (M = Linv^T), 1 LU (M = U^{-1}), 2 LDL^T
 // (X_p = l^{-T} (D^{-1} Z_p - Tacc_p), 1/d on the diagonal of Dinv).
 template <typename T>
-__global__ void __launch_bounds__(kQThreads, 4) bwd_queue_kernel(DevPlan p, SweepQueue q,
+__global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_kernel(DevPlan p, SweepQueue q,
                                                               const RowChunk *__restrict__ chunks,
                                                               const T *__restrict__ Dinv, int lu,
                                                               const T *__restrict__ Lop,
