@@ -82,50 +82,51 @@ __device__ __forceinline__ void cta_release(int32_t *flag, int32_t *cnt, const i
     }
 }
 
-// The staging loops below issue every load of a batch before its first
-// store, so that a thread's global loads overlap instead of each waiting
-// for the previous one.
+// The factor's blocks (read-only during a sweep) go to shared memory by
+// asynchronous copies (cp.async, one element each, zero-filled past the
+// panel): every copy of an item is in flight at once, beside the item's
+// dependency wait, and stage_wait() before the barrier that precedes their
+// first use completes them.  The right-hand sides, written by other CTAs
+// of the same launch, are read through L2 after the wait; those staging
+// loops issue every load of a batch before its first store.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+    const int bytes = valid ? (int)sizeof(T) : 0;
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(src), "r"(bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(saddr), "l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// This thread's asynchronous copies are done (a barrier after it makes
+// every thread's visible to the CTA).
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Rows [r0, r0 + 64) of a panel's off-diagonal block to dst[k * ld + r]
 // (rows past the panel as zeros).
 template <typename T>
 __device__ __forceinline__ void stage_chunk(T *dst, int ld, const T *Pn, int h, int w, int r0, int nr)
 {
-    constexpr int NB = 8;
     const int total = w * 64;
-    for (int base = threadIdx.x; base < total; base += kQThreads * NB) {
-        T v[NB];
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int e = base + q * kQThreads, r = e & 63, k = e >> 6;
-            v[q] = (e < total && r < nr) ? Pn[r0 + r + (int64_t)k * h] : (T)0;
-        }
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int e = base + q * kQThreads;
-            if (e < total) dst[(e >> 6) * ld + (e & 63)] = v[q];
-        }
+    for (int e = threadIdx.x; e < total; e += kQThreads) {
+        const int r = e & 63, k = e >> 6;
+        const bool ok = r < nr;
+        cp_async_elem(dst + k * ld + r, ok ? Pn + r0 + r + (int64_t)k * h : Pn, ok);
     }
+    stage_commit();
 }
 
 // dst[e] = src[e], e < total (a diagonal block's inverse, column-major).
 template <typename T>
 __device__ __forceinline__ void stage_copy(T *dst, const T *src, int total)
 {
-    constexpr int NB = 8;
-    for (int base = threadIdx.x; base < total; base += kQThreads * NB) {
-        T v[NB];
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int e = base + q * kQThreads;
-            v[q] = e < total ? src[e] : (T)0;
-        }
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int e = base + q * kQThreads;
-            if (e < total) dst[e] = v[q];
-        }
-    }
+    for (int e = threadIdx.x; e < total; e += kQThreads) cp_async_elem(dst + e, src + e, true);
+    stage_commit();
 }
 
 // Right-hand-side blocks in shared memory hold kQRhs columns per row, the
@@ -283,10 +284,14 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) fwd_queue_k
                 stage_chunk(matB, 64, L + p.pval[pid], h, w, w, nr);
                 if (rt < nr) row = p.rows[p.prow[pid] + w + rt];
             }
-            if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err, q.spin_limit)) return;
+            if (!cta_wait(q.cnt + pid, nullptr, 1, q.need[pid], q.err, q.spin_limit)) {
+                stage_wait();   // no copy left in flight on the way out
+                return;
+            }
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_vec(vec, Y, f, w, nc, n, c0);
+                stage_wait();
                 __syncthreads();
                 for (int i = rt; i < w; i += 64) {
                     T acc[4];
@@ -325,10 +330,14 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) fwd_queue_k
             const int nr = min(64, h - ch.r0);
             stage_chunk(matA, 64, L + p.pval[pid], h, w, ch.r0, nr);
             const int64_t row = rt < nr ? p.rows[p.prow[pid] + ch.r0 + rt] : 0;
-            if (!cta_wait(q.flag + pid, nullptr, 1, 1, q.err, q.spin_limit)) return;
+            if (!cta_wait(q.flag + pid, nullptr, 1, 1, q.err, q.spin_limit)) {
+                stage_wait();   // no copy left in flight on the way out
+                return;
+            }
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_vec(vec, Z, f, w, nc, n, c0);
+                stage_wait();
                 __syncthreads();
                 fwd_chunk_pass(matA, vec, w, nr, nc, row, Y, n, c0);
                 __syncthreads();
@@ -425,7 +434,10 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_k
                 int ok = 1;
                 if (tid < m) ok = wait_geq(q.flag + q.tgt[t0 + tid], 1, q.err, q.spin_limit);
                 else if (tid == m) ok = wait_geq(q.cnt + pid, q.need[pid], q.err, q.spin_limit);
-                if (!__syncthreads_and(ok)) return;
+                if (!__syncthreads_and(ok)) {
+                    stage_wait();
+                    return;
+                }
             }
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
@@ -452,6 +464,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_k
                         if (e < w * kQRhs && e / w < nc) vec[vslot(e % w, e / w)] -= t[q];
                     }
                 }
+                stage_wait();
                 __syncthreads();
                 if (mc >= 0) {   // vec -= Lc^T X[rows]
                     for (int k = rt; k < w; k += 64) {
@@ -493,10 +506,14 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_k
             stage_chunk(matA, 65, Lop + p.pval[pid], h, w, ch.r0, nr);
             const int64_t row = rt < nr ? p.rows[p.prow[pid] + ch.r0 + rt] : 0;
             const int t0 = q.tptr[item], t1 = q.tptr[item + 1];
-            if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err, q.spin_limit)) return;
+            if (!cta_wait(q.flag, q.tgt + t0, t1 - t0, 1, q.err, q.spin_limit)) {
+                stage_wait();   // no copy left in flight on the way out
+                return;
+            }
             for (int c0 = 0; c0 < nrhs; c0 += kQRhs) {
                 const int nc = min(kQRhs, nrhs - c0);
                 stage_rows(vec, X, row, nr, nc, n, c0);
+                stage_wait();
                 __syncthreads();
                 for (int k = rt; k < w; k += 64) {
                     T acc[4] = {(T)0, (T)0, (T)0, (T)0};
