@@ -449,8 +449,19 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_k
                         vec[vslot(k, c)] = c < nc ? (lu == 2 ? Z[gk] * Mi[k + k * w] : Z[gk]) : (T)0;
                     }
                 }
-                // vec -= Tacc_p, loaded with the chunk's rows of X
-                if (mc >= 0) stage_rows(vec2, X, row, nr, nc, n, c0);
+                // vec -= Tacc_p, and the chunk's rows of X: both read through
+                // L2 in one batch (the X rows' loads go first, their stores
+                // after Tacc's loads are in flight)
+                constexpr int NCX = kQRhs / (kQThreads / 64);
+                const int xr = tid & 63, xc = tid >> 6;
+                T xv[NCX];
+                if (mc >= 0) {
+#pragma unroll
+                    for (int q = 0; q < NCX; ++q) {
+                        const int c = xc + q * (kQThreads / 64);
+                        xv[q] = (xr < nr && c < nc) ? ld_l2(X + row + (int64_t)(c0 + c) * n) : (T)0;
+                    }
+                }
                 for (int base = tid; base < w * kQRhs; base += kQThreads * 4) {
                     T t[4];
 #pragma unroll
@@ -463,6 +474,10 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_k
                         const int e = base + q * kQThreads;
                         if (e < w * kQRhs && e / w < nc) vec[vslot(e % w, e / w)] -= t[q];
                     }
+                }
+                if (mc >= 0) {
+#pragma unroll
+                    for (int q = 0; q < NCX; ++q) vec2[vslot(xr, xc + q * (kQThreads / 64))] = xv[q];
                 }
                 stage_wait();
                 __syncthreads();
