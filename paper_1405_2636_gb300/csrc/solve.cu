@@ -74,6 +74,10 @@ __device__ __forceinline__ unsigned long long abs_bits_inf(double v)
     return u > 0x7FF0000000000000ull ? 0x7FF0000000000000ull : u;
 }
 
+// Right-hand sides per pass of the residual: a row's entries are read once
+// per pass and applied to all of them (16 accumulators a thread).
+constexpr int kResRhs = 16;
+
 __global__ void __launch_bounds__(256) residual_kernel(int64_t n, int nrhs,
                                                        const int64_t *__restrict__ rp,
                                                        const int32_t *__restrict__ ci,
@@ -87,28 +91,44 @@ __global__ void __launch_bounds__(256) residual_kernel(int64_t n, int nrhs,
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int64_t e0 = i < n ? rp[i] : 0, e1 = i < n ? rp[i + 1] : 0;
-    for (int c = 0; c < nrhs; ++c) {
-        unsigned long long r = 0, ax = 0, ab = 0;
-        if (i < n) {
-            double s = 0.0;
-            for (int64_t e = e0; e < e1; ++e) s += vals[src[e]] * X[ci[e] + c * ldx];
-            const double b = B[i + c * ldb];
-            const double rr = b - s;
-            R[i + c * n] = rr;
-            r = abs_bits_inf(rr);
-            ax = abs_bits_inf(X[i + c * ldx]);
-            ab = abs_bits_inf(b);
+    for (int c0 = 0; c0 < nrhs; c0 += kResRhs) {
+        const int nc = min(kResRhs, nrhs - c0);
+        double s[kResRhs];
+#pragma unroll
+        for (int c = 0; c < kResRhs; ++c) s[c] = 0.0;
+        // per (row, column) the products are summed in entry order, as one
+        // column at a time would
+        for (int64_t e = e0; e < e1; ++e) {
+            const double v = vals[src[e]];
+            const double *xe = X + ci[e] + (int64_t)c0 * ldx;
+#pragma unroll
+            for (int c = 0; c < kResRhs; ++c)
+                if (c < nc) s[c] += v * xe[(int64_t)c * ldx];
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            r = max(r, __shfl_down_sync(0xffffffffu, r, o));
-            ax = max(ax, __shfl_down_sync(0xffffffffu, ax, o));
-            ab = max(ab, __shfl_down_sync(0xffffffffu, ab, o));
-        }
-        if (lane == 0) {
-            atomicMax(norms + 3 * c + 0, r);
-            atomicMax(norms + 3 * c + 1, ax);
-            atomicMax(norms + 3 * c + 2, ab);
+        for (int c = 0; c < kResRhs; ++c) {
+            if (c >= nc) break;
+            const int cc = c0 + c;
+            unsigned long long r = 0, ax = 0, ab = 0;
+            if (i < n) {
+                const double b = B[i + cc * ldb];
+                const double rr = b - s[c];
+                R[i + cc * n] = rr;
+                r = abs_bits_inf(rr);
+                ax = abs_bits_inf(X[i + cc * ldx]);
+                ab = abs_bits_inf(b);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r = max(r, __shfl_down_sync(0xffffffffu, r, o));
+                ax = max(ax, __shfl_down_sync(0xffffffffu, ax, o));
+                ab = max(ab, __shfl_down_sync(0xffffffffu, ab, o));
+            }
+            if (lane == 0) {
+                atomicMax(norms + 3 * cc + 0, r);
+                atomicMax(norms + 3 * cc + 1, ax);
+                atomicMax(norms + 3 * cc + 2, ab);
+            }
         }
     }
 }
