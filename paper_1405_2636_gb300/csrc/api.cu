@@ -884,7 +884,9 @@ spx_status ensure_device(spx_handle h)
         h->q_nitems = (int32_t)itf.size();
         // staging sizes in elements, multiples of 4 so that the vectors
         // after the matrices stay aligned for 4-element vector accesses
-        h->q_mat = (wmax * std::max(wmax + 1, 65) + 3) & ~3;
+        // (the backward sweep stores a w x w inverse with an odd leading
+        // dimension, w + 1 or w + 2)
+        h->q_mat = (wmax * std::max(wmax + ((wmax & 1) ? 2 : 1), 65) + 3) & ~3;
         h->q_matb = merge ? (65 * wmax + 3) & ~3 : 0;
         h->q_vec = 16 * std::max(wmax, 64);
         if ((st = upload(h, &h->d_qitems_f, itf)) || (st = upload(h, &h->d_qitems_b, itb)) ||

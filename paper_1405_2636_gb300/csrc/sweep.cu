@@ -377,30 +377,17 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_k
         if (item < 0) {
             // panel: X_p = M (Z_p - Tacc_p - Lc^T X[rows of its first chunk])
             const int pid = -item - 1;
-            const int w = p.pw[pid], h = p.ph[pid], ld = w + 1;
+            // ld odd, so that a warp's rows i of M(i, k) = matA[k + i ld] fall
+            // in distinct banks
+            const int w = p.pw[pid], h = p.ph[pid], ld = (w & 1) ? w + 2 : w + 1;
             const int64_t f = p.pfcol[pid];
             const T *Mi = Dinv + p.pinv[pid];
             const int mc = q.merge[pid];
-            // matA[i + k ld] = M(i, k), k >= i; source element e read in order
-            for (int base = tid; base < w * w; base += kQThreads * 8) {
-                T v[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int e = base + q * kQThreads;
-                    v[q] = e < w * w ? Mi[e] : (T)0;
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int e = base + q * kQThreads;
-                    if (e >= w * w) continue;
-                    // Mi[e] is M(i, k) with (i, k) = (e % w, e / w) (LU: U^{-1}),
-                    // else M(i, k) = Linv(k, i) with (k, i) = (e % w, e / w)
-                    const int a0 = e % w, a1 = e / w;
-                    const int i = lu == 1 ? a0 : a1, k = lu == 1 ? a1 : a0;
-                    const T val = (lu == 2 && k == i) ? (T)1 : v[q];
-                    matA[i + k * ld] = k >= i ? val : (T)0;
-                }
-            }
+            // the stored inverse as it is, column-major with leading dimension ld (by
+            // asynchronous copies): M(i, k) is matA[i + k ld] for LU (U^{-1})
+            // and matA[k + i ld] = Linv(k, i) otherwise; only k >= i is read
+            for (int e = tid; e < w * w; e += kQThreads) cp_async_elem(matA + (e % w) + (e / w) * ld, Mi + e, true);
+            stage_commit();
             int nr = 0, t0 = 0, m = 0;
             int64_t row = 0;
             if (mc >= 0) {
@@ -495,9 +482,15 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 5 : 4) bwd_queue_k
                 }
                 for (int i = rt; i < w; i += 64) {
                     T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+                    int k = i;
+                    if (lu == 2) {   // LDL^T: l^{-T} has a unit diagonal
+                        ld_quad(vec, i, g, acc);
+                        ++k;
+                    }
+                    const int sa = lu == 1 ? 1 : ld, sk = lu == 1 ? ld : 1;   // M(i, k) = matA[i sa + k sk]
 #pragma unroll 4
-                    for (int k = i; k < w; ++k) {
-                        const T a = matA[i + k * ld];
+                    for (; k < w; ++k) {
+                        const T a = matA[i * sa + k * sk];
                         T v[4];
                         ld_quad(vec, k, g, v);
 #pragma unroll
